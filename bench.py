@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the overlap operator's hot path on GB300.
+
+Metric: sgn(gamma5 D_w(mu)) b solves/s at 1e-8 relative error (mixed
+precision two-pass two-sided Lanczos, with the FP64 form beside it), plus the
+Wilson stencil's bandwidth against the HBM roof.
+
+Workload (one step = one solve D_ov(mu) b = b + gamma5 sgn(A) b of one
+Gaussian source): 8^4 lattice (N = 49152), SU(3) links U = exp(i eps H) with
+eps = 1.0, m_w = -1.5 (kappa = 0.2), mu = 0.3, antiperiodic time.  The Krylov
+size k is the smallest on a grid whose result agrees with a self-converged
+FP64 solve (k = 1000) to 1e-8.  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (a 512 MiB write) before every timed step and
+each step is timed on the device with CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: each rank solves its own sources on its own GPU
+(replicas; the path has no data exchange), the max over ranks of the timed
+device time sets the aggregate rate.  --impl reference times the FP64 CPU
+oracle (scipy sparse matvec) on the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sgn(γ5Dw(μ))b solves/s at 1e-8 rel err, mixed vs FP64; Dw GB/s vs HBM peak"
+DIMS = (8, 8, 8, 8)
+EPS, SEED_U, SEED_B = 1.0, 1001, 2001
+MU, KAPPA = 0.3, 0.2
+K_GRID = list(range(300, 1001, 50))
+K_REF = 1000
+DW_DIMS = (48, 48, 48, 64)  # 7.1M sites: every stencil operand is far larger than L2
+WORKLOAD = "8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3, Gaussian b, two-sided Lanczos"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 ALU roof: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# algorithmic work per site: Wilson hopping term 1320 flop, diagonal and
+# gamma5 48 flop; FP64 bytes: 4 links (576) + x (192) + y (192)
+DW_FLOP_SITE = 1368
+DW_BYTES = {"f64": 960, "f32_12": 384, "f32_18": 480}
+# two-pass regeneration step (FP64): stencil + recurrence/accumulate epilogue of 12 complex
+REGEN_FLOP_SITE = DW_FLOP_SITE + 12 * 30
+REGEN_BYTES_SITE = 576 + 192 + 192 + 2 * 192 + 192
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(torch, n_src, rank):
+    from paper_0810_4228_gb300 import synth
+    U = synth.gauge_field(DIMS, EPS, SEED_U)
+    srcs = synth.gaussian_source(DIMS, SEED_B + 7919 * rank, nrhs=n_src)
+    return U, srcs
+
+
+def calibrate_k(ovl, ctx, torch, b, flags_list):
+    """Smallest k on K_GRID whose solve agrees with the FP64 k=1000 solve to 1e-8."""
+    ref, _ = ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, b)
+    ref = ref.clone()
+    nrm = torch.linalg.vector_norm(ref).item()
+    out = {}
+    for name, fl in flags_list:
+        chosen, err = K_GRID[-1], None
+        for k in K_GRID:
+            y, info = ctx.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, b, flags=fl)
+            e = torch.linalg.vector_norm(y - ref).item() / nrm
+            if e <= 1e-8:
+                chosen, err = k, e
+                break
+            err = e
+        out[name] = (chosen, err)
+    return out
+
+
+def time_solves(torch, ctx, fn, bufs, warmup, steps, flush):
+    """Per-step device time (CUDA events on the library's stream), L2 flushed before each step."""
+    st = torch.cuda.current_stream()
+    times = []
+    for i in range(warmup + steps):
+        flush.fill_(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn(bufs[i % len(bufs)])
+        e1.record(st)
+        e1.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    return times
+
+
+def dw_bandwidth(torch, ovl, reps=20):
+    """Stencil GB/s on a lattice far larger than L2 (device-layout vectors)."""
+    from paper_0810_4228_gb300 import synth
+    dims = DW_DIMS
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    ctx = ovl.Context(dims)
+    U = synth.gauge_field_torch(dims, EPS, SEED_U, device="cuda")
+    ctx.set_gauge(U)
+    del U
+    torch.cuda.empty_cache()
+    res = {}
+    st = torch.cuda.current_stream()
+    for name, flag, prec in (("f32_12", ovl.F32, 1), ("f32_18", ovl.F32_FULL, 1), ("f64", 0, 0)):
+        x = ctx.empty_native(prec)
+        if prec == 1:
+            x.copy_(torch.randn(ctx.n, dtype=torch.complex64, device="cuda"))
+        else:
+            x.copy_(torch.randn(ctx.n, dtype=torch.complex128, device="cuda"))
+        y = ctx.empty_native(prec)
+        for _ in range(3):
+            ctx.apply_Dw(MU, KAPPA, x, y, flags=ovl.GAMMA5 | ovl.NATIVE | flag)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            ctx.apply_Dw(MU, KAPPA, x, y, flags=ovl.GAMMA5 | ovl.NATIVE | flag)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "GB_s": DW_BYTES[name] * V / ms / 1e6, "GFLOP_s": DW_FLOP_SITE * V / ms / 1e6}
+        del x, y
+    ctx.close()
+    torch.cuda.empty_cache()
+    return dims, V, res
+
+
+def cpu_baseline(k: int, budget_s: float = 30.0):
+    """The FP64 oracle's two-sided Lanczos on the same workload, single-threaded, in a child process."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import wilson as W, krylov as K
+from paper_0810_4228_gb300 import synth
+U = synth.gauge_field({DIMS!r}, {EPS}, {SEED_U})
+b = synth.gaussian_source({DIMS!r}, {SEED_B})
+A = W.a_operator(U, {DIMS!r}, {MU}, {KAPPA})
+Ad = A.conj().T.tocsr()
+t0 = time.perf_counter()
+K.lanczos2(A.dot, Ad.dot, b / np.linalg.norm(b), b / np.linalg.norm(b), 20)
+t20 = time.perf_counter() - t0
+k = {k}
+frac = min(1.0, {budget_s} / max(t20 * k / 20.0, 1e-9))
+ks = max(20, int(k * frac))
+t0 = time.perf_counter()
+y = K.sign_lanczos2(A.dot, Ad.dot, b, ks)
+t = time.perf_counter() - t0
+print(json.dumps({{"t": t, "ks": ks, "k": k}}))
+"""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    per_solve = d["t"] * d["k"] / d["ks"]  # basis cost is linear in k; inner sign is small at this k
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one FP64 oracle two-sided Lanczos solve with {d['ks']} of k={d['k']} steps "
+                       f"(scipy CSR matvec + numpy, 1 thread) on the same 8^4 field and source, "
+                       f"{d['t']:.1f} s, scaled by k/{d['ks']}")}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    k = args.k or 600
+    t_all = []
+    # each step is a bounded sample: a two-sided Lanczos run of the oracle
+    budget = max(2.0, 200.0 / max(args.steps + args.warmup, 1))
+    for i in range(args.warmup + args.steps):
+        d = cpu_baseline(k, budget_s=budget)
+        if i >= args.warmup:
+            t_all.append(1.0 / d["value"])
+    per = sum(t_all) / len(t_all)
+    val = 1.0 / per
+    line = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "mu": MU, "kappa": KAPPA, "eps": EPS, "k": k},
+            "impl": "reference",
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": d["sample"]},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_0810_4228_gb300 import ovl
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ovl.load()
+    hbm_peak, peak_kind = peaks()
+    nbuf = max(args.steps + args.warmup, 1)
+    U, srcs = make_inputs(torch, nbuf, rank)
+    ctx = ovl.Context(DIMS)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    bdev = [torch.from_numpy(srcs[i]).cuda() for i in range(nbuf)]
+    out = torch.empty_like(bdev[0])
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    # ---- accuracy calibration (untimed)
+    if args.k:
+        cal = {"mixed": (args.k, None), "fp64": (args.k, None)}
+    else:
+        cal = calibrate_k(ovl, ctx, torch, bdev[0], [("mixed", ovl.MIXED), ("fp64", 0)])
+    k_mix, err_mix = cal["mixed"]
+    k_64, err_64 = cal["fp64"]
+    fl_mix = ovl.MIXED | ovl.OVERLAP
+    fl_64 = ovl.OVERLAP
+
+    # ---- per-kernel profile of one solve (CUDA events around every kernel class)
+    ctx.profile(reset=True)
+    ctx.sign_krylov(ovl.LANCZOS2, k_mix, MU, KAPPA, bdev[0], out, flags=fl_mix | ovl.PROFILE)
+    prof = ctx.profile(reset=True)
+    kernels_per_solve = sum(v["kernels"] for v in prof.values())
+
+    # ---- timed region: mixed two-pass (headline), device-resident inputs
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_mix = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_mix, MU, KAPPA, b, out, flags=fl_mix),
+                        bdev, args.warmup, args.steps, flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot = sum(t_mix)
+    if world > 1:
+        tt = torch.tensor([tot], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tot = tt.item()
+        torch.distributed.barrier()
+    value = world * args.steps / (tot / 1e3)
+
+    # ---- FP64 form and Arnoldi (context, fewer steps)
+    t_64 = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_64, MU, KAPPA, b, out, flags=fl_64),
+                       bdev, 2, max(3, min(args.steps, 5)), flush)
+    t_arn = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, min(k_64, 600), MU, KAPPA, b, out,
+                                                              flags=ovl.OVERLAP),
+                        bdev, 1, 2, flush)
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    bh = torch.empty(bdev[0].shape, dtype=bdev[0].dtype, pin_memory=True)
+    oh = torch.empty_like(bh)
+    hsrc = [b.cpu().pin_memory() for b in bdev]
+
+    def e2e_step(b):
+        ctx.sign_krylov(ovl.LANCZOS2, k_mix, MU, KAPPA, b, oh, flags=fl_mix)
+
+    t_e2e = time_solves(torch, ctx, e2e_step, hsrc, args.warmup, args.steps, flush)
+    tot_e2e = sum(t_e2e)
+    e2e_val = world * args.steps / (tot_e2e / 1e3)
+    nbytes = bdev[0].numel() * bdev[0].element_size()
+
+    # ---- dominant kernel of the solve and its roofline
+    V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else ("none", {"ms": 0, "launches": 1})
+    dname, dstat = dom
+    per_launch_ms = dstat["ms"] / max(dstat["launches"], 1)
+    if dname == "dslash_regen":
+        roof = {"bound": "alu", "achieved": REGEN_FLOP_SITE * V / per_launch_ms / 1e9,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    elif dname == "dslash_pair":
+        roof = {"bound": "hbm", "achieved": 2 * 96 * 2 * V / per_launch_ms / 1e6 + 192 * V / per_launch_ms / 1e6,
+                "peak": hbm_peak, "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    if roof["achieved"] is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"kernel": dname, "ms_per_launch": per_launch_ms, "traffic": None,
+                 "peak_kind": ("derived FP64 roof 152 SM x 2 FMA/clk x 2.07 GHz" if roof["bound"] == "alu"
+                               else f"{peak_kind} hbm_gbs")})
+
+    # ---- stencil bandwidth on a lattice far larger than L2
+    dw = None
+    if rank == 0 and not args.no_dw:
+        try:
+            ddims, dV, dres = dw_bandwidth(torch, ovl)
+        except Exception as exc:  # report, keep the solve measurement
+            dres, ddims, dV = {}, DW_DIMS, 0
+            dw = {"error": repr(exc)[:200]}
+        dw = dw or {"dims": list(ddims), "sites": dV}
+        for nm, r in dres.items():
+            dw[nm] = {"ms": round(r["ms"], 4), "GB_s": round(r["GB_s"], 1), "frac_hbm": round(r["GB_s"] / hbm_peak, 3),
+                      "GFLOP_s": round(r["GFLOP_s"], 1)}
+            if nm == "f64":
+                dw[nm]["frac_fp64_roof"] = round(r["GFLOP_s"] / (FP64_PEAK_TFLOPS * 1e3), 3)
+        dw["hbm_peak_gbs"] = hbm_peak
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(k_mix)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(t_mix), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "mu": MU, "kappa": KAPPA, "eps": EPS,
+                       "method": "two-sided Lanczos, two-pass mixed (FP32 pass 1, FP64 pass 2)",
+                       "k": k_mix, "m_deflated": 0, "rel_err_vs_k1000_fp64": err_mix,
+                       "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": kernels_per_solve * args.steps,
+            "clocks": clk,
+            "fp64": {"solves_per_s": 1e3 / statistics.mean(t_64), "ms": statistics.mean(t_64), "k": k_64,
+                     "rel_err_vs_k1000_fp64": err_64},
+            "arnoldi_fp64": {"solves_per_s": 1e3 / statistics.mean(t_arn), "ms": statistics.mean(t_arn),
+                             "k": min(k_64, 600)},
+            "profile_ms_per_solve": {k: round(v["ms"], 4) for k, v in prof.items()},
+            "dw": dw,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=0, help="fix the Krylov size (skip the accuracy calibration)")
+    ap.add_argument("--no-dw", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * ovl.h -- C ABI of the GB300 library computing the overlap Dirac operator at
+ * nonzero chemical potential,
+ *
+ *     D_ov(mu) b = b + gamma5 sgn(gamma5 D_w(mu)) b            (Sec. 1, Eq. 1.1)
+ *
+ * with the Arnoldi (Sec. 2, Eq. 2.6) and two-sided Lanczos (Sec. 4, Eq. 4.4)
+ * Krylov approximations of sgn(A) b, A = gamma5 D_w(mu), and LR deflation of
+ * the critical eigenvalues (Sec. 3, Eq. 3.4; Sec. 4, Eq. 4.5).
+ *
+ * Conventions (fixed by this library; the paper leaves them open):
+ *   - lattice dims[4] = (L1, L2, L3, L4), L4 = Euclidean time; every extent
+ *     >= 2 and L4 even (the device layout is even/odd ordered).
+ *   - canonical site index s = ((x1*L2 + x2)*L3 + x3)*L4 + x4 (time fastest).
+ *   - gauge field: complex128 U[V][4][3][3], U[s][nu] = link from x to x+nu.
+ *   - spinor: complex128 psi[V][4][3] (spin, colour), gamma matrices in the
+ *     chiral basis, gamma5 = diag(1, 1, -1, -1).
+ *   - hops of Eq. 1.2: (T_nu^+ psi)(x) = (1 + gamma_nu) U_{x,nu} psi(x + nu),
+ *     (T_nu^- psi)(x) = (1 - gamma_nu) U_{x-nu,nu}^dag psi(x - nu);
+ *     e^{+mu} multiplies T_4^+, e^{-mu} multiplies T_4^-.
+ *   - boundary: periodic in space, bc_t = -1 (antiperiodic) or +1 in time.
+ *   - complex numbers are interleaved (re, im) pairs of double.
+ *
+ * Memory: unless OVL_HOST is given, every pointer argument that names a
+ * field is a DEVICE pointer owned by the caller, which keeps it alive until
+ * the work queued on the context's stream has finished.  The library owns
+ * only its workspace (device memory it allocates with cudaMalloc on first
+ * use and frees in ovl_destroy).  All work is queued on the stream given to
+ * ovl_create; calls that return results to the host (info structs, status)
+ * synchronise that stream.
+ *
+ * Errors: every function returns an ovl_status; OVL_OK is 0.  On failure
+ * ovl_last_error(ctx) returns a message; outputs are then unspecified.
+ * A context is not thread safe: one host thread at a time.
+ */
+#ifndef OVL_H
+#define OVL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OVL_OK = 0,
+    OVL_EINVAL = 1,      /* bad argument (sizes, flags, null pointer, mismatched mu/kappa) */
+    OVL_ENOMEM = 2,      /* device allocation failed */
+    OVL_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    OVL_EBREAKDOWN = 4,  /* serious breakdown of two-sided Lanczos: w_hat^dag v_hat = 0 */
+    OVL_ESINGULAR = 5,   /* sgn undefined (eigenvalue on the imaginary axis) or singular matrix */
+    OVL_ENOCONV = 6,     /* the inner sign iteration did not converge */
+    OVL_ETIMEOUT = 7,    /* a bounded device-side wait gave up; the context stays usable */
+    OVL_ESTATE = 8       /* call order: gauge field or deflation not set */
+} ovl_status;
+
+typedef struct ovl_ctx ovl_ctx;
+
+/* Methods of sgn(A) b. */
+#define OVL_ARNOLDI   0   /* Sec. 2, Eq. 2.6 (with deflation Eq. 3.4) */
+#define OVL_LANCZOS2  1   /* Sec. 4, Eq. 4.4 (with deflation Eq. 4.5)  */
+
+/* Flags (bit set). */
+#define OVL_GAMMA5       0x0001  /* apply_Dw: y = gamma5 D_w(mu) x  (A x)                  */
+#define OVL_DAGGER       0x0002  /* apply_Dw: y = A^dag x = gamma5 D_w(-mu) x              */
+#define OVL_NATIVE       0x0004  /* x, y in the device layout (see ovl_vector_bytes)       */
+#define OVL_HOST         0x0008  /* field pointers are host memory (canonical layout)      */
+#define OVL_F32          0x0010  /* apply_Dw: FP32 stencil with 12-real links (NATIVE FP32 vectors) */
+#define OVL_F32_FULL     0x0020  /* apply_Dw: FP32 stencil with 18-real links              */
+#define OVL_OVERLAP      0x0100  /* sign_krylov: out = D_ov b = b + gamma5 sgn(A) b,
+                                    otherwise out = sgn(A) b                               */
+#define OVL_MIXED        0x0200  /* sign_krylov: FP32 basis + 12-real links in pass 1, FP64
+                                    coefficients, FP64 regeneration pass (two-pass, Sec. 5) */
+#define OVL_TWO_PASS     0x0400  /* sign_krylov LANCZOS2: do not store the basis, regenerate it
+                                    from alpha, beta, gamma in a second pass (Sec. 5)       */
+#define OVL_INNER_NEWTON 0x1000  /* inner sgn(G_k): Roberts/Newton (Sec. 2) instead of the
+                                    resolvent quadrature (2sL only)                        */
+#define OVL_NO_GRAPH     0x2000  /* sign_krylov: launch kernels directly, no CUDA graph     */
+#define OVL_PROFILE      0x4000  /* sign_krylov: time every kernel class with CUDA events on the
+                                    context's stream (implies OVL_NO_GRAPH); read the totals with
+                                    ovl_profile_get                                        */
+
+/* Information returned by ovl_sign_krylov. */
+typedef struct {
+    int    k_used;          /* Krylov steps taken (< k after a lucky breakdown)          */
+    int    breakdown_step;  /* step of a serious breakdown, -1 if none                   */
+    int    inner_iters;     /* Newton iterations, or quadrature nodes, of the inner sign */
+    int    inner_method;    /* 0 = quadrature, 1 = Newton                                */
+    double bperp_norm;      /* |b_perp^R| (|b| without deflation)                         */
+    double inner_err;       /* a-posteriori estimate of the inner sign's relative error  */
+} ovl_info;
+
+/* --- context ---------------------------------------------------------------------------- */
+
+/* Create a context for one lattice on the current CUDA device; stream is a
+ * cudaStream_t (NULL = legacy default stream).  Fails with OVL_EINVAL if an
+ * extent is < 2 or L4 is odd, or bc_t is not +-1. */
+int ovl_create(ovl_ctx** ctx, const int dims[4], int bc_t, void* stream);
+int ovl_destroy(ovl_ctx* ctx);
+const char* ovl_last_error(const ovl_ctx* ctx);
+/* Change the stream later work is queued on. */
+int ovl_set_stream(ovl_ctx* ctx, void* stream);
+/* Bytes of one vector in the device layout: prec 0 = FP64 (12V complex128),
+ * 1 = FP32 (12V complex64).  The layout is site-major in even/odd order with
+ * 16-byte components [component-chunk][site] (see the implementation). */
+size_t ovl_vector_bytes(const ovl_ctx* ctx, int prec);
+
+/* --- gauge field ------------------------------------------------------------------------- */
+
+/* Install U (canonical complex128 [V][4][3][3], SU(3) links).  The library
+ * keeps an FP64 copy and FP32 copies (12-real: rows 0,1; 18-real) in the
+ * device layout.  flags: OVL_HOST if U is host memory. */
+int ovl_set_gauge(ovl_ctx* ctx, const void* U, int flags);
+
+/* --- the Wilson operator (Sec. 1, Eq. 1.2) ---------------------------------------------- */
+
+/* y = D_w(mu) x, gamma5 D_w(mu) x (OVL_GAMMA5) or gamma5 D_w(-mu) x (OVL_DAGGER), with
+ * kappa = 1/(8 + 2 m_w).  Canonical complex128 vectors by default; with OVL_NATIVE
+ * x and y are device-layout vectors (FP64, or FP32 with OVL_F32 / OVL_F32_FULL).
+ * x and y must not overlap. */
+int ovl_apply_Dw(ovl_ctx* ctx, double mu, double kappa, const void* x, void* y, int flags);
+
+/* Pair application of the two-sided Lanczos step (Sec. 4, Eq. 4.2): t = A v and s = A^dag w
+ * in one pass over the links, plus alpha = w^dag t (FP64 accumulation) written to
+ * *alpha_host (2 doubles) if non-NULL.  Device-layout vectors; prec 0 = FP64,
+ * 1 = FP32 with 12-real links. */
+int ovl_apply_pair(ovl_ctx* ctx, double mu, double kappa, int prec,
+                   const void* v, const void* w, void* t, void* s, double* alpha_host);
+
+/* Convert a canonical complex128 vector (device) into the device layout (prec 0 or 1)
+ * and back. */
+int ovl_pack(ovl_ctx* ctx, const void* canon, void* native, int prec);
+int ovl_unpack(ovl_ctx* ctx, const void* native, void* canon, int prec);
+
+/* --- deflation (Sec. 3, Eq. 3.1; Sec. 5) ------------------------------------------------- */
+
+/* Install m critical eigenpairs of A = gamma5 D_w(mu) for the given (mu, kappa):
+ * lambda: host array of m complex (2m doubles); R, L: canonical complex128 [m][12V]
+ * right and left eigenvectors (A r_j = lambda_j r_j, l_j^dag A = lambda_j l_j^dag).
+ * The library makes them bi-orthonormal, L <- L (L^dag R)^-H, and returns OVL_ESINGULAR
+ * if L^dag R is numerically singular.  m = 0 removes the deflation.  Later sign_krylov
+ * calls must use the same mu and kappa (else OVL_EINVAL). */
+int ovl_set_deflation(ovl_ctx* ctx, double mu, double kappa, int m, const double* lambda,
+                      const void* R, const void* L, int flags);
+
+/* Copy the installed (bi-orthonormalised) deflation out: *m_out = m; lambda (host, 2m
+ * doubles), R and L canonical complex128 [m][12V] (device, or host with OVL_HOST).  NULL
+ * output pointers are skipped (pass R = L = lambda = NULL to query m). */
+int ovl_get_deflation(ovl_ctx* ctx, int* m_out, double* lambda, void* R, void* L, int flags);
+
+/* --- sgn(A) b and D_ov(mu) b ------------------------------------------------------------- */
+
+/* out = sgn(A) b (or D_ov(mu) b with OVL_OVERLAP), A = gamma5 D_w(mu), by the method
+ * (OVL_ARNOLDI / OVL_LANCZOS2) with Krylov size k >= 1 and the installed deflation.
+ * b, out: canonical complex128 (device, or host with OVL_HOST), may not overlap.
+ * info may be NULL.  Returns OVL_EBREAKDOWN on a serious 2sL breakdown (out holds the
+ * approximation from the steps before it), OVL_ESINGULAR if the projected matrix has an
+ * eigenvalue on the imaginary axis, OVL_ENOCONV if the inner sign did not converge. */
+int ovl_sign_krylov(ovl_ctx* ctx, int method, int k, double mu, double kappa,
+                    const void* b, void* out, int flags, ovl_info* info);
+
+/* --- per-kernel profile -------------------------------------------------------------------- */
+
+/* One kernel class of a profiled solve: its name, how many times it was queued, how many
+ * kernels those launches contain and their total device time (CUDA events). */
+typedef struct {
+    char      name[24];
+    int       launches;
+    long long kernels;
+    double    ms;
+} ovl_kstat;
+
+/* Accumulated per-class totals of every OVL_PROFILE solve since the last reset.  Writes at
+ * most max entries to out and the number of classes with data to *count. */
+int ovl_profile_get(ovl_ctx* ctx, ovl_kstat* out, int max, int* count);
+int ovl_profile_reset(ovl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OVL_H */

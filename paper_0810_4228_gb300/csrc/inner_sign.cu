@@ -1,0 +1,458 @@
+// The inner sign function c = |b_perp| sgn(G_k) e_1 of the projected k x k
+// matrix (Sec. 2, Eq. 2.6 and the remark after it; Sec. 4, Eq. 4.4-4.5).
+//
+// Two methods, both FP64 and both driven entirely from device memory (the
+// matrix size is the number of Krylov steps actually taken, read from the
+// solve state), so they can be captured in a CUDA graph.
+//
+// (1) Resolvent quadrature, for the tridiagonal G_k of two-sided Lanczos.
+//     For a matrix with no eigenvalue on the imaginary axis,
+//         sgn(G) = (2/pi) int_0^inf G (G^2 + t^2)^-1 dt
+//                = (1/pi) int_R e^u [(G + i e^u)^-1 + (G - i e^u)^-1] du,   t = e^u,
+//     which reproduces sgn z = z / sqrt(z^2) (Sec. 1, Eq. 1.4) eigenvalue by
+//     eigenvalue.  The u-integrand is analytic in a strip whose half-width is
+//     the smallest angle between an eigenvalue and the imaginary axis, so the
+//     trapezoidal rule converges geometrically.  Each node costs one
+//     tridiagonal solve (Gaussian elimination with partial pivoting, O(k)),
+//     one thread per node; the step is halved (reusing all earlier nodes)
+//     until two successive sums agree.  Cost O(nodes * k) instead of the
+//     O(k^3) per iteration of a dense matrix iteration; on this GPU FP64 runs
+//     at 1/58 of the FP32 rate, which makes the difference decisive.
+// (2) Roberts' iteration S <- (S + S^-1)/2, S^0 = G (Sec. 2), with
+//     |det S|^(-1/n) scaling of the first iterates; the inverse by in-place
+//     Gauss-Jordan elimination with partial pivoting in one cooperative kernel
+//     (rows distributed over all SMs, bounded grid barriers).  Used for the
+//     Hessenberg H_k of Arnoldi and on request for G_k.
+#include <math.h>
+
+#include "ovl_kernels.h"
+
+namespace ovl {
+
+static constexpr double QUAD_H0 = 0.25;       // first trapezoid step in u
+static constexpr double QUAD_HALFWIDTH = 45;  // u range: log|G| -+ 45
+static constexpr int QUAD_LEVELS = 6;         // steps 0.25 ... 0.25/32
+
+static int quad_nodes_level0() { return (int)ceil(2 * QUAD_HALFWIDTH / QUAD_H0); }
+static int quad_threads(int level) {
+    const int m0 = quad_nodes_level0();
+    const int nodes = level == 0 ? m0 : m0 << (level - 1);
+    return 2 * nodes;  // +- i e^u
+}
+
+size_t inner_work_elems(int kmax, int method) {
+    if (method == 0) {
+        // per thread and row: 3 complex (b/d, u/d, w/d), plus T and S sums
+        return (size_t)quad_threads(QUAD_LEVELS - 1) * (size_t)kmax * 3 + 2 * (size_t)kmax + 64;
+    }
+    // Newton: S, X (kmax^2 each) + pivots, slots, scalars, barrier, partials
+    return 2 * (size_t)kmax * kmax + 4 * (size_t)kmax + 8192;
+}
+
+// ---------------------------------------------------------- quadrature --
+// log of a Gershgorin bound on |lambda_max(G)| -> ks->red[7].x
+__global__ void k_quad_prep(const double2* alpha, const double2* beta, const double2* gamma, KState* ks) {
+    __shared__ double red[32];
+    const int n = ks->kused;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double r = hypot(alpha[i].x, alpha[i].y);
+        if (i > 0) r += hypot(beta[i - 1].x, beta[i - 1].y);
+        if (i + 1 < n) r += hypot(gamma[i].x, gamma[i].y);
+        m = fmax(m, r);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
+        ks->red[7] = make_double2(log(fmax(mm, 1e-300)), 0.0);
+        ks->inner_done = 0;
+        ks->inner_iters = 0;
+        ks->inner_method = 0;
+        ks->inner_err = 0.0;
+        if (n == 0) ks->inner_done = 1;
+    }
+}
+
+// One thread per (node, sign): solve (G + s i e^u) x = e_1, store e^u x in the
+// scratch column of the thread (row-major over rows, thread fastest).
+__global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* __restrict__ beta,
+                             const double2* __restrict__ gamma, KState* ks, double2* __restrict__ work, int level,
+                             int nthreads) {
+    if (ks->inner_done || ks->status || ks->timeout) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nthreads) return;
+    const int n = ks->kused;
+    const double lo = ks->red[7].x - QUAD_HALFWIDTH;
+    const int node = t >> 1;
+    const double sgn = (t & 1) ? -1.0 : 1.0;
+    double u;
+    if (level == 0) {
+        u = lo + node * QUAD_H0;
+    } else {
+        const double hl = QUAD_H0 / (double)(1 << level);
+        u = lo + (2 * node + 1) * hl;
+    }
+    const double tau = exp(u);
+    const cx<double> sig = mk(0.0, sgn * tau);
+    // arrays: bd = b/d, ud = u/d, wd = w/d of the final (upper triangular) rows
+    double2* bd = work;
+    double2* ud = work + (size_t)n * nthreads;
+    double2* wd = work + 2 * (size_t)n * nthreads;
+#define IDX(i) ((size_t)(i) * nthreads + t)
+    // current row i: (d, u) at (i, i+1), rhs rb
+    cx<double> d = d2c(alpha[0]) + sig;
+    cx<double> uu = n > 1 ? d2c(gamma[0]) : mk(0.0, 0.0);
+    cx<double> rb = mk(1.0, 0.0);
+    for (int i = 0; i + 1 < n; ++i) {
+        const cx<double> l = d2c(beta[i]);                    // row i+1, column i
+        const cx<double> dn = d2c(alpha[i + 1]) + sig;        // row i+1, column i+1
+        const cx<double> un = (i + 2 < n) ? d2c(gamma[i + 1]) : mk(0.0, 0.0);
+        if (norm2(d) >= norm2(l)) {
+            // no interchange: final row i = (d, uu, 0)
+            const cx<double> m = cdiv(l, d);
+            const cx<double> id = cdiv(mk(1.0, 0.0), d);
+            bd[IDX(i)] = c2d(rb * id);
+            ud[IDX(i)] = c2d(uu * id);
+            wd[IDX(i)] = make_double2(0.0, 0.0);
+            d = dn - m * uu;
+            uu = un;
+            rb = mk(0.0, 0.0) - m * rb;   // rhs of row i+1 is 0 for e_1 beyond row 0
+        } else {
+            // interchange rows i and i+1: final row i = (l, dn, un), rhs 0
+            const cx<double> m = cdiv(d, l);
+            const cx<double> il = cdiv(mk(1.0, 0.0), l);
+            bd[IDX(i)] = make_double2(0.0, 0.0);
+            ud[IDX(i)] = c2d(dn * il);
+            wd[IDX(i)] = c2d(un * il);
+            const cx<double> nd = uu - m * dn;
+            const cx<double> nu = mk(0.0, 0.0) - m * un;
+            d = nd;
+            uu = nu;
+            // new rhs of row i+1: rb (old row i) - m * 0
+        }
+    }
+    if (norm2(d) == 0.0) {
+        atomicExch(&ks->status, 5);  // singular shifted matrix
+        return;
+    }
+    // back substitution, x overwrites bd
+    const cx<double> w8 = mk(tau, 0.0);
+    cx<double> x1 = cdiv(rb, d), x2 = mk(0.0, 0.0);
+    bd[IDX(n - 1)] = c2d(w8 * x1);
+    for (int i = n - 2; i >= 0; --i) {
+        cx<double> x = d2c(bd[IDX(i)]) - d2c(ud[IDX(i)]) * x1 - d2c(wd[IDX(i)]) * x2;
+        bd[IDX(i)] = c2d(w8 * x);
+        x2 = x1;
+        x1 = x;
+    }
+#undef IDX
+}
+
+// T_l = (l == 0 ? 0 : T_{l-1}/2) + (h_l/pi) sum_threads x ; convergence on |T_l - T_{l-1}|.
+__global__ void k_quad_sum(const double2* __restrict__ work, double2* __restrict__ T, double2* __restrict__ c,
+                           KState* ks, int level, int nthreads, double* partials, unsigned int* counter) {
+    __shared__ double red[96];
+    if (ks->inner_done || ks->status || ks->timeout) return;
+    const int n = ks->kused;
+    const double hl = QUAD_H0 / (double)(1 << level);
+    const double wgt = hl / M_PI;
+    double part[2] = {0.0, 0.0};  // |T_l - T_{l-1}|^2, |T_l|^2
+    // one warp per row i
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = blockIdx.x * nw + wid; i < n; i += gridDim.x * nw) {
+        double sr = 0.0, si = 0.0;
+        for (int t = lane; t < nthreads; t += 32) {
+            double2 v = work[(size_t)i * nthreads + t];
+            sr += v.x;
+            si += v.y;
+        }
+        sr = warp_sum(sr);
+        si = warp_sum(si);
+        if (lane == 0) {
+            double2 old = level == 0 ? make_double2(0.0, 0.0) : T[i];
+            double2 nt = make_double2((level == 0 ? 0.0 : 0.5 * old.x) + wgt * sr,
+                                      (level == 0 ? 0.0 : 0.5 * old.y) + wgt * si);
+            T[i] = nt;
+            const double nr = ks->nR;
+            c[i] = make_double2(nr * nt.x, nr * nt.y);
+            part[0] += (nt.x - old.x) * (nt.x - old.x) + (nt.y - old.y) * (nt.y - old.y);
+            part[1] += nt.x * nt.x + nt.y * nt.y;
+        }
+    }
+    double out[2];
+    if (grid_sum_last<2>(part, partials, counter, out, red)) {
+        if (threadIdx.x == 0) {
+            const double diff = sqrt(out[0]), nrm = sqrt(out[1]);
+            ks->inner_iters += nthreads;
+            if (level > 0) {
+                // geometric convergence: the error of T_l is about (diff/|T|)^2
+                const double rel = diff / fmax(nrm, 1e-300);
+                ks->inner_err = rel * rel;
+                if (rel <= 1e-7) ks->inner_done = 1;
+            }
+            if (level == QUAD_LEVELS - 1 && !ks->inner_done) ks->status = 6;  // no convergence
+        }
+    }
+}
+
+int launch_inner_quadrature(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,
+                            double2* c, double2* work, size_t work_elems, int kmax, double* partials,
+                            unsigned int* counter, cudaStream_t st) {
+    const int tmax = quad_threads(QUAD_LEVELS - 1);
+    if (inner_work_elems(kmax, 0) > work_elems) return -1;
+    double2* T = work + (size_t)tmax * kmax * 3;
+    k_quad_prep<<<1, 256, 0, st>>>(alpha, beta, gamma, ks);
+    for (int level = 0; level < QUAD_LEVELS; ++level) {
+        const int nt = quad_threads(level);
+        k_quad_solve<<<(nt + 127) / 128, 128, 0, st>>>(alpha, beta, gamma, ks, work, level, nt);
+        int blocks = (kmax + 7) / 8;
+        if (blocks > 256) blocks = 256;
+        k_quad_sum<<<blocks, 256, 0, st>>>(work, T, c, ks, level, nt, partials, counter);
+    }
+    return 0;
+}
+
+// --------------------------------------------------------------- Newton --
+struct NewtonWork {
+    double2* S;            // n x n (ld kmax), current iterate
+    double2* X;            // n x n, inverse workspace
+    int* pivrow;           // kmax
+    int* invr;             // kmax
+    unsigned long long* slot;  // kmax + 1
+    double* scal;          // [0] logdet, [1] mu, [2] diff2, [3] norm2, [4] final flag
+    unsigned int* bar;     // grid barrier (count, generation)
+    unsigned int* counter;
+    double* partials;
+};
+
+static NewtonWork newton_layout(double2* work, int kmax) {
+    NewtonWork w;
+    w.S = work;
+    w.X = work + (size_t)kmax * kmax;
+    char* p = reinterpret_cast<char*>(work + 2 * (size_t)kmax * kmax);
+    w.pivrow = reinterpret_cast<int*>(p);
+    p += sizeof(int) * kmax;
+    w.invr = reinterpret_cast<int*>(p);
+    p += sizeof(int) * kmax;
+    p = reinterpret_cast<char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    w.slot = reinterpret_cast<unsigned long long*>(p);
+    p += sizeof(unsigned long long) * (kmax + 1);
+    w.scal = reinterpret_cast<double*>(p);
+    p += sizeof(double) * 8;
+    w.bar = reinterpret_cast<unsigned int*>(p);
+    p += 16;
+    w.counter = reinterpret_cast<unsigned int*>(p);
+    p += 16;
+    w.partials = reinterpret_cast<double*>(p);
+    return w;
+}
+
+// S^0 = G (tridiagonal) or H (Hessenberg), row-major with ld = kmax
+__global__ void k_newton_init(const double2* alpha, const double2* beta, const double2* gamma, const double2* H,
+                              int ldH, int tri, KState* ks, NewtonWork w, int kmax) {
+    const int n = ks->kused;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ks->inner_done = (n == 0);
+        ks->inner_iters = 0;
+        ks->inner_method = 1;
+        ks->inner_err = 0.0;
+        w.scal[4] = 0.0;
+        w.bar[0] = 0u;
+        w.bar[1] = 0u;
+        *w.counter = 0u;
+    }
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), cI = (int)(e % n);
+        double2 v = make_double2(0.0, 0.0);
+        if (tri) {
+            if (r == cI) v = alpha[r];
+            else if (r == cI + 1) v = beta[cI];
+            else if (cI == r + 1) v = gamma[r];
+        } else if (r <= cI + 1) {
+            v = H[r + (size_t)cI * ldH];  // column-major Hessenberg; zero below the subdiagonal
+        }
+        w.S[(size_t)r * kmax + cI] = v;
+    }
+}
+
+// X = S, clear pivot slots
+__global__ void k_newton_prep(KState* ks, NewtonWork w, int kmax) {
+    if (ks->inner_done || ks->status || ks->timeout) return;
+    const int n = ks->kused;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), cI = (int)(e % n);
+        w.X[(size_t)r * kmax + cI] = w.S[(size_t)r * kmax + cI];
+    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n; e += gridDim.x * blockDim.x) {
+        w.slot[e] = 0ull;
+        if (e < n) w.invr[e] = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.scal[0] = 0.0;
+}
+
+__device__ __forceinline__ unsigned long long pivkey(double mag, int row) {
+    // non-negative float bits are monotone; ties prefer the smaller row
+    const float f = (float)mag;
+    return ((unsigned long long)__float_as_uint(f) << 32) | (unsigned long long)(0x7fffffff - row);
+}
+
+// In-place Gauss-Jordan inversion of X (n x n) with partial pivoting; rows are
+// owned cyclically by the CTAs; the pivot row chosen at step p is pivrow[p]
+// and invr[pivrow[p]] = p.  Inverse: S^-1[a][b] = X[pivrow[a]][invr[b]].
+// Data another CTA wrote during this kernel is read with L1-bypassing loads.
+__global__ void __launch_bounds__(256) k_gj_invert(KState* ks, NewtonWork w, int kmax) {
+    extern __shared__ double2 prow[];
+    __shared__ unsigned long long best;
+    if (ks->inner_done || ks->status || ks->timeout) return;
+    const int n = ks->kused;
+    const int G = gridDim.x;
+    const long long max_spins = 20000000;
+    int* err = &ks->timeout;
+    if (threadIdx.x == 0) {
+        best = 0ull;
+        for (int r = blockIdx.x; r < n; r += G) {
+            const double2 v = w.X[(size_t)r * kmax];
+            const unsigned long long k = pivkey(hypot(v.x, v.y), r);
+            if (k > best) best = k;
+        }
+        if (best) atomicMax(&w.slot[0], best);
+    }
+    grid_barrier(w.bar, err, 1, max_spins);
+    for (int p = 0; p < n; ++p) {
+        const unsigned long long key = __ldcg(&w.slot[p]);
+        if (key == 0ull) {  // no pivot candidate (cannot happen for p < n): report, never index
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ks->status, 5);
+            return;
+        }
+        const int r = 0x7fffffff - (int)(key & 0xffffffffull);
+        if (r < 0 || r >= n) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ks->status, 5);
+            return;
+        }
+        // phase A: the owner scales the pivot row in place
+        if (r % G == (int)blockIdx.x) {
+            const double2 pv = w.X[(size_t)r * kmax + p];
+            const cx<double> ip = cdiv(mk(1.0, 0.0), d2c(pv));
+            __syncthreads();
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                if (j == p) w.X[(size_t)r * kmax + j] = c2d(ip);
+                else w.X[(size_t)r * kmax + j] = c2d(ip * d2c(w.X[(size_t)r * kmax + j]));
+            }
+            if (threadIdx.x == 0) {
+                w.pivrow[p] = r;
+                w.invr[r] = p;
+                const double a = hypot(pv.x, pv.y);
+                if (a == 0.0) atomicExch(&ks->status, 5);
+                atomicAdd(&w.scal[0], log(a));
+            }
+        }
+        grid_barrier(w.bar, err, 1, max_spins);
+        if (*(volatile int*)err) return;  // a wait gave up: leave (the host reports OVL_ETIMEOUT)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(w.X + (size_t)r * kmax + j);
+        if (threadIdx.x == 0) best = 0ull;
+        __syncthreads();
+        const cx<double> pp = d2c(prow[p]);
+        for (int i = blockIdx.x; i < n; i += G) {
+            if (i == r) continue;
+            const cx<double> f = d2c(w.X[(size_t)i * kmax + p]);
+            const bool cand = (p + 1 < n) && (w.invr[i] < 0);  // own row: coherent
+            __syncthreads();  // every thread has read X[i][p] before it is overwritten
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                cx<double> x;
+                if (j == p) x = mk(0.0, 0.0) - f * pp;
+                else x = d2c(w.X[(size_t)i * kmax + j]) - f * d2c(prow[j]);
+                w.X[(size_t)i * kmax + j] = c2d(x);
+                if (j == p + 1 && cand) atomicMax(&best, pivkey(hypot(x.r, x.i), i));
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && best && p + 1 < n) atomicMax(&w.slot[p + 1], best);
+        grid_barrier(w.bar, err, 1, max_spins);
+        if (*(volatile int*)err) return;
+    }
+}
+
+// S <- (mu S + X'/mu)/2 with X' the unscrambled inverse; convergence bookkeeping.
+__global__ void k_newton_update(KState* ks, NewtonWork w, int kmax, int it) {
+    __shared__ double red[64];
+    if (ks->inner_done || ks->status || ks->timeout) return;
+    const int n = ks->kused;
+    // determinant scaling during the first iterates, unscaled near convergence
+    const bool scale = it < 8 && w.scal[4] == 0.0;
+    const double mu = scale ? exp(-w.scal[0] / n) : 1.0;
+    double part[2] = {0.0, 0.0};
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / n), b = (int)(e % n);
+        const cx<double> s = d2c(w.S[(size_t)a * kmax + b]);
+        const cx<double> xi = d2c(w.X[(size_t)w.pivrow[a] * kmax + w.invr[b]]);
+        const cx<double> ns = mk(0.5 * (mu * s.r + xi.r / mu), 0.5 * (mu * s.i + xi.i / mu));
+        w.S[(size_t)a * kmax + b] = c2d(ns);
+        const cx<double> d = ns - s;
+        part[0] += norm2(d);
+        part[1] += norm2(ns);
+    }
+    double out[2];
+    if (grid_sum_last<2>(part, w.partials, w.counter, out, red)) {
+        if (threadIdx.x == 0) {
+            ks->inner_iters = it + 1;
+            const double diff = sqrt(out[0]), nrm = sqrt(out[1]);
+            ks->inner_err = diff / fmax(nrm, 1e-300);
+            if (w.scal[4] != 0.0) {
+                ks->inner_done = 1;  // the extra unscaled step after convergence
+            } else if (diff <= 1e-7 * nrm) {
+                w.scal[4] = 1.0;
+            }
+        }
+    }
+}
+
+__global__ void k_newton_out(KState* ks, NewtonWork w, double2* c, int kmax, int max_it) {
+    const int n = ks->kused;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !ks->inner_done && !ks->status && n > 0) ks->status = 6;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 s = w.S[(size_t)i * kmax];
+        c[i] = make_double2(ks->nR * s.x, ks->nR * s.y);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ks->timeout) ks->status = 7;
+}
+
+int launch_inner_newton(const double2* alpha, const double2* beta, const double2* gamma, const double2* H, int ldH,
+                        int tri, KState* ks, double2* c, double2* work, size_t work_elems, int kmax, int num_sms,
+                        cudaStream_t st) {
+    if (inner_work_elems(kmax, 1) > work_elems) return -1;
+    NewtonWork w = newton_layout(work, kmax);
+    const int max_it = 40;
+    k_newton_init<<<num_sms, 256, 0, st>>>(alpha, beta, gamma, H, ldH, tri, ks, w, kmax);
+    const size_t smem = sizeof(double2) * kmax;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_gj_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    for (int it = 0; it < max_it; ++it) {
+        k_newton_prep<<<num_sms, 256, 0, st>>>(ks, w, kmax);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(num_sms);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_gj_invert, ks, w, kmax);
+        if (e != cudaSuccess) return (int)e;
+        k_newton_update<<<num_sms, 256, 0, st>>>(ks, w, kmax, it);
+    }
+    k_newton_out<<<(kmax + 255) / 256, 256, 0, st>>>(ks, w, c, kmax, max_it);
+    return 0;
+}
+
+}  // namespace ovl

@@ -1,0 +1,106 @@
+// Host-side launchers of the library's kernels (internal C++ interface between
+// the translation units; the public C ABI is include/ovl.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "ovl_common.cuh"
+
+namespace ovl {
+
+// Device-side scalar state of one Krylov solve.  Coefficients follow the
+// paper's notation (Sec. 4, Eq. 4.1-4.2): alpha on the diagonal of G_k, beta
+// below, gamma above.  Basis vectors are stored unnormalised (v~_i = v_i /
+// vscale[i]); consumers multiply by the recorded scales.
+struct KState {
+    int status;        // 0 = running/ok, else an ovl_status code
+    int done;          // 1 after a lucky breakdown or the last step
+    int kused;         // Krylov steps completed (size of G_k / H_k)
+    int bdstep;        // serious-breakdown step, -1 if none
+    int timeout;       // a bounded wait gave up
+    int inner_iters;
+    int inner_method;
+    int inner_done;    // the inner sign has converged (quadrature or Newton)
+    double anorm;      // running max |A v_i|, breakdown tolerance scale
+    double nR;         // |b_perp^R|
+    double inner_err;
+    double pad2;
+    double2 sv, sw;    // scale of the current v~, w~ (v = sv v~, w = sw w~)
+    double2 svp, swp;  // scale of the previous v~, w~
+    double2 red[8];    // scratch results of the last grid reduction
+};
+
+struct Workspace;   // defined in api.cu
+
+// ---- stencil.cu
+void launch_pack_gauge(const double2* U_canon, double2* U64, float4* U12, float2* U18, const Geom& g,
+                       cudaStream_t st);
+void launch_pack_spinor(const double2* canon, void* native, int prec, const Geom& g, cudaStream_t st);
+// out_canon = b_canon (if given) + (g5 ? gamma5 : 1) * native
+void launch_unpack_spinor(const void* native, int prec, double2* canon, const double2* b_canon, int g5,
+                          const Geom& g, cudaStream_t st);
+// y = [gamma5] D_w(mu) x  (single application), prec 0 = FP64, 1 = FP32-12, 2 = FP32-18;
+// skipped when ks is given and the solve is finished.
+void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, double kappa, int gamma5,
+                   const Geom& g, cudaStream_t st, const KState* ks = nullptr);
+// pair: t = sv * A v~, s = sw * A^dag w~, alpha[step] = w^dag t (fused grid reduction),
+// kused = step + 1, done after step klast.
+void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, void* t, void* s,
+                        double mu, double kappa, KState* ks, double2* alpha, int step, int klast,
+                        double* partials, unsigned int* counter, const Geom& g, cudaStream_t st);
+// FP64 regeneration step of the two-pass 2sL (Sec. 5): v_{i+1} = ((A - alpha_i) v_i - gamma_{i-1} v_{i-1})
+// / beta_i and y += c_{i+1} v_{i+1}, no reductions.
+void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim1, double2* vip1, double2* y,
+                         double mu, double kappa, const KState* ks, const double2* alpha, const double2* beta,
+                         const double2* gamma, const double2* c, int step, const Geom& g, cudaStream_t st);
+int dslash_grid(const Geom& g, int threads);
+
+// ---- krylov.cu
+void launch_state_init(KState* ks, cudaStream_t st);
+// 2sL recurrence of Sec. 4, Eq. 4.2 with fused reductions (w^^dag v^, |v^|^2, |w^|^2);
+// the last block sets beta[step], gamma[step], the scales and vscale[step+1].
+void launch_lanczos_step(int prec, const void* t, const void* s, const void* vi, const void* wi,
+                         const void* vim1, const void* wim1, void* vnext, void* wnext, KState* ks,
+                         const double2* alpha, double2* beta, double2* gamma, double2* vscale, int step, int kmax,
+                         double* partials, unsigned int* counter, size_t n, cudaStream_t st);
+// h[l] (+)= V_l^dag x for l < nvec (V_l = V + l*ld), deterministic two-stage reduction.
+int multidot_blocks(size_t n);
+void launch_multidot(const double2* V, size_t ld, int nvec, const double2* x, double2* h, int acc,
+                     double* partials, size_t n, cudaStream_t st, const KState* ks = nullptr, int step = -1);
+// x -= sum_l h[l] V_l
+void launch_multiaxpy(const double2* V, size_t ld, int nvec, const double2* h, double2* x, double* partials,
+                      unsigned int* counter, KState* ks, int norm_out, size_t n, cudaStream_t st, int step = -1);
+// second Gram-Schmidt update of Arnoldi step j, then H[0..j, j] = h1 + h2, H[j+1, j] = |x|,
+// kused = j + 1, done on a lucky breakdown or at j = jlast.
+void launch_arnoldi_orth2(const double2* V, size_t ld, int nvec, const double2* h2, double2* x, double2* H, int ldH,
+                          const double2* h1, int j, int jlast, double* partials, unsigned int* counter, KState* ks,
+                          size_t n, cudaStream_t st);
+void launch_arnoldi_normalize(double2* t, const KState* ks, size_t n, cudaStream_t st);
+// Deflation split (Sec. 3, Eq. 3.2-3.4; Sec. 4, Eq. 4.5): bR = b - R p, bL = b - L q (bL may be null),
+// y = R (sgn(lambda) p), with p = pq[0..m), q = pq[m..2m); sets nR = |bR|, sv = 1/nR, sw = 1/conj(bL^dag v_1).
+void launch_deflate_split(const double2* b, const double2* R, const double2* L, const double2* lam, int m,
+                          const double2* pq, double2* bR, double2* bL, double2* y, KState* ks, double2* vscale,
+                          double* partials, unsigned int* counter, size_t n, cudaStream_t st);
+void launch_convert_f64_f32(const double2* x, float2* y, size_t n, cudaStream_t st);
+// v = sv * x; if y: y += c[0] * v
+void launch_scale_start(const double2* x, double2* v, double2* y, const double2* c, const KState* ks, size_t n,
+                        cudaStream_t st);
+// y += sum_{l < kused} c_l vscale_l V_l
+void launch_combine(const double2* V, size_t ld, const double2* vscale, const double2* c, const KState* ks,
+                    int kmax, double2* y, size_t n, cudaStream_t st);
+
+// ---- inner_sign.cu
+// c[0..n) = nR * sgn(G) e_1 for the tridiagonal G (alpha, beta, gamma) of size ks->kused, by the
+// resolvent quadrature sgn(G) = (2/pi) int_0^inf G (G^2 + t^2)^-1 dt (see inner_sign.cu).
+int launch_inner_quadrature(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,
+                            double2* c, double2* work, size_t work_elems, int kmax, double* partials,
+                            unsigned int* counter, cudaStream_t st);
+// c = nR * sgn(M) e_1 by Roberts' iteration (Sec. 2) with determinant scaling, M dense n x n
+// (n = ks->kused) built from the tridiagonal (tri = 1) or taken as the Hessenberg H (ld = ldH).
+int launch_inner_newton(const double2* alpha, const double2* beta, const double2* gamma, const double2* H,
+                        int ldH, int tri, KState* ks, double2* c, double2* work, size_t work_elems, int kmax,
+                        int num_sms, cudaStream_t st);
+size_t inner_work_elems(int kmax, int method);
+
+}  // namespace ovl

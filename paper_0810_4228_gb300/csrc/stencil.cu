@@ -1,0 +1,349 @@
+// Wilson stencil kernels: A = gamma5 D_w(mu) and A^dag = gamma5 D_w(-mu)
+// (Sec. 1, Eq. 1.1-1.2; the adjoint enters the two-sided Lanczos recurrence of
+// Sec. 4, Eq. 4.2), plus the layout conversions at the library boundary.
+//
+// One thread per lattice site.  A block covers a range of checkerboard
+// indices for both parities (first half of the block parity 0, second half
+// parity 1), so neighbouring sites -- which have the opposite parity -- are
+// processed by the same block and their links/spinors are re-read from L1/L2.
+// Spinors are stored [component-chunk][site] with 16-byte chunks (double2 for
+// FP64, float4 = two complex for FP32): every load of a warp is one 512-byte
+// coalesced transaction.  Links are stored [nu][element][site]; the FP32 12-real
+// format keeps rows 0 and 1 and rebuilds row 2 = conj(row0 x row1) in registers.
+// The e^{+-mu} factors, kappa and the antiperiodic time phase are applied as
+// real scalars to the projected half spinor, so links stay in SU(3).
+#include "ovl_kernels.h"
+
+namespace ovl {
+
+template <class R> struct VecT;
+template <> struct VecT<double> { using T = double2; };
+template <> struct VecT<float> { using T = float4; };
+
+template <int LF> struct LinkReal { using R = float; };
+template <> struct LinkReal<LINK_F64> { using R = double; };
+
+template <int LF, class R>
+__device__ __forceinline__ void load_link_any(const void* U, int V, int nu, int i, Link<R>& L) {
+    if constexpr (LF == LINK_F64) load_link((const double2*)U, V, nu, i, L);
+    else if constexpr (LF == LINK_F32_12) load_link12((const float4*)U, V, nu, i, L);
+    else load_link18((const float2*)U, V, nu, i, L);
+}
+
+// Hop coefficients of one input: -kappa * (e^{+-mu} for time) for the forward
+// (T^+) and backward (T^-) hop of each direction.
+template <class R> struct HopCoef { R f[4], b[4]; };
+
+template <class R> __host__ HopCoef<R> make_coef(double mu, double kappa) {
+    HopCoef<R> h;
+    for (int nu = 0; nu < 3; ++nu) h.f[nu] = h.b[nu] = R(-kappa);
+    h.f[3] = R(-kappa * exp(mu));
+    h.b[3] = R(-kappa * exp(-mu));
+    return h;
+}
+
+// Accumulate the eight hops of direction NU for NIN inputs sharing the links.
+template <int NU, int LF, class R, int NIN>
+__device__ __forceinline__ void hops_dir(const Geom& g, const Coord& c, int i, const void* U,
+                                         const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                         const HopCoef<R> (&hc)[NIN]) {
+    Link<R> L;
+    Spinor<R> p;
+    Half<R> h, uh;
+    // forward: (1 + gamma_nu) U_{x,nu} psi(x + nu)
+    {
+        const int f = neighbour(g, c, NU, +1);
+        const R ph = (NU == 3 && c.x[3] == g.L[3] - 1) ? R(g.bc_t) : R(1);
+        load_link_any<LF>(U, g.V, NU, i, L);
+#pragma unroll
+        for (int n = 0; n < NIN; ++n) {
+            load_spinor(x[n], g.V, f, p);
+            project<NU, +1>(p, h);
+            mul_link(L, h, uh);
+            recon_acc<NU, +1>(acc[n], uh, hc[n].f[NU] * ph);
+        }
+    }
+    // backward: (1 - gamma_nu) U_{x-nu,nu}^dag psi(x - nu)
+    {
+        const int b = neighbour(g, c, NU, -1);
+        const R ph = (NU == 3 && c.x[3] == 0) ? R(g.bc_t) : R(1);
+        load_link_any<LF>(U, g.V, NU, b, L);
+#pragma unroll
+        for (int n = 0; n < NIN; ++n) {
+            load_spinor(x[n], g.V, b, p);
+            project<NU, -1>(p, h);
+            mul_link_dag(L, h, uh);
+            recon_acc<NU, -1>(acc[n], uh, hc[n].b[NU] * ph);
+        }
+    }
+}
+
+template <int LF, class R, int NIN>
+__device__ __forceinline__ void apply_site(const Geom& g, int i, const void* U,
+                                           const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                           const HopCoef<R> (&hc)[NIN]) {
+    const Coord c = site_coord(g, i);
+#pragma unroll
+    for (int n = 0; n < NIN; ++n)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[n].s[s][a] = mk(R(0), R(0));
+    hops_dir<0, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<1, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<2, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<3, LF, R, NIN>(g, c, i, U, x, acc, hc);
+}
+
+// add the diagonal term and apply gamma5 = diag(1, 1, -1, -1)
+template <class R>
+__device__ __forceinline__ void finish_site(Spinor<R>& acc, const Spinor<R>& self, bool g5) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<R> z = acc.s[s][a] + self.s[s][a];
+            acc.s[s][a] = (g5 && s >= 2) ? -z : z;
+        }
+}
+
+__device__ __forceinline__ int site_of_thread(const Geom& g) {
+    const int half = blockDim.x >> 1;
+    const int par = threadIdx.x >= half;
+    const int cb = blockIdx.x * half + (threadIdx.x - par * half);
+    return cb < g.Vh ? par * g.Vh + cb : -1;
+}
+
+int dslash_grid(const Geom& g, int threads) { return (g.Vh + threads / 2 - 1) / (threads / 2); }
+
+// ------------------------------------------------------------ single apply --
+template <int LF>
+__global__ void __launch_bounds__(256) k_dslash(const void* __restrict__ U,
+                                                const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ x,
+                                                typename VecT<typename LinkReal<LF>::R>::T* __restrict__ y,
+                                                HopCoef<typename LinkReal<LF>::R> hc, int g5, const KState* ks,
+                                                Geom g) {
+    using R = typename LinkReal<LF>::R;
+    if (ks && (ks->done || ks->status)) return;
+    const int i = site_of_thread(g);
+    if (i < 0) return;
+    const typename VecT<R>::T* const xs[1] = {x};
+    Spinor<R> acc[1];
+    const HopCoef<R> hcs[1] = {hc};
+    apply_site<LF, R, 1>(g, i, U, xs, acc, hcs);
+    Spinor<R> self;
+    load_spinor(x, g.V, i, self);
+    finish_site(acc[0], self, g5 != 0);
+    store_spinor(y, g.V, i, acc[0]);
+}
+
+void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, double kappa, int gamma5,
+                   const Geom& g, cudaStream_t st, const KState* ks) {
+    const int T = 256, B = dslash_grid(g, T);
+    if (prec == 0)
+        k_dslash<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)x, (double2*)y, make_coef<double>(mu, kappa),
+                                            gamma5, ks, g);
+    else if (prec == 1)
+        k_dslash<LINK_F32_12><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
+                                               gamma5, ks, g);
+    else
+        k_dslash<LINK_F32_18><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
+                                               gamma5, ks, g);
+}
+
+// -------------------------------------------------------------- pair apply --
+// t = sv * gamma5 D_w(mu) v~,  s = sw * gamma5 D_w(-mu) w~,  alpha[step] = w^dag t
+// with w = sw w~.  Skipped (uniformly) once the solve is done or failed.
+template <int LF>
+__global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
+                                                     const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ v,
+                                                     const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ w,
+                                                     typename VecT<typename LinkReal<LF>::R>::T* __restrict__ t,
+                                                     typename VecT<typename LinkReal<LF>::R>::T* __restrict__ s,
+                                                     HopCoef<typename LinkReal<LF>::R> hv,
+                                                     HopCoef<typename LinkReal<LF>::R> hw, KState* ks,
+                                                     double2* alpha, int step, int klast, double* partials,
+                                                     unsigned int* counter, Geom g) {
+    using R = typename LinkReal<LF>::R;
+    __shared__ double red[64];
+    if (ks->done || ks->status) return;
+    const double2 sv = ks->sv, sw = ks->sw;
+    const int i = site_of_thread(g);
+    double part[3] = {0.0, 0.0, 0.0};
+    if (i >= 0) {
+        const typename VecT<R>::T* const xs[2] = {v, w};
+        Spinor<R> acc[2];
+        const HopCoef<R> hcs[2] = {hv, hw};
+        apply_site<LF, R, 2>(g, i, U, xs, acc, hcs);
+        Spinor<R> self;
+        load_spinor(v, g.V, i, self);
+        finish_site(acc[0], self, true);
+        load_spinor(w, g.V, i, self);
+        finish_site(acc[1], self, true);
+        // scale by the (complex) normalisation of v~, w~
+        const cx<R> csv = mk(R(sv.x), R(sv.y)), csw = mk(R(sw.x), R(sw.y));
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                acc[0].s[sp][a] = csv * acc[0].s[sp][a];
+                acc[1].s[sp][a] = csw * acc[1].s[sp][a];
+                // w~^dag t in FP64
+                cx<double> z = cdot(up(self.s[sp][a]), up(acc[0].s[sp][a]));
+                part[0] += z.r;
+                part[1] += z.i;
+                part[2] += norm2(up(acc[0].s[sp][a]));
+            }
+        store_spinor(t, g.V, i, acc[0]);
+        store_spinor(s, g.V, i, acc[1]);
+    }
+    double out[3];
+    if (grid_sum_last<3>(part, partials, counter, out, red)) {
+        if (threadIdx.x == 0) {
+            // alpha = w^dag t = conj(sw) * (w~^dag t)
+            cx<double> a = cdot(d2c(sw), mk(out[0], out[1]));
+            alpha[step] = c2d(a);
+            const double tn = sqrt(out[2]);
+            if (tn > ks->anorm) ks->anorm = tn;
+            ks->kused = step + 1;
+            if (step == klast) ks->done = 1;
+        }
+    }
+}
+
+void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, void* t, void* s, double mu,
+                        double kappa, KState* ks, double2* alpha, int step, int klast, double* partials,
+                        unsigned int* counter, const Geom& g, cudaStream_t st) {
+    const int T = 256, B = dslash_grid(g, T);
+    if (prec == 0)
+        k_dslash_pair<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s,
+                                                 make_coef<double>(mu, kappa), make_coef<double>(-mu, kappa), ks,
+                                                 alpha, step, klast, partials, counter, g);
+    else
+        k_dslash_pair<LINK_F32_12><<<B, T, 0, st>>>(U, (const float4*)v, (const float4*)w, (float4*)t, (float4*)s,
+                                                    make_coef<float>(mu, kappa), make_coef<float>(-mu, kappa), ks,
+                                                    alpha, step, klast, partials, counter, g);
+}
+
+// ------------------------------------------------------ two-pass regeneration --
+// v_{i+1} = ((A - alpha_i) v_i - gamma_{i-1} v_{i-1}) / beta_i ;  y += c_{i+1} v_{i+1}
+__global__ void __launch_bounds__(256) k_dslash_regen(const double2* __restrict__ U, const double2* __restrict__ vi,
+                                                      const double2* __restrict__ vim1, double2* __restrict__ vip1,
+                                                      double2* __restrict__ y, HopCoef<double> hc, const KState* ks,
+                                                      const double2* __restrict__ alpha,
+                                                      const double2* __restrict__ beta,
+                                                      const double2* __restrict__ gamma,
+                                                      const double2* __restrict__ c, int step, Geom g) {
+    if (ks->status || step + 1 >= ks->kused) return;
+    const int i = site_of_thread(g);
+    if (i < 0) return;
+    const double2* const xs[1] = {vi};
+    Spinor<double> acc[1];
+    const HopCoef<double> hcs[1] = {hc};
+    apply_site<LINK_F64, double, 1>(g, i, U, xs, acc, hcs);
+    Spinor<double> self;
+    load_spinor(vi, g.V, i, self);
+    finish_site(acc[0], self, true);
+    const cx<double> a = d2c(alpha[step]);
+    const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(beta[step]));
+    const cx<double> gm = step > 0 ? d2c(gamma[step - 1]) : mk(0.0, 0.0);
+    const cx<double> cc = d2c(c[step + 1]);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const size_t e = (size_t)(3 * sp + q) * g.V + i;
+            cx<double> z = acc[0].s[sp][q] - a * self.s[sp][q];
+            if (step > 0) z = z - gm * d2c(vim1[e]);
+            z = ib * z;
+            vip1[e] = c2d(z);
+            cx<double> yy = d2c(y[e]);
+            cfma(yy, cc, z);
+            y[e] = c2d(yy);
+        }
+}
+
+void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim1, double2* vip1, double2* y,
+                         double mu, double kappa, const KState* ks, const double2* alpha, const double2* beta,
+                         const double2* gamma, const double2* c, int step, const Geom& g, cudaStream_t st) {
+    const int T = 256, B = dslash_grid(g, T);
+    k_dslash_regen<<<B, T, 0, st>>>(U, vi, vim1, vip1, y, make_coef<double>(mu, kappa), ks, alpha, beta, gamma, c,
+                                    step, g);
+}
+
+// ---------------------------------------------------------------- layouts --
+__global__ void k_pack_gauge(const double2* __restrict__ Uc, double2* __restrict__ U64, float4* __restrict__ U12,
+                             float2* __restrict__ U18, Geom g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const Coord c = site_coord(g, i);
+    const int s = canon_index(g, c.x);
+    for (int nu = 0; nu < 4; ++nu) {
+        double2 e[9];
+        for (int q = 0; q < 9; ++q) e[q] = Uc[((size_t)s * 4 + nu) * 9 + q];
+        for (int q = 0; q < 9; ++q) {
+            U64[((size_t)nu * 9 + q) * g.V + i] = e[q];
+            U18[((size_t)nu * 9 + q) * g.V + i] = make_float2((float)e[q].x, (float)e[q].y);
+        }
+        U12[((size_t)nu * 3 + 0) * g.V + i] = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
+        U12[((size_t)nu * 3 + 1) * g.V + i] = make_float4(e[2].x, e[2].y, e[3].x, e[3].y);
+        U12[((size_t)nu * 3 + 2) * g.V + i] = make_float4(e[4].x, e[4].y, e[5].x, e[5].y);
+    }
+}
+
+void launch_pack_gauge(const double2* U_canon, double2* U64, float4* U12, float2* U18, const Geom& g,
+                       cudaStream_t st) {
+    k_pack_gauge<<<(g.V + 127) / 128, 128, 0, st>>>(U_canon, U64, U12, U18, g);
+}
+
+__global__ void k_pack_spinor(const double2* __restrict__ canon, void* __restrict__ native, int prec, Geom g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const Coord c = site_coord(g, i);
+    const int s = canon_index(g, c.x);
+    if (prec == 0) {
+        double2* o = (double2*)native;
+        for (int q = 0; q < 12; ++q) o[(size_t)q * g.V + i] = canon[(size_t)s * 12 + q];
+    } else {
+        float4* o = (float4*)native;
+        for (int q = 0; q < 6; ++q) {
+            double2 a = canon[(size_t)s * 12 + 2 * q], b = canon[(size_t)s * 12 + 2 * q + 1];
+            o[(size_t)q * g.V + i] = make_float4(a.x, a.y, b.x, b.y);
+        }
+    }
+}
+
+void launch_pack_spinor(const double2* canon, void* native, int prec, const Geom& g, cudaStream_t st) {
+    k_pack_spinor<<<(g.V + 127) / 128, 128, 0, st>>>(canon, native, prec, g);
+}
+
+__global__ void k_unpack_spinor(const void* __restrict__ native, int prec, double2* __restrict__ canon,
+                                const double2* __restrict__ b, int g5, Geom g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const Coord c = site_coord(g, i);
+    const int s = canon_index(g, c.x);
+    for (int q = 0; q < 12; ++q) {
+        double2 v;
+        if (prec == 0) {
+            v = ((const double2*)native)[(size_t)q * g.V + i];
+        } else {
+            float4 f = ((const float4*)native)[(size_t)(q / 2) * g.V + i];
+            v = (q & 1) ? make_double2(f.z, f.w) : make_double2(f.x, f.y);
+        }
+        if (g5 && q >= 6) v = make_double2(-v.x, -v.y);
+        if (b) {
+            double2 bb = b[(size_t)s * 12 + q];
+            v.x += bb.x;
+            v.y += bb.y;
+        }
+        canon[(size_t)s * 12 + q] = v;
+    }
+}
+
+void launch_unpack_spinor(const void* native, int prec, double2* canon, const double2* b_canon, int g5,
+                          const Geom& g, cudaStream_t st) {
+    k_unpack_spinor<<<(g.V + 127) / 128, 128, 0, st>>>(native, prec, canon, b_canon, g5, g);
+}
+
+}  // namespace ovl

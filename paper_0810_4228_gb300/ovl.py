@@ -1,0 +1,243 @@
+"""Python binding of the C ABI in include/ovl.h (argument marshalling only).
+
+Every computation runs in libovl.so's CUDA kernels; this module passes
+torch device pointers, sizes and the current CUDA stream.  It raises if the
+library is missing: there is no CPU fallback.
+
+Names follow the C functions: ``Context.apply_Dw``, ``Context.apply_pair``,
+``Context.set_deflation``, ``Context.sign_krylov``.  Tensors are complex128
+in the canonical layout [V, 4, 3] (spinors) and [V, 4, 3, 3] (links) unless a
+``native=True`` argument says otherwise; see include/ovl.h for the layout and
+the physics conventions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libovl.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ESINGULAR, ENOCONV, ETIMEOUT, ESTATE = range(9)
+ARNOLDI, LANCZOS2 = 0, 1
+GAMMA5, DAGGER, NATIVE, HOST, F32, F32_FULL = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+OVERLAP, MIXED, TWO_PASS, INNER_NEWTON, NO_GRAPH, PROFILE = 0x100, 0x200, 0x400, 0x1000, 0x2000, 0x4000
+
+_ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EBREAKDOWN",
+             ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
+
+EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
+           "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_pack", "ovl_unpack",
+           "ovl_set_deflation", "ovl_sign_krylov", "ovl_profile_get", "ovl_profile_reset"]
+
+
+class OvlError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int), ("kernels", ctypes.c_longlong),
+                ("ms", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("k_used", ctypes.c_int), ("breakdown_step", ctypes.c_int),
+                ("inner_iters", ctypes.c_int), ("inner_method", ctypes.c_int),
+                ("bperp_norm", ctypes.c_double), ("inner_err", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libovl.so (once).  Raises ImportError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_0810_4228_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "ovl_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), I, P]),
+        "ovl_destroy": (I, [P]),
+        "ovl_last_error": (ctypes.c_char_p, [P]),
+        "ovl_set_stream": (I, [P, P]),
+        "ovl_vector_bytes": (ctypes.c_size_t, [P, I]),
+        "ovl_set_gauge": (I, [P, P, I]),
+        "ovl_apply_Dw": (I, [P, D, D, P, P, I]),
+        "ovl_apply_pair": (I, [P, D, D, I, P, P, P, P, ctypes.POINTER(D)]),
+        "ovl_pack": (I, [P, P, P, I]),
+        "ovl_unpack": (I, [P, P, P, I]),
+        "ovl_set_deflation": (I, [P, D, D, I, ctypes.POINTER(D), P, P, I]),
+        "ovl_sign_krylov": (I, [P, I, I, D, D, P, P, I, ctypes.POINTER(Info)]),
+        "ovl_profile_get": (I, [P, ctypes.POINTER(KStat), I, ctypes.POINTER(I)]),
+        "ovl_profile_reset": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int:
+    import torch
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if not t.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _is_host(t) -> bool:
+    import torch
+    return isinstance(t, np.ndarray) or (isinstance(t, torch.Tensor) and not t.is_cuda)
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+@dataclass
+class Lattice:
+    dims: tuple
+    bc_t: int = -1
+
+    @property
+    def volume(self) -> int:
+        L = self.dims
+        return L[0] * L[1] * L[2] * L[3]
+
+
+class Context:
+    """One lattice (and gauge field) on the current CUDA device."""
+
+    def __init__(self, dims, bc_t: int = -1, stream=None):
+        self._lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.bc_t = int(bc_t)
+        self.V = int(np.prod(self.dims))
+        self.n = 12 * self.V
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        self._stream = stream
+        r = self._lib.ovl_create(ctypes.byref(h), arr, self.bc_t, _stream_handle(stream))
+        if r:
+            raise OvlError(r, f"ovl_create failed for dims={self.dims}, bc_t={bc_t}")
+        self._h = h
+
+    # -- helpers
+    def _check(self, r):
+        if r:
+            raise OvlError(r, self._lib.ovl_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ovl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        self._check(self._lib.ovl_set_stream(self._h, _stream_handle(stream)))
+
+    def vector_bytes(self, prec: int = 0) -> int:
+        return int(self._lib.ovl_vector_bytes(self._h, prec))
+
+    def empty_native(self, prec: int = 0):
+        import torch
+        return torch.empty(self.n, dtype=torch.complex128 if prec == 0 else torch.complex64, device="cuda")
+
+    # -- C ABI
+    def set_gauge(self, U):
+        flags = HOST if _is_host(U) else 0
+        self._check(self._lib.ovl_set_gauge(self._h, _ptr(U), flags))
+
+    def pack(self, canon, native, prec: int = 0):
+        self._check(self._lib.ovl_pack(self._h, _ptr(canon), _ptr(native), prec))
+
+    def unpack(self, native, canon, prec: int = 0):
+        self._check(self._lib.ovl_unpack(self._h, _ptr(native), _ptr(canon), prec))
+
+    def apply_Dw(self, mu: float, kappa: float, x, y=None, flags: int = GAMMA5):
+        """y = D_w(mu) x, gamma5 D_w(mu) x (GAMMA5, default) or A^dag x (DAGGER)."""
+        import torch
+        if y is None:
+            if _is_host(x):
+                y = np.empty_like(x) if isinstance(x, np.ndarray) else torch.empty_like(x)
+            else:
+                y = torch.empty_like(x)
+        if _is_host(x):
+            flags |= HOST
+        self._check(self._lib.ovl_apply_Dw(self._h, mu, kappa, _ptr(x), _ptr(y), flags))
+        return y
+
+    def apply_pair(self, mu: float, kappa: float, v, w, t, s, prec: int = 0):
+        """t = A v, s = A^dag w on device-layout vectors; returns alpha = w^dag t."""
+        a = (ctypes.c_double * 2)()
+        self._check(self._lib.ovl_apply_pair(self._h, mu, kappa, prec, _ptr(v), _ptr(w), _ptr(t), _ptr(s), a))
+        return complex(a[0], a[1])
+
+    def set_deflation(self, mu: float, kappa: float, lam, R, L):
+        """Install m critical eigenpairs: lam (m,) complex, R and L (m, 12V) complex128."""
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128))
+        m = int(lam.shape[0])
+        if m == 0:
+            self._check(self._lib.ovl_set_deflation(self._h, mu, kappa, 0, None, None, None, 0))
+            return
+        lam_d = np.ascontiguousarray(np.stack([lam.real, lam.imag], axis=1).ravel())
+        flags = HOST if _is_host(R) else 0
+        self._keep = (R, L)
+        self._check(self._lib.ovl_set_deflation(
+            self._h, mu, kappa, m, lam_d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            _ptr(R), _ptr(L), flags))
+
+    def profile(self, reset: bool = True):
+        """Per-kernel-class totals of the OVL_PROFILE solves since the last reset."""
+        arr = (KStat * 32)()
+        cnt = ctypes.c_int()
+        self._check(self._lib.ovl_profile_get(self._h, arr, 32, ctypes.byref(cnt)))
+        out = {arr[i].name.decode(): {"launches": arr[i].launches, "kernels": int(arr[i].kernels),
+                                      "ms": arr[i].ms} for i in range(min(cnt.value, 32))}
+        if reset:
+            self._check(self._lib.ovl_profile_reset(self._h))
+        return out
+
+    def sign_krylov(self, method: int, k: int, mu: float, kappa: float, b, out=None, flags: int = 0):
+        """out = sgn(gamma5 D_w(mu)) b, or D_ov(mu) b with flags |= OVERLAP.
+        Returns (out, info dict).  b may be a CUDA tensor or host memory."""
+        import torch
+        if out is None:
+            out = (np.empty_like(b) if isinstance(b, np.ndarray) else torch.empty_like(b))
+        if _is_host(b) != _is_host(out):
+            raise ValueError("b and out must both be host or both be device memory")
+        if _is_host(b):
+            flags |= HOST
+        info = Info()
+        r = self._lib.ovl_sign_krylov(self._h, method, int(k), mu, kappa, _ptr(b), _ptr(out), flags,
+                                      ctypes.byref(info))
+        if r and r != EBREAKDOWN:
+            self._check(r)
+        d = info.as_dict()
+        d["status"] = r
+        return out, d

@@ -128,3 +128,24 @@ def gauge_transformation(dims, seed: int, eps: float = 3.0) -> np.ndarray:
     V = volume(dims)
     rng = np.random.default_rng(seed)
     return random_su3(V, float(eps), rng)
+
+
+def gauge_field_torch(dims, eps: float, seed: int, device="cuda"):
+    """Seeded SU(3) field of the same recipe drawn with torch on ``device``
+    (for lattices too large to draw on the host).  Canonical layout
+    [V, 4, 3, 3] complex128.  Not bit-identical to ``gauge_field``."""
+    import torch
+
+    V = volume(dims)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lam = torch.from_numpy(gell_mann()).to(device)
+    out = torch.empty((V, 4, 3, 3), dtype=torch.complex128, device=device)
+    chunk = 1 << 20
+    flat = out.view(V * 4, 3, 3)
+    for s in range(0, V * 4, chunk):
+        e = min(V * 4, s + chunk)
+        h = torch.randn((e - s, 8), generator=g, device=device, dtype=torch.float64)
+        H = torch.einsum("na,aij->nij", h.to(torch.complex128), lam) * 0.5
+        flat[s:e] = torch.linalg.matrix_exp(1j * eps * H)
+    return out

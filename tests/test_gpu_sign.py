@@ -1,0 +1,224 @@
+"""GPU parity of sgn(A) b and D_ov(mu) b (Secs. 1-5) through the C ABI against
+the FP64 oracle: the dense spectral sign on 4^4 (N = 3072), the oracle's own
+Krylov runs of the same algorithm, LR deflation with the oracle's exact
+eigenpairs, the mixed-precision two-pass form, closed forms on free and
+gauge-transformed free fields at 8^4, and the degenerate cases."""
+import numpy as np
+import pytest
+
+from gpu_common import KAPPA, config4, rel, torch_c128
+from oracle import deflation as Dm
+from oracle import freefield as F
+from oracle import krylov as K
+from oracle import wilson as W
+from paper_0810_4228_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ovl():
+    from paper_0810_4228_gb300 import ovl as O
+    O.load()
+    return O
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return config4()
+
+
+def _ctx(ovl, dims, U):
+    ctx = ovl.Context(dims)
+    ctx.set_gauge(torch_c128(U))
+    return ctx
+
+
+def _solve(ovl, ctx, method, k, mu, b, flags=0):
+    out, info = ctx.sign_krylov(method, k, mu, KAPPA, torch_c128(b), flags=flags)
+    return out.cpu().numpy(), info
+
+
+def test_lanczos2_fp64_matches_dense(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 400, c4["mu"], c4["b"])
+    assert info["status"] == 0 and info["k_used"] == 400
+    assert rel(y, c4["ref"]) < 1e-10
+
+
+def test_arnoldi_fp64_matches_dense(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, info = _solve(ovl, ctx, ovl.ARNOLDI, 300, c4["mu"], c4["b"])
+    assert info["status"] == 0
+    assert rel(y, c4["ref"]) < 1e-10
+
+
+@pytest.mark.parametrize("method", ["arnoldi", "lanczos2"])
+@pytest.mark.parametrize("k", [1, 2, 7, 60])
+def test_same_algorithm_parity(ovl, c4, method, k):
+    """At equal k the GPU and the oracle run the same algorithm; before the
+    two-sided Lanczos loses bi-orthogonality their results agree far below the
+    approximation error itself."""
+    A = c4["A"]
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    if method == "arnoldi":
+        yo = K.sign_arnoldi(A.dot, c4["b"], k)
+        y, _ = _solve(ovl, ctx, ovl.ARNOLDI, k, c4["mu"], c4["b"])
+    else:
+        Ad = A.conj().T.tocsr()
+        yo = K.sign_lanczos2(A.dot, Ad.dot, c4["b"], k)
+        y, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, c4["mu"], c4["b"])
+    assert rel(y, yo) < 1e-9
+
+
+@pytest.mark.parametrize("k", [150, 200, 250])
+def test_lanczos2_error_matches_oracle_error(ovl, c4, k):
+    """Past the loss of bi-orthogonality the recurrence amplifies rounding (a
+    1e-15 change of b moves the oracle's own k = 200 result by ~6e-8), so the
+    comparison is of the distance to the dense sgn(A) b, which both runs share."""
+    A = c4["A"]
+    yo = K.sign_lanczos2(A.dot, A.conj().T.tocsr().dot, c4["b"], k)
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, c4["mu"], c4["b"])
+    eo, eg = rel(yo, c4["ref"]), rel(y, c4["ref"])
+    assert eg <= 3 * eo + 1e-12 and eo <= 3 * eg + 1e-12, (eg, eo)
+
+
+def test_overlap_output(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, _ = _solve(ovl, ctx, ovl.LANCZOS2, 400, c4["mu"], c4["b"], flags=ovl.OVERLAP)
+    g5 = np.tile(np.repeat([1.0, 1, -1, -1], 3), 256)
+    ref = c4["b"] + g5 * c4["ref"]
+    assert rel(y, ref) < 1e-10
+
+
+@pytest.mark.parametrize("method", ["arnoldi", "lanczos2"])
+def test_deflated_matches_dense(ovl, c4, method):
+    """m = 20 exact eigenpairs of smallest |Re lambda| (Sec. 3, Eq. 3.4; Sec. 4, Eq. 4.5)."""
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:20]
+    R = np.ascontiguousarray(X[:, idx].T)
+    L = np.ascontiguousarray(Xi[idx, :].conj())
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(R), torch_c128(L))
+    m = ovl.ARNOLDI if method == "arnoldi" else ovl.LANCZOS2
+    y, info = _solve(ovl, ctx, m, 300, c4["mu"], c4["b"])
+    assert info["status"] == 0
+    assert rel(y, c4["ref"]) < 1e-10
+    # same algorithm at small k
+    defl = Dm.Deflation(lam=lam[idx], R=X[:, idx], L=Xi[idx, :].conj().T)
+    A = c4["A"]
+    if method == "arnoldi":
+        yo = K.sign_arnoldi(A.dot, c4["b"], 40, defl)
+    else:
+        yo = K.sign_lanczos2(A.dot, A.conj().T.tocsr().dot, c4["b"], 40, defl)
+    y40, _ = _solve(ovl, ctx, m, 40, c4["mu"], c4["b"])
+    assert rel(y40, yo) < 1e-9
+
+
+def test_deflation_biorthonormalises(ovl, c4):
+    """L is rescaled internally so that L^dag R = I: scaling the given left
+    vectors must not change the result."""
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:8]
+    R = np.ascontiguousarray(X[:, idx].T)
+    L = np.ascontiguousarray(Xi[idx, :].conj()) * (1.7 - 0.4j)
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(R), torch_c128(L))
+    y, _ = _solve(ovl, ctx, ovl.LANCZOS2, 400, c4["mu"], c4["b"])
+    assert rel(y, c4["ref"]) < 1e-10
+
+
+def test_fully_deflated_source(ovl, c4):
+    """b an eigenvector in the deflated set: b_perp = 0 and sgn(A) b is exact."""
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:4]
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(X[:, idx].T.copy()), torch_c128(Xi[idx, :].conj().copy()))
+    b = X[:, idx[1]].copy()
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 10, c4["mu"], b)
+    assert info["k_used"] == 0 and info["bperp_norm"] < 1e-12
+    assert rel(y, np.sign(lam[idx[1]].real) * b) < 1e-12
+
+
+def test_zero_source(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 10, c4["mu"], np.zeros_like(c4["b"]))
+    assert np.abs(y).max() == 0.0
+
+
+@pytest.mark.parametrize("flags,tol", [("TWO_PASS", 1e-10), ("MIXED", 1e-8)])
+def test_two_pass(ovl, c4, flags, tol):
+    """Two-pass 2sL (Sec. 5): FP64 or FP32 pass 1 for the coefficients, FP64
+    regeneration of the basis in pass 2."""
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 400, c4["mu"], c4["b"], flags=getattr(ovl, flags))
+    assert info["status"] == 0
+    assert rel(y, c4["ref"]) < tol
+
+
+def test_inner_newton_equals_quadrature(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y1, i1 = _solve(ovl, ctx, ovl.LANCZOS2, 250, c4["mu"], c4["b"])
+    y2, i2 = _solve(ovl, ctx, ovl.LANCZOS2, 250, c4["mu"], c4["b"], flags=ovl.INNER_NEWTON)
+    assert i1["inner_method"] == 0 and i2["inner_method"] == 1
+    assert rel(y1, y2) < 1e-11
+
+
+def test_host_buffers_and_no_graph(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y1, _ = ctx.sign_krylov(ovl.LANCZOS2, 120, c4["mu"], KAPPA, np.ascontiguousarray(c4["b"]))
+    y2, _ = _solve(ovl, ctx, ovl.LANCZOS2, 120, c4["mu"], c4["b"], flags=ovl.NO_GRAPH)
+    assert isinstance(y1, np.ndarray)
+    assert rel(y1, y2) < 1e-14
+
+
+def test_repeat_is_deterministic(ovl, c4):
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y1, _ = _solve(ovl, ctx, ovl.LANCZOS2, 150, c4["mu"], c4["b"], flags=ovl.MIXED)
+    y2, _ = _solve(ovl, ctx, ovl.LANCZOS2, 150, c4["mu"], c4["b"], flags=ovl.MIXED)
+    assert np.array_equal(y1, y2)
+
+
+@pytest.mark.parametrize("gauge", [False, True])
+def test_free_field_8x4_closed_form(ovl, gauge):
+    """8^4, U = 1 or a random gauge transform of it: D_ov b from the momentum-
+    space closed form (FFT), at a volume the dense oracle cannot reach."""
+    dims, mu = (8, 8, 8, 8), 0.3
+    V = 4096
+    b = synth.gaussian_source(dims, 31)
+    ref = F.overlap_free_apply(dims, mu, KAPPA, b)
+    if gauge:
+        g = synth.gauge_transformation(dims, 32)
+        fwd, _, _, _ = W.neighbours(dims)
+        U = np.einsum("vab,vndb->vnad", g, g[fwd].conj())
+        b = np.einsum("vab,vsb->vsa", g, b.reshape(V, 4, 3)).reshape(-1)
+        ref = np.einsum("vab,vsb->vsa", g, ref.reshape(V, 4, 3)).reshape(-1)
+    else:
+        U = synth.free_gauge_field(dims)
+    ctx = _ctx(ovl, dims, U)
+    for flags in (ovl.OVERLAP, ovl.OVERLAP | ovl.MIXED):
+        y, info = _solve(ovl, ctx, ovl.LANCZOS2, 300, mu, b, flags=flags)
+        assert rel(y, ref) < (1e-10 if not flags & ovl.MIXED else 1e-8)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 4), (3, 2, 5, 4)])
+def test_small_ragged_lattices(ovl, dims):
+    """Lattices smaller than one thread block and with odd spatial extents."""
+    from oracle import sign as S
+    U = synth.gauge_field(dims, 0.4, 41)
+    A = W.a_operator(U, dims, 0.3, KAPPA)
+    Ad = A.conj().T.tocsr()
+    b = synth.gaussian_source(dims, 42)
+    ctx = _ctx(ovl, dims, U)
+    N = A.shape[0]
+    if N <= 400:  # Krylov space exhausted: exact (Sec. 2, Eq. 2.1)
+        ref = S.sign_spectral(A.toarray()) @ b
+        y, _ = _solve(ovl, ctx, ovl.ARNOLDI, N, 0.3, b)
+        assert rel(y, ref) < 1e-9
+    k = 150
+    y, _ = _solve(ovl, ctx, ovl.ARNOLDI, k, 0.3, b)
+    assert rel(y, K.sign_arnoldi(A.dot, b, k)) < 1e-9
+    k = 40
+    yl, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, 0.3, b)
+    assert rel(yl, K.sign_lanczos2(A.dot, Ad.dot, b, k)) < 1e-8
