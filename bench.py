@@ -283,14 +283,24 @@ def run_ours(args, world, rank, local):
         cal = calibrate_k(ovl, ctx, torch, bdev[0], [("mixed", ovl.MIXED), ("fp64", 0)])
     k_mix, err_mix = cal["mixed"]
     k_64, err_64 = cal["fp64"]
+    print(f"[bench] k mixed={k_mix} (err {err_mix}), k fp64={k_64} (err {err_64})", file=sys.stderr, flush=True)
     fl_mix = ovl.MIXED | ovl.OVERLAP
     fl_64 = ovl.OVERLAP
+
+    if args.solves_only:
+        if not args.k:
+            raise SystemExit("--solves-only needs --k")
+        t = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_mix, MU, KAPPA, b, out, flags=fl_mix),
+                        bdev, args.warmup, args.steps, flush)
+        print(json.dumps({"solves_only": True, "k": k_mix, "ms_per_step": statistics.mean(t)}))
+        return
 
     # ---- per-kernel profile of one solve (CUDA events around every kernel class)
     ctx.profile(reset=True)
     ctx.sign_krylov(ovl.LANCZOS2, k_mix, MU, KAPPA, bdev[0], out, flags=fl_mix | ovl.PROFILE)
     prof = ctx.profile(reset=True)
     kernels_per_solve = sum(v["kernels"] for v in prof.values())
+    print(f"[bench] profile {prof}", file=sys.stderr, flush=True)
 
     # ---- timed region: mixed two-pass (headline), device-resident inputs
     clocks = Clocks(local)
@@ -309,6 +319,7 @@ def run_ours(args, world, rank, local):
         tot = tt.item()
         torch.distributed.barrier()
     value = world * args.steps / (tot / 1e3)
+    print(f"[bench] mixed solves/s {value:.2f}, ms/step {statistics.mean(t_mix):.3f}", file=sys.stderr, flush=True)
 
     # ---- FP64 form and Arnoldi (context, fewer steps)
     t_64 = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_64, MU, KAPPA, b, out, flags=fl_64),
@@ -405,6 +416,9 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="fix the Krylov size (skip the accuracy calibration)")
     ap.add_argument("--no-dw", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--solves-only", action="store_true",
+                    help="only the timed solves (for profiler captures): needs --k, skips calibration, "
+                         "profile, FP64/Arnoldi/e2e legs, the bandwidth lattice and the CPU baseline")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

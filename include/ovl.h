@@ -144,6 +144,24 @@ int ovl_unpack(ovl_ctx* ctx, const void* native, void* canon, int prec);
 int ovl_set_deflation(ovl_ctx* ctx, double mu, double kappa, int m, const double* lambda,
                       const void* R, const void* L, int flags);
 
+/* Result of ovl_deflation_eigs. */
+typedef struct {
+    int       m;             /* eigenpairs installed                                     */
+    int       iterations;    /* filtered subspace iterations (right + left side)          */
+    long long matvecs;       /* applications of A or A^dag                                */
+    double    max_residual;  /* max |A r_j - lambda_j r_j| of the installed right pairs  */
+    double    lambda_cut;    /* |lambda| above which the last filter damped the spectrum  */
+} ovl_eiginfo;
+
+/* Deflation phase on the GPU (Sec. 3 and Sec. 5, where ARPACK plays this role): compute the
+ * m + nextra eigenvalues of A = gamma5 D_w(mu) nearest 0 with right and left eigenvectors
+ * (Chebyshev-filtered subspace iteration on A^2 with Rayleigh-Ritz on A and on A^dag,
+ * filter degree `degree`, at most `maxit` iterations, residual |A r - lambda r| <= tol |A|),
+ * keep the m of smallest |Re lambda|, and install them as by ovl_set_deflation.  Returns
+ * OVL_ENOCONV if the iteration did not converge.  Uses its own temporary device memory. */
+int ovl_deflation_eigs(ovl_ctx* ctx, double mu, double kappa, int m, int nextra, double tol, int degree,
+                       int maxit, ovl_eiginfo* info);
+
 /* Copy the installed (bi-orthonormalised) deflation out: *m_out = m; lambda (host, 2m
  * doubles), R and L canonical complex128 [m][12V] (device, or host with OVL_HOST).  NULL
  * output pointers are skipped (pass R = L = lambda = NULL to query m). */

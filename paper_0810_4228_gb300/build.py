@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libovl.so")
-SOURCES = ["stencil.cu", "krylov.cu", "inner_sign.cu", "api.cu"]
-HEADERS = ["ovl_common.cuh", "ovl_kernels.h"]
+SOURCES = ["stencil.cu", "krylov.cu", "inner_sign.cu", "api.cu", "eigs.cu", "host_eig.cpp"]
+HEADERS = ["ovl_common.cuh", "ovl_kernels.h", "ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--extended-lambda"]
 
@@ -43,7 +43,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     objs, jobs = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(s)[0] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
             jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])

@@ -55,6 +55,8 @@ void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim
                          double mu, double kappa, const KState* ks, const double2* alpha, const double2* beta,
                          const double2* gamma, const double2* c, int step, const Geom& g, cudaStream_t st);
 int dslash_grid(const Geom& g, int threads);
+// stencil thread layout: -1 automatic (by volume), 0 one thread per site, 1 direction split
+void set_dslash_variant(int mode);
 
 // ---- krylov.cu
 void launch_state_init(KState* ks, cudaStream_t st);

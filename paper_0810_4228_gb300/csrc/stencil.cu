@@ -116,6 +116,205 @@ __device__ __forceinline__ int site_of_thread(const Geom& g) {
 
 int dslash_grid(const Geom& g, int threads) { return (g.Vh + threads / 2 - 1) / (threads / 2); }
 
+// --------------------------------------------- direction-split variants --
+// For lattices too small to fill the GPU with one thread per site, the four
+// directions of a site go to four warps of the same block (warp w computes the
+// forward and backward hop of direction w for 32 consecutive sites, so no warp
+// diverges); the four partial spinors meet in shared memory, and the 128
+// threads then finish (site, spin) pairs: diagonal term, gamma5, scaling and
+// the fused epilogue.  Four times the threads, a quarter of the dependent
+// loads per thread.
+static constexpr int DS_SITES = 32;
+
+template <class R> __device__ __forceinline__ cx<R> ld_comp(const typename VecT<R>::T* x, int V, int i, int q);
+template <> __device__ __forceinline__ cx<double> ld_comp<double>(const double2* x, int V, int i, int q) {
+    const double2 v = __ldg(x + (size_t)q * V + i);
+    return mk(v.x, v.y);
+}
+template <> __device__ __forceinline__ cx<float> ld_comp<float>(const float4* x, int V, int i, int q) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(x) + ((size_t)(q >> 1) * V + i) * 2 + (q & 1));
+    return mk(v.x, v.y);
+}
+template <class R> __device__ __forceinline__ void st_comp(typename VecT<R>::T* x, int V, int i, int q, cx<R> z);
+template <> __device__ __forceinline__ void st_comp<double>(double2* x, int V, int i, int q, cx<double> z) {
+    x[(size_t)q * V + i] = make_double2(z.r, z.i);
+}
+template <> __device__ __forceinline__ void st_comp<float>(float4* x, int V, int i, int q, cx<float> z) {
+    reinterpret_cast<float2*>(x)[((size_t)(q >> 1) * V + i) * 2 + (q & 1)] = make_float2(z.r, z.i);
+}
+
+// partial spinors of the four directions: smem[dir][input][site][12]
+template <int LF, int NIN>
+__device__ __forceinline__ void dir_partials(const Geom& g, const void* U,
+                                             const typename VecT<typename LinkReal<LF>::R>::T* const (&x)[NIN],
+                                             const HopCoef<typename LinkReal<LF>::R> (&hc)[NIN],
+                                             cx<typename LinkReal<LF>::R>* sm) {
+    using R = typename LinkReal<LF>::R;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * DS_SITES + lane;
+    Spinor<R> acc[NIN];
+#pragma unroll
+    for (int n = 0; n < NIN; ++n)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[n].s[s][a] = mk(R(0), R(0));
+    if (i < g.V) {
+        const Coord c = site_coord(g, i);
+        switch (w) {  // uniform per warp
+            case 0: hops_dir<0, LF, R, NIN>(g, c, i, U, x, acc, hc); break;
+            case 1: hops_dir<1, LF, R, NIN>(g, c, i, U, x, acc, hc); break;
+            case 2: hops_dir<2, LF, R, NIN>(g, c, i, U, x, acc, hc); break;
+            default: hops_dir<3, LF, R, NIN>(g, c, i, U, x, acc, hc); break;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NIN; ++n)
+#pragma unroll
+        for (int q = 0; q < 12; ++q) sm[((w * NIN + n) * DS_SITES + lane) * 12 + q] = acc[n].s[q / 3][q % 3];
+    __syncthreads();
+}
+
+// sum of the four direction partials for (site, spin) of this thread, input n
+template <class R, int NIN>
+__device__ __forceinline__ void dir_sum(const cx<R>* sm, int n, int site, int sp, cx<R> (&o)[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<R> z = mk(R(0), R(0));
+#pragma unroll
+        for (int w = 0; w < 4; ++w) z = z + sm[((w * NIN + n) * DS_SITES + site) * 12 + 3 * sp + a];
+        o[a] = z;
+    }
+}
+
+template <int LF>
+__global__ void __launch_bounds__(128) k_dslash_ds(const void* __restrict__ U,
+                                                  const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ x,
+                                                  typename VecT<typename LinkReal<LF>::R>::T* __restrict__ y,
+                                                  HopCoef<typename LinkReal<LF>::R> hc, int g5, const KState* ks,
+                                                  Geom g) {
+    using R = typename LinkReal<LF>::R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R>* sm = reinterpret_cast<cx<R>*>(smraw);
+    if (ks && (ks->done || ks->status)) return;
+    const typename VecT<R>::T* const xs[1] = {x};
+    const HopCoef<R> hcs[1] = {hc};
+    dir_partials<LF, 1>(g, U, xs, hcs, sm);
+    const int site = threadIdx.x >> 2, sp = threadIdx.x & 3;
+    const int i = blockIdx.x * DS_SITES + site;
+    if (i >= g.V) return;
+    cx<R> o[3];
+    dir_sum<R, 1>(sm, 0, site, sp, o);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<R> z = o[a] + ld_comp<R>(x, g.V, i, 3 * sp + a);
+        if (g5 && sp >= 2) z = -z;
+        st_comp<R>(y, g.V, i, 3 * sp + a, z);
+    }
+}
+
+template <int LF>
+__global__ void __launch_bounds__(128) k_dslash_pair_ds(
+    const void* __restrict__ U, const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ v,
+    const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ w,
+    typename VecT<typename LinkReal<LF>::R>::T* __restrict__ t, typename VecT<typename LinkReal<LF>::R>::T* __restrict__ s,
+    HopCoef<typename LinkReal<LF>::R> hv, HopCoef<typename LinkReal<LF>::R> hw, KState* ks, double2* alpha, int step,
+    int klast, double* partials, unsigned int* counter, Geom g) {
+    using R = typename LinkReal<LF>::R;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R>* sm = reinterpret_cast<cx<R>*>(smraw);
+    __shared__ double red[96];
+    if (ks->done || ks->status) return;
+    const double2 sv = ks->sv, sw = ks->sw;
+    const typename VecT<R>::T* const xs[2] = {v, w};
+    const HopCoef<R> hcs[2] = {hv, hw};
+    dir_partials<LF, 2>(g, U, xs, hcs, sm);
+    const int site = threadIdx.x >> 2, sp = threadIdx.x & 3;
+    const int i = blockIdx.x * DS_SITES + site;
+    double part[3] = {0.0, 0.0, 0.0};
+    if (i < g.V) {
+        cx<R> ov[3], ow[3];
+        dir_sum<R, 2>(sm, 0, site, sp, ov);
+        dir_sum<R, 2>(sm, 1, site, sp, ow);
+        const cx<R> csv = mk(R(sv.x), R(sv.y)), csw = mk(R(sw.x), R(sw.y));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int q = 3 * sp + a;
+            const cx<R> wq = ld_comp<R>(w, g.V, i, q);
+            cx<R> tv = ov[a] + ld_comp<R>(v, g.V, i, q);
+            cx<R> sq = ow[a] + wq;
+            if (sp >= 2) {
+                tv = -tv;
+                sq = -sq;
+            }
+            tv = csv * tv;
+            sq = csw * sq;
+            st_comp<R>(t, g.V, i, q, tv);
+            st_comp<R>(s, g.V, i, q, sq);
+            const cx<double> z = cdot(up(wq), up(tv));
+            part[0] += z.r;
+            part[1] += z.i;
+            part[2] += norm2(up(tv));
+        }
+    }
+    double out[3];
+    if (grid_sum_last<3>(part, partials, counter, out, red)) {
+        if (threadIdx.x == 0) {
+            const cx<double> a = cdot(d2c(sw), mk(out[0], out[1]));
+            alpha[step] = c2d(a);
+            const double tn = sqrt(out[2]);
+            if (tn > ks->anorm) ks->anorm = tn;
+            ks->kused = step + 1;
+            if (step == klast) ks->done = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_dslash_regen_ds(const double2* __restrict__ U, const double2* __restrict__ vi,
+                                                         const double2* __restrict__ vim1, double2* __restrict__ vip1,
+                                                         double2* __restrict__ y, HopCoef<double> hc,
+                                                         const KState* ks, const double2* __restrict__ alpha,
+                                                         const double2* __restrict__ beta,
+                                                         const double2* __restrict__ gamma,
+                                                         const double2* __restrict__ c, int step, Geom g) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<double>* sm = reinterpret_cast<cx<double>*>(smraw);
+    if (ks->status || step + 1 >= ks->kused) return;
+    const double2* const xs[1] = {vi};
+    const HopCoef<double> hcs[1] = {hc};
+    dir_partials<LINK_F64, 1>(g, U, xs, hcs, sm);
+    const int site = threadIdx.x >> 2, sp = threadIdx.x & 3;
+    const int i = blockIdx.x * DS_SITES + site;
+    if (i >= g.V) return;
+    cx<double> o[3];
+    dir_sum<double, 1>(sm, 0, site, sp, o);
+    const cx<double> a = d2c(alpha[step]);
+    const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(beta[step]));
+    const cx<double> gm = step > 0 ? d2c(gamma[step - 1]) : mk(0.0, 0.0);
+    const cx<double> cc = d2c(c[step + 1]);
+#pragma unroll
+    for (int q3 = 0; q3 < 3; ++q3) {
+        const int q = 3 * sp + q3;
+        const size_t e = (size_t)q * g.V + i;
+        const cx<double> self = d2c(vi[e]);
+        cx<double> z = o[q3] + self;
+        if (sp >= 2) z = -z;
+        z = z - a * self;
+        if (step > 0) z = z - gm * d2c(vim1[e]);
+        z = ib * z;
+        vip1[e] = c2d(z);
+        cx<double> yy = d2c(y[e]);
+        cfma(yy, cc, z);
+        y[e] = c2d(yy);
+    }
+}
+
+static size_t ds_smem(int bytes_per_cx, int nin) { return (size_t)4 * nin * DS_SITES * 12 * bytes_per_cx; }
+static int ds_grid(const Geom& g) { return (g.V + DS_SITES - 1) / DS_SITES; }
+
+// one thread per site fills the GPU from about this many sites up
+static bool use_ds(const Geom& g) { return g.V < 152 * 1024; }
+
 // ------------------------------------------------------------ single apply --
 template <int LF>
 __global__ void __launch_bounds__(256) k_dslash(const void* __restrict__ U,
@@ -137,8 +336,24 @@ __global__ void __launch_bounds__(256) k_dslash(const void* __restrict__ U,
     store_spinor(y, g.V, i, acc[0]);
 }
 
+static int g_ds_mode = -1;  // -1 auto, 0 one thread per site, 1 direction split
+void set_dslash_variant(int mode) { g_ds_mode = mode; }
+static bool pick_ds(const Geom& g) { return g_ds_mode < 0 ? use_ds(g) : g_ds_mode == 1; }
+
 void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, double kappa, int gamma5,
                    const Geom& g, cudaStream_t st, const KState* ks) {
+    if (pick_ds(g)) {
+        if (prec == 0)
+            k_dslash_ds<LINK_F64><<<ds_grid(g), 128, ds_smem(16, 1), st>>>(U, (const double2*)x, (double2*)y,
+                                                                          make_coef<double>(mu, kappa), gamma5, ks, g);
+        else if (prec == 1)
+            k_dslash_ds<LINK_F32_12><<<ds_grid(g), 128, ds_smem(8, 1), st>>>(U, (const float4*)x, (float4*)y,
+                                                                            make_coef<float>(mu, kappa), gamma5, ks, g);
+        else
+            k_dslash_ds<LINK_F32_18><<<ds_grid(g), 128, ds_smem(8, 1), st>>>(U, (const float4*)x, (float4*)y,
+                                                                            make_coef<float>(mu, kappa), gamma5, ks, g);
+        return;
+    }
     const int T = 256, B = dslash_grid(g, T);
     if (prec == 0)
         k_dslash<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)x, (double2*)y, make_coef<double>(mu, kappa),
@@ -214,6 +429,23 @@ __global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
 void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, void* t, void* s, double mu,
                         double kappa, KState* ks, double2* alpha, int step, int klast, double* partials,
                         unsigned int* counter, const Geom& g, cudaStream_t st) {
+    if (pick_ds(g)) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_dslash_pair_ds<LINK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ds_smem(16, 2));
+            attr = true;
+        }
+        if (prec == 0)
+            k_dslash_pair_ds<LINK_F64><<<ds_grid(g), 128, ds_smem(16, 2), st>>>(
+                U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s, make_coef<double>(mu, kappa),
+                make_coef<double>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
+        else
+            k_dslash_pair_ds<LINK_F32_12><<<ds_grid(g), 128, ds_smem(8, 2), st>>>(
+                U, (const float4*)v, (const float4*)w, (float4*)t, (float4*)s, make_coef<float>(mu, kappa),
+                make_coef<float>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
+        return;
+    }
     const int T = 256, B = dslash_grid(g, T);
     if (prec == 0)
         k_dslash_pair<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s,
@@ -266,6 +498,11 @@ __global__ void __launch_bounds__(256) k_dslash_regen(const double2* __restrict_
 void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim1, double2* vip1, double2* y,
                          double mu, double kappa, const KState* ks, const double2* alpha, const double2* beta,
                          const double2* gamma, const double2* c, int step, const Geom& g, cudaStream_t st) {
+    if (pick_ds(g)) {
+        k_dslash_regen_ds<<<ds_grid(g), 128, ds_smem(16, 1), st>>>(U, vi, vim1, vip1, y, make_coef<double>(mu, kappa),
+                                                                   ks, alpha, beta, gamma, c, step, g);
+        return;
+    }
     const int T = 256, B = dslash_grid(g, T);
     k_dslash_regen<<<B, T, 0, st>>>(U, vi, vim1, vip1, y, make_coef<double>(mu, kappa), ks, alpha, beta, gamma, c,
                                     step, g);

@@ -31,7 +31,8 @@ _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EB
 
 EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
            "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_pack", "ovl_unpack",
-           "ovl_set_deflation", "ovl_sign_krylov", "ovl_profile_get", "ovl_profile_reset"]
+           "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
+           "ovl_profile_get", "ovl_profile_reset"]
 
 
 class OvlError(RuntimeError):
@@ -43,6 +44,14 @@ class OvlError(RuntimeError):
 class KStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int), ("kernels", ctypes.c_longlong),
                 ("ms", ctypes.c_double)]
+
+
+class EigInfo(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("iterations", ctypes.c_int), ("matvecs", ctypes.c_longlong),
+                ("max_residual", ctypes.c_double), ("lambda_cut", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Info(ctypes.Structure):
@@ -80,6 +89,8 @@ def load(path: str = LIB_PATH):
         "ovl_set_deflation": (I, [P, D, D, I, ctypes.POINTER(D), P, P, I]),
         "ovl_sign_krylov": (I, [P, I, I, D, D, P, P, I, ctypes.POINTER(Info)]),
         "ovl_profile_get": (I, [P, ctypes.POINTER(KStat), I, ctypes.POINTER(I)]),
+        "ovl_get_deflation": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D), P, P, I]),
+        "ovl_deflation_eigs": (I, [P, D, D, I, I, D, I, I, ctypes.POINTER(EigInfo)]),
         "ovl_profile_reset": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -211,6 +222,33 @@ class Context:
         self._check(self._lib.ovl_set_deflation(
             self._h, mu, kappa, m, lam_d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             _ptr(R), _ptr(L), flags))
+
+    def deflation_eigs(self, mu: float, kappa: float, m: int, nextra: int = 10, tol: float = 1e-10,
+                       degree: int = 80, maxit: int = 60):
+        """Compute and install the m critical eigenpairs on the GPU; returns info dict."""
+        info = EigInfo()
+        self._check(self._lib.ovl_deflation_eigs(self._h, mu, kappa, m, nextra, tol, degree, maxit,
+                                                  ctypes.byref(info)))
+        return info.as_dict()
+
+    def get_deflation(self, device: bool = True):
+        """(lam, R, L) of the installed deflation; R, L canonical (m, 12V) complex128."""
+        import torch
+        m = ctypes.c_int()
+        self._check(self._lib.ovl_get_deflation(self._h, ctypes.byref(m), None, None, None, 0))
+        m = m.value
+        lam = np.empty(2 * max(m, 1))
+        if device:
+            R = torch.empty((m, self.n), dtype=torch.complex128, device="cuda")
+            L = torch.empty_like(R)
+            flags = 0
+        else:
+            R = np.empty((m, self.n), dtype=np.complex128)
+            L = np.empty_like(R)
+            flags = HOST
+        self._check(self._lib.ovl_get_deflation(self._h, None, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                _ptr(R) if m else None, _ptr(L) if m else None, flags))
+        return lam[0:2 * m:2] + 1j * lam[1:2 * m:2], R, L
 
     def profile(self, reset: bool = True):
         """Per-kernel-class totals of the OVL_PROFILE solves since the last reset."""
