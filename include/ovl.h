@@ -77,6 +77,8 @@ typedef struct ovl_ctx ovl_ctx;
 #define OVL_INNER_NEWTON 0x1000  /* inner sgn(G_k): Roberts/Newton (Sec. 2) instead of the
                                     resolvent quadrature (2sL only)                        */
 #define OVL_NO_GRAPH     0x2000  /* sign_krylov: launch kernels directly, no CUDA graph     */
+#define OVL_STENCIL_SITE  0x10000 /* apply_Dw: force one thread per site (default: by volume)    */
+#define OVL_STENCIL_SPLIT 0x20000 /* apply_Dw: force the direction-split layout (4 threads/site)   */
 #define OVL_PROFILE      0x4000  /* sign_krylov: time every kernel class with CUDA events on the
                                     context's stream (implies OVL_NO_GRAPH); read the totals with
                                     ovl_profile_get                                        */

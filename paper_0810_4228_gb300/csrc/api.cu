@@ -409,6 +409,7 @@ int ovl_destroy(ovl_ctx* c) {
     drop_graph(c);
     free_solve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
     dfree(&c->U64), dfree(&c->U12), dfree(&c->U18);
     dfree(&c->R), dfree(&c->L), dfree(&c->lam);
     dfree(&c->b64), dfree(&c->y64), dfree(&c->bR), dfree(&c->bL), dfree(&c->t64), dfree(&c->s64);
@@ -480,6 +481,10 @@ int ovl_apply_Dw(ovl_ctx* c, double mu, double kappa, const void* x, void* y, in
     const void* U = prec == 0 ? (const void*)c->U64 : prec == 1 ? (const void*)c->U12 : (const void*)c->U18;
     const int g5 = (flags & (OVL_GAMMA5 | OVL_DAGGER)) ? 1 : 0;
     const double m = (flags & OVL_DAGGER) ? -mu : mu;
+    struct VariantGuard {
+        explicit VariantGuard(int f) { ovl::set_dslash_variant(f & OVL_STENCIL_SITE ? 0 : f & OVL_STENCIL_SPLIT ? 1 : -1); }
+        ~VariantGuard() { ovl::set_dslash_variant(-1); }
+    } vg(flags);
     if (flags & OVL_NATIVE) {
         if (flags & OVL_HOST) return fail(c, OVL_EINVAL, "OVL_NATIVE vectors must be device memory");
         ovl::launch_dslash(U, prec, x, y, m, kappa, g5, c->g, c->st);
@@ -616,9 +621,15 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
               ge.kappa == kappa)) {
             drop_graph(c);
             cudaGraph_t graph = nullptr;
-            if (c->st && cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            // capture on a private stream (the caller's may be the legacy default stream, which
+            // cannot be captured); the graph is then launched on the caller's stream
+            if (!c->cap_st) cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
+            cudaStream_t user_st = c->st;
+            if (c->cap_st && cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                c->st = c->cap_st;
                 const int er = enqueue_solve(c, method, k, mu, kappa, gflags);
-                const cudaError_t ec = cudaStreamEndCapture(c->st, &graph);
+                const cudaError_t ec = cudaStreamEndCapture(c->cap_st, &graph);
+                c->st = user_st;
                 if (er == OVL_OK && ec == cudaSuccess && graph) {
                     cudaGraphExec_t exec = nullptr;
                     if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {

@@ -38,6 +38,7 @@ struct ovl_ctx {
     ovl::Geom g{};
     size_t n = 0;  // 12 V complex per vector
     cudaStream_t st = nullptr;
+    cudaStream_t cap_st = nullptr;  // private stream the solve graph is captured on
     int device = 0, num_sms = 0;
     std::string err;
 

@@ -24,13 +24,15 @@ def ovl():
 @pytest.mark.parametrize("dims", SHAPES)
 @pytest.mark.parametrize("mu", [0.0, 0.3])
 @pytest.mark.parametrize("bc_t", [-1, 1])
-def test_A_fp64(ovl, dims, mu, bc_t):
+@pytest.mark.parametrize("layout", ["SITE", "SPLIT"])
+def test_A_fp64(ovl, dims, mu, bc_t, layout):
     U = synth.gauge_field(dims, 1.0, 7)
     x = synth.gaussian_source(dims, 8)
     ref = W.a_operator(U, dims, mu, KAPPA, bc_t) @ x
     ctx = ovl.Context(dims, bc_t)
     ctx.set_gauge(torch_c128(U))
-    y = ctx.apply_Dw(mu, KAPPA, torch_c128(x), flags=ovl.GAMMA5).cpu().numpy()
+    fl = ovl.GAMMA5 | getattr(ovl, "STENCIL_" + layout)
+    y = ctx.apply_Dw(mu, KAPPA, torch_c128(x), flags=fl).cpu().numpy()
     assert maxrel(y, ref) < 1e-14
 
 
@@ -50,14 +52,16 @@ def test_dw_and_dagger_fp64(ovl, dims):
 
 @pytest.mark.parametrize("flag,tol", [("F32", 3e-6), ("F32_FULL", 3e-6)])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 2, 5, 4), (8, 8, 8, 8)])
-def test_A_fp32(ovl, dims, flag, tol):
+@pytest.mark.parametrize("layout", ["SITE", "SPLIT"])
+def test_A_fp32(ovl, dims, flag, tol, layout):
     mu = 0.3
     U = synth.gauge_field(dims, 1.0, 11)
     x = synth.gaussian_source(dims, 12)
     ref = W.a_operator(U, dims, mu, KAPPA) @ x
     ctx = ovl.Context(dims)
     ctx.set_gauge(torch_c128(U))
-    y = ctx.apply_Dw(mu, KAPPA, torch_c128(x), flags=ovl.GAMMA5 | getattr(ovl, flag)).cpu().numpy()
+    fl = ovl.GAMMA5 | getattr(ovl, flag) | getattr(ovl, "STENCIL_" + layout)
+    y = ctx.apply_Dw(mu, KAPPA, torch_c128(x), flags=fl).cpu().numpy()
     assert maxrel(y, ref) < tol
 
 
@@ -146,3 +150,22 @@ def test_invalid_arguments(ovl):
     with pytest.raises(ovl.OvlError) as e:
         ctx.apply_Dw(0.1, KAPPA, x)  # no gauge field
     assert e.value.code == ovl.ESTATE
+
+
+@pytest.mark.parametrize("layout", ["SITE", "SPLIT"])
+def test_large_lattice_sampled(ovl, layout):
+    """24^4 (331776 sites, above the split threshold): sampled sites of the FP64
+    and FP32-12 stencils against the oracle's single-site evaluator."""
+    dims, mu = (24, 24, 24, 24), 0.3
+    U = synth.gauge_field(dims, 1.0, 23)
+    x = synth.gaussian_source(dims, 24)
+    ctx = ovl.Context(dims)
+    ctx.set_gauge(torch_c128(U))
+    fl = getattr(ovl, "STENCIL_" + layout)
+    y = ctx.apply_Dw(mu, KAPPA, torch_c128(x), flags=ovl.GAMMA5 | fl).cpu().numpy()
+    y32 = ctx.apply_Dw(mu, KAPPA, torch_c128(x), flags=ovl.GAMMA5 | ovl.F32 | fl).cpu().numpy()
+    rng = np.random.default_rng(25)
+    for site in list(rng.integers(0, 331776, 6)) + [0, 331775]:
+        ref = W.wilson_site(U, dims, mu, KAPPA, x, int(site))
+        np.testing.assert_allclose(y[12 * site:12 * site + 12], ref, atol=1e-13)
+        np.testing.assert_allclose(y32[12 * site:12 * site + 12], ref, atol=3e-5)
