@@ -130,6 +130,24 @@ int ovl_apply_Dw(ovl_ctx* ctx, double mu, double kappa, const void* x, void* y, 
 int ovl_apply_pair(ovl_ctx* ctx, double mu, double kappa, int prec,
                    const void* v, const void* w, void* t, void* s, double* alpha_host);
 
+/* The same pair application as ovl_apply_pair, for callers that must not allocate device
+ * memory when they call it -- code capturing a CUDA graph (allocation is illegal there), or
+ * a caller whose memory belongs to its own pool or arena.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine: the reduction's scratch is a static device array of the
+ * library (768 KiB, resident on every GPU that loads the library).  The paper has no
+ * counterpart; this is a calling convention of this library.
+ *   - alpha_dev: DEVICE pointer to 2 doubles receiving alpha = w^dag t; nothing is copied
+ *     to the host and the call does not synchronise (read alpha after the stream's work).
+ *   - the context and its gauge field must exist already (they allocate when created).
+ *   - lattices above 8388608 sites are rejected with OVL_EINVAL.
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     no allocation); make that first call before any stream capture that includes it.
+ *   - all calls share the array and it keeps the last call's contents; each call resets
+ *     what must start at zero, but calls that overlap on the GPU (e.g. on two streams at
+ *     once) race on it and give wrong results. */
+int ovl_apply_pair_noalloc(ovl_ctx* ctx, double mu, double kappa, int prec,
+                           const void* v, const void* w, void* t, void* s, double* alpha_dev);
+
 /* Convert a canonical complex128 vector (device) into the device layout (prec 0 or 1)
  * and back. */
 int ovl_pack(ovl_ctx* ctx, const void* canon, void* native, int prec);

@@ -31,7 +31,7 @@ _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EB
              ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
 
 EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
-           "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_pack", "ovl_unpack",
+           "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
            "ovl_profile_get", "ovl_profile_reset"]
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         "ovl_set_gauge": (I, [P, P, I]),
         "ovl_apply_Dw": (I, [P, D, D, P, P, I]),
         "ovl_apply_pair": (I, [P, D, D, I, P, P, P, P, ctypes.POINTER(D)]),
+        "ovl_apply_pair_noalloc": (I, [P, D, D, I, P, P, P, P, P]),
         "ovl_pack": (I, [P, P, P, I]),
         "ovl_unpack": (I, [P, P, P, I]),
         "ovl_set_deflation": (I, [P, D, D, I, ctypes.POINTER(D), P, P, I]),
@@ -209,6 +210,12 @@ class Context:
         a = (ctypes.c_double * 2)()
         self._check(self._lib.ovl_apply_pair(self._h, mu, kappa, prec, _ptr(v), _ptr(w), _ptr(t), _ptr(s), a))
         return complex(a[0], a[1])
+
+    def apply_pair_noalloc(self, mu: float, kappa: float, v, w, t, s, alpha_dev, prec: int = 0):
+        """As apply_pair, without any device allocation: alpha = w^dag t is written to the
+        device tensor alpha_dev (2 float64) and nothing is synchronised."""
+        self._check(self._lib.ovl_apply_pair_noalloc(self._h, mu, kappa, prec, _ptr(v), _ptr(w), _ptr(t), _ptr(s),
+                                                      _ptr(alpha_dev)))
 
     def set_deflation(self, mu: float, kappa: float, lam, R, L):
         """Install m critical eigenpairs: lam (m,) complex, R and L (m, 12V) complex128."""
