@@ -142,6 +142,7 @@ def calibrate_k(ovl, ctx, torch, b, flags_list):
         for k in K_GRID:
             y, info = ctx.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, b, flags=fl)
             e = torch.linalg.vector_norm(y - ref).item() / nrm
+            print(f"[bench] calibrate {name} k={k} err={e:.3e}", file=sys.stderr, flush=True)
             if e <= 1e-8:
                 chosen, err = k, e
                 break

@@ -76,6 +76,12 @@ typedef struct ovl_ctx ovl_ctx;
                                     from alpha, beta, gamma in a second pass (Sec. 5)       */
 #define OVL_INNER_NEWTON 0x1000  /* inner sgn(G_k): Roberts/Newton (Sec. 2) instead of the
                                     resolvent quadrature (2sL only)                        */
+#define OVL_REPROJ       0x8000  /* sign_krylov MIXED with deflation: project the deflated directions
+                                    out of every FP32 pass-1 vector (v^ -= R L^dag v^, w^ -= L R^dag w^).
+                                    Off by default: with FP32 copies of R, L the projected operator
+                                    differs from A at the 1e-8 level, which then bounds the accuracy */
+#define OVL_STEPWISE     0x40000 /* sign_krylov MIXED: one kernel per recurrence step instead of the
+                                    persistent cooperative kernels (default on small lattices)   */
 #define OVL_NO_GRAPH     0x2000  /* sign_krylov: launch kernels directly, no CUDA graph     */
 #define OVL_STENCIL_SITE  0x10000 /* apply_Dw: force one thread per site (default: by volume)    */
 #define OVL_STENCIL_SPLIT 0x20000 /* apply_Dw: force the direction-split layout (4 threads/site)   */
@@ -147,6 +153,16 @@ int ovl_apply_pair(ovl_ctx* ctx, double mu, double kappa, int prec,
  *     once) race on it and give wrong results. */
 int ovl_apply_pair_noalloc(ovl_ctx* ctx, double mu, double kappa, int prec,
                            const void* v, const void* w, void* t, void* s, double* alpha_dev);
+
+/* Adjoint of y = A x, A = gamma5 D_w(mu; U) (Eq. 1.2), for a real function l(y), in PyTorch's
+ * convention for complex gradients (g_z = dl/dRe z + i dl/dIm z, so dl = Re <g_z, dz>): given
+ * g = g_y, writes
+ *   grad_U[x][nu] = g_{U_{x,nu}}     (canonical complex128 [V][4][3][3], device; may be NULL)
+ *   *grad_mu      = dl/dmu = Re <g, (dA/dmu) x>, dA/dmu = -kappa gamma5 (e^mu T_4^+ - e^-mu T_4^-)
+ * (host double; may be NULL).  x, g: canonical complex128 device vectors.  grad_x = A^dag g is
+ * ovl_apply_Dw with OVL_DAGGER.  Uses the installed gauge field U. */
+int ovl_dw_grad(ovl_ctx* ctx, double mu, double kappa, const void* x, const void* g, void* grad_U,
+                double* grad_mu, int flags);
 
 /* Convert a canonical complex128 vector (device) into the device layout (prec 0 or 1)
  * and back. */

@@ -22,8 +22,8 @@ namespace {
 
 const char* kclass_name[ovl_priv::KC_COUNT] = {"setup", "deflate_split", "dslash_pair", "lanczos_step", "inner_sign",
                                      "dslash_regen", "combine", "dslash", "multidot", "multiaxpy",
-                                     "arnoldi_normalize", "convert"};
-const int kclass_kernels[ovl_priv::KC_COUNT] = {1, 1, 1, 1, 0, 1, 1, 1, 2, 1, 1, 1};
+                                     "arnoldi_normalize", "convert", "pass1_persistent", "pass2_persistent"};
+const int kclass_kernels[ovl_priv::KC_COUNT] = {1, 1, 1, 1, 0, 1, 1, 1, 2, 1, 1, 1, 1, 1};
 
 }  // namespace
 
@@ -77,7 +77,7 @@ int ensure_base(ovl_ctx* c) {
     if ((r = dalloc(c, &c->b64, vb)) || (r = dalloc(c, &c->y64, vb)) || (r = dalloc(c, &c->bR, vb)) ||
         (r = dalloc(c, &c->bL, vb)) || (r = dalloc(c, &c->t64, vb)) || (r = dalloc(c, &c->s64, vb)) ||
         (r = dalloc(c, &c->t32, c->n * sizeof(float2))) || (r = dalloc(c, &c->s32, c->n * sizeof(float2))) ||
-        (r = dalloc(c, &c->ks, sizeof(KState))) || (r = dalloc(c, &c->counter, 64)) ||
+        (r = dalloc(c, &c->ks, sizeof(KState))) || (r = dalloc(c, &c->counter, 64)) || (r = dalloc(c, &c->bar, 64)) ||
         (r = dalloc(c, &c->stage_in, vb)) || (r = dalloc(c, &c->stage_out, vb)) ||
         (r = dalloc(c, &c->nat_a, vb)) || (r = dalloc(c, &c->nat_b, vb)) || (r = dalloc(c, &c->pq, 4096 * sizeof(double2))))
         return r;
@@ -94,7 +94,7 @@ int ensure_solve(ovl_ctx* c, int k) {
     if (r) return r;
     const int mdb = ovl::multidot_blocks(c->n);
     const size_t need_part = std::max<size_t>((size_t)(k + 2 + 2 * std::max(c->m, 1)) * mdb * sizeof(double2),
-                                              (size_t)8 * 4096 * sizeof(double));
+                                              (size_t)1 << 19);
     if (k <= c->kcap && c->partials_bytes >= need_part) return OVL_OK;
     drop_graph(c);
     dfree(&c->V64);
@@ -112,6 +112,7 @@ int ensure_solve(ovl_ctx* c, int k) {
         return r;
     }
     CUDA_TRY(c, cudaMemsetAsync(c->counter, 0, 64, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(c->bar, 0, 64, c->st));
     c->kcap = kc;
     c->partials_bytes = need_part;
     c->inner_elems = ie;
@@ -157,10 +158,12 @@ int install_deflation(ovl_ctx* c, double mu, double kappa, int m, const double* 
     for (int j = 0; j < m; ++j)
         if (std::fabs(lambda[2 * j]) <= 1e-12 * lmax)
             return fail(c, OVL_ESINGULAR, "deflated eigenvalue on the imaginary axis");
+    if (m > 64) return fail(c, OVL_EINVAL, "at most 64 deflated eigenpairs");
     if (m > c->mcap) {
-        dfree(&c->R), dfree(&c->L), dfree(&c->lam);
+        dfree(&c->R), dfree(&c->L), dfree(&c->lam), dfree(&c->R32), dfree(&c->L32);
         if ((r = dalloc(c, &c->R, vb * m)) || (r = dalloc(c, &c->L, vb * m)) ||
-            (r = dalloc(c, &c->lam, sizeof(double2) * m)))
+            (r = dalloc(c, &c->lam, sizeof(double2) * m)) || (r = dalloc(c, &c->R32, n * sizeof(float2) * m)) ||
+            (r = dalloc(c, &c->L32, n * sizeof(float2) * m)))
             return r;
         c->mcap = m;
     }
@@ -208,6 +211,8 @@ int install_deflation(ovl_ctx* c, double mu, double kappa, int m, const double* 
         c->m = 0;
         return fail(c, OVL_ESINGULAR, "L^dag R not bi-orthonormal after normalisation");
     }
+    ovl::launch_native_f64_to_f32(c->R, c->R32, c->g, m, c->st);
+    ovl::launch_native_f64_to_f32(c->L, c->L32, c->g, m, c->st);
     c->dmu = mu;
     c->dkappa = kappa;
     return OVL_OK;
@@ -263,6 +268,7 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
     const bool mixed = (flags & OVL_MIXED) != 0;
     const bool twopass = mixed || (flags & OVL_TWO_PASS);
     const int m = c->m;
+    const int mproj = (flags & OVL_REPROJ) ? m : 0;
 
     prof(c, KC_SETUP, [&] { ovl::launch_state_init(ks, st); });
     if (m > 0) {
@@ -280,26 +286,46 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
         });
         if (mixed) {
             prof(c, KC_CONVERT, [&] {
-                ovl::launch_convert_f64_f32(c->bR, c->v32[0], n, st);
-                ovl::launch_convert_f64_f32(c->bL, c->w32[0], n, st);
+                ovl::launch_native_f64_to_f32(c->bR, c->v32[0], g, 1, st);
+                ovl::launch_native_f64_to_f32(c->bL, c->w32[0], g, 1, st);
             }, 2);
         } else if (twopass) {
             cudaMemcpyAsync(c->R64[0], c->bR, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
             cudaMemcpyAsync(c->W64[0], c->bL, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
         }
         // pass 1: basis (stored for one-pass FP64) and coefficients
-        for (int i = 0; i < k; ++i) {
+        const bool persist = mixed && !(flags & OVL_STEPWISE) && ovl::persistent_ok(g, c->num_sms);
+        if (persist) {
+            cudaMemsetAsync(c->bar, 0, 64, st);
+            int lr = 0;
+            prof(c, KC_PASS1, [&] {
+                float4* vv[3] = {(float4*)c->v32[0], (float4*)c->v32[1], (float4*)c->v32[2]};
+                float4* ww[3] = {(float4*)c->w32[0], (float4*)c->w32[1], (float4*)c->w32[2]};
+                lr = ovl::launch_pass1_persistent(c->U12, vv, ww, ks, c->alpha, c->beta, c->gamma, c->R32, c->L32,
+                                                  mproj, mu, kappa, k, part, c->bar, g, c->num_sms, st);
+            });
+            if (lr) return fail(c, OVL_ECUDA, std::string("persistent pass 1 launch: ") +
+                                                   cudaGetErrorString((cudaError_t)lr));
+        }
+        for (int i = 0; i < (persist ? 0 : k); ++i) {
             if (mixed) {
                 prof(c, KC_PAIR, [&] {
                     ovl::launch_dslash_pair(c->U12, 1, c->v32[i % 3], c->w32[i % 3], c->t32, c->s32, mu, kappa, ks,
                                             c->alpha, i, k - 1, part, cnt, g, st);
                 });
+                // optional re-projection of the deflated directions (p = L^dag t, q = R^dag s)
+                double2* pq2 = c->pq + 2048;
+                if (i + 1 < k && mproj > 0)
+                    prof(c, KC_DEFLATE, [&] {
+                        ovl::launch_multidot_f32(c->L32, n, mproj, c->t32, pq2, part, n, st, ks);
+                        ovl::launch_multidot_f32(c->R32, n, mproj, c->s32, pq2 + mproj, part, n, st, ks);
+                    }, 4);
                 if (i + 1 < k)
                     prof(c, KC_LSTEP, [&] {
                         ovl::launch_lanczos_step(1, c->t32, c->s32, c->v32[i % 3], c->w32[i % 3],
                                                  c->v32[(i + 2) % 3], c->w32[(i + 2) % 3], c->v32[(i + 1) % 3],
                                                  c->w32[(i + 1) % 3], ks, c->alpha, c->beta, c->gamma, c->vscale, i,
-                                                 k, part, cnt, n, st);
+                                                 k, part, cnt, n, st, c->R32, c->L32, pq2, mproj);
                     });
             } else {
                 const double2* vi = twopass ? c->R64[i % 3] : c->V64 + (size_t)i * n;
@@ -323,15 +349,29 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
             prof(c, KC_INNER, [&] {
                 r = ovl::launch_inner_newton(c->alpha, c->beta, c->gamma, nullptr, 0, 1, ks, c->cvec, c->inner,
                                              c->inner_elems, c->kcap, c->num_sms, st);
-            }, 122);
+            }, 2);
         else
             prof(c, KC_INNER, [&] {
                 r = ovl::launch_inner_quadrature(c->alpha, c->beta, c->gamma, ks, c->cvec, c->inner,
                                                  c->inner_elems, c->kcap, part, cnt, st);
-            }, 13);
+                // Roberts/Newton only if the quadrature did not converge (Ritz values near the axis)
+                if (!r)
+                    r = ovl::launch_inner_newton(c->alpha, c->beta, c->gamma, nullptr, 0, 1, ks, c->cvec, c->inner,
+                                                 c->inner_elems, c->kcap, c->num_sms, st, 1);
+            }, 15);
         if (r) return fail(c, OVL_ECUDA, "inner sign launch failed");
         // combination y += |b_perp^R| V_k sgn(G_k) e_1
-        if (twopass) {
+        if (twopass && persist) {
+            prof(c, KC_COMBINE, [&] { ovl::launch_scale_start(c->bR, c->R64[0], c->y64, c->cvec, ks, n, st); });
+            int lr = 0;
+            prof(c, KC_PASS2, [&] {
+                double2* rr[3] = {c->R64[0], c->R64[1], c->R64[2]};
+                lr = ovl::launch_pass2_persistent(c->U64, rr, c->y64, ks, c->alpha, c->beta, c->gamma, c->cvec, mu,
+                                                  kappa, c->bar, &ks->timeout, g, c->num_sms, st);
+            });
+            if (lr) return fail(c, OVL_ECUDA, std::string("persistent pass 2 launch: ") +
+                                                   cudaGetErrorString((cudaError_t)lr));
+        } else if (twopass) {
             prof(c, KC_COMBINE, [&] { ovl::launch_scale_start(c->bR, c->R64[0], c->y64, c->cvec, ks, n, st); });
             for (int i = 0; i + 1 < k; ++i)
                 prof(c, KC_REGEN, [&] {
@@ -365,7 +405,7 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
         prof(c, KC_INNER, [&] {
             r = ovl::launch_inner_newton(nullptr, nullptr, nullptr, c->H, ldH, 0, ks, c->cvec, c->inner,
                                          c->inner_elems, c->kcap, c->num_sms, st);
-        }, 122);
+        }, 2);
         if (r) return fail(c, OVL_ECUDA, "inner sign launch failed");
         prof(c, KC_COMBINE, [&] { ovl::launch_combine(c->V64, n, nullptr, c->cvec, ks, c->kcap, c->y64, n, st); });
     }
@@ -411,9 +451,10 @@ int ovl_destroy(ovl_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
     dfree(&c->U64), dfree(&c->U12), dfree(&c->U18);
-    dfree(&c->R), dfree(&c->L), dfree(&c->lam);
+    dfree(&c->R), dfree(&c->L), dfree(&c->lam), dfree(&c->R32), dfree(&c->L32);
     dfree(&c->b64), dfree(&c->y64), dfree(&c->bR), dfree(&c->bL), dfree(&c->t64), dfree(&c->s64);
-    dfree(&c->t32), dfree(&c->s32), dfree(&c->ks), dfree(&c->counter), dfree(&c->stage_in), dfree(&c->stage_out);
+    dfree(&c->t32), dfree(&c->s32), dfree(&c->ks), dfree(&c->counter), dfree(&c->bar), dfree(&c->stage_in),
+        dfree(&c->stage_out);
     dfree(&c->nat_a), dfree(&c->nat_b), dfree(&c->pq);
     for (int i = 0; i < 3; ++i) dfree(&c->W64[i]), dfree(&c->R64[i]), dfree(&c->v32[i]), dfree(&c->w32[i]);
     delete c;
@@ -612,7 +653,7 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
     ovl::launch_pack_spinor(bin, c->b64, 0, c->g, c->st);
     CUDA_TRY(c, cudaGetLastError());
 
-    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON);
+    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_STEPWISE);
     bool ran = false;
     c->prof_on = (flags & OVL_PROFILE) != 0;
     if (!(flags & (OVL_NO_GRAPH | OVL_PROFILE))) {

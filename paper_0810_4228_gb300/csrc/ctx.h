@@ -16,7 +16,7 @@ namespace ovl_priv {
 // kernel classes of the per-kernel profile (OVL_PROFILE)
 enum KClass {
     KC_SETUP = 0, KC_DEFLATE, KC_PAIR, KC_LSTEP, KC_INNER, KC_REGEN, KC_COMBINE, KC_ADSLASH, KC_ADOT, KC_AAXPY,
-    KC_ANORM, KC_CONVERT, KC_COUNT
+    KC_ANORM, KC_CONVERT, KC_PASS1, KC_PASS2, KC_COUNT
 };
 
 struct ProfRec {
@@ -54,6 +54,8 @@ struct ovl_ctx {
     double2* R = nullptr;
     double2* L = nullptr;
     double2* lam = nullptr;
+    float2* R32 = nullptr;  // FP32 copies for re-projection in the FP32 pass
+    float2* L32 = nullptr;
     int mcap = 0;
 
     // solve workspace
@@ -71,6 +73,7 @@ struct ovl_ctx {
     double* partials = nullptr;
     size_t partials_bytes = 0;
     unsigned int* counter = nullptr;
+    unsigned int* bar = nullptr;  // grid barrier of the persistent kernels
     double2* inner = nullptr;
     size_t inner_elems = 0;
     double2* stage_in = nullptr;   // canonical staging (host transfers, apply_Dw)

@@ -30,7 +30,7 @@
 namespace ovl {
 
 static constexpr double QUAD_H0 = 0.25;       // first trapezoid step in u
-static constexpr double QUAD_HALFWIDTH = 45;  // u range: log|G| -+ 45
+static constexpr double QUAD_HALFWIDTH = 40;  // u range: log|G| -+ 40 (tails below e^-40)
 static constexpr int QUAD_LEVELS = 6;         // steps 0.25 ... 0.25/32
 
 static int quad_nodes_level0() { return (int)ceil(2 * QUAD_HALFWIDTH / QUAD_H0); }
@@ -110,10 +110,12 @@ __global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* _
         const cx<double> l = d2c(beta[i]);                    // row i+1, column i
         const cx<double> dn = d2c(alpha[i + 1]) + sig;        // row i+1, column i+1
         const cx<double> un = (i + 2 < n) ? d2c(gamma[i + 1]) : mk(0.0, 0.0);
-        if (norm2(d) >= norm2(l)) {
-            // no interchange: final row i = (d, uu, 0)
-            const cx<double> m = cdiv(l, d);
-            const cx<double> id = cdiv(mk(1.0, 0.0), d);
+        const double nd2 = norm2(d), nl2 = norm2(l);
+        if (nd2 >= nl2) {
+            // no interchange: final row i = (d, uu, 0); one reciprocal 1/d = conj(d)/|d|^2
+            const double inv = 1.0 / nd2;
+            const cx<double> id = mk(d.r * inv, -d.i * inv);
+            const cx<double> m = l * id;
             bd[IDX(i)] = c2d(rb * id);
             ud[IDX(i)] = c2d(uu * id);
             wd[IDX(i)] = make_double2(0.0, 0.0);
@@ -122,8 +124,9 @@ __global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* _
             rb = mk(0.0, 0.0) - m * rb;   // rhs of row i+1 is 0 for e_1 beyond row 0
         } else {
             // interchange rows i and i+1: final row i = (l, dn, un), rhs 0
-            const cx<double> m = cdiv(d, l);
-            const cx<double> il = cdiv(mk(1.0, 0.0), l);
+            const double inv = 1.0 / nl2;
+            const cx<double> il = mk(l.r * inv, -l.i * inv);
+            const cx<double> m = d * il;
             bd[IDX(i)] = make_double2(0.0, 0.0);
             ud[IDX(i)] = c2d(dn * il);
             wd[IDX(i)] = c2d(un * il);
@@ -163,18 +166,26 @@ __global__ void k_quad_sum(const double2* __restrict__ work, double2* __restrict
     // one warp per row i
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = blockIdx.x * nw + wid; i < n; i += gridDim.x * nw) {
-        double sr = 0.0, si = 0.0;
+        double sr = 0.0, si = 0.0, er = 0.0, ei = 0.0;  // all nodes; even nodes (step 2h)
         for (int t = lane; t < nthreads; t += 32) {
             double2 v = work[(size_t)i * nthreads + t];
             sr += v.x;
             si += v.y;
+            if (((t >> 1) & 1) == 0) {
+                er += v.x;
+                ei += v.y;
+            }
         }
         sr = warp_sum(sr);
         si = warp_sum(si);
+        er = warp_sum(er);
+        ei = warp_sum(ei);
         if (lane == 0) {
-            double2 old = level == 0 ? make_double2(0.0, 0.0) : T[i];
+            // level 0 compares with the trapezoid sum of step 2h over its even nodes
+            double2 old = level == 0 ? make_double2(2.0 * wgt * er, 2.0 * wgt * ei) : T[i];
             double2 nt = make_double2((level == 0 ? 0.0 : 0.5 * old.x) + wgt * sr,
                                       (level == 0 ? 0.0 : 0.5 * old.y) + wgt * si);
+            // (at level 0 `old` is the 2h estimate, not a previous level)
             T[i] = nt;
             const double nr = ks->nR;
             c[i] = make_double2(nr * nt.x, nr * nt.y);
@@ -187,12 +198,10 @@ __global__ void k_quad_sum(const double2* __restrict__ work, double2* __restrict
         if (threadIdx.x == 0) {
             const double diff = sqrt(out[0]), nrm = sqrt(out[1]);
             ks->inner_iters += nthreads;
-            if (level > 0) {
-                // geometric convergence: the error of T_l is about (diff/|T|)^2
-                const double rel = diff / fmax(nrm, 1e-300);
-                ks->inner_err = rel * rel;
-                if (rel <= 1e-7) ks->inner_done = 1;
-            }
+            // geometric convergence: the error of T_l is about (diff/|T|)^2
+            const double rel = diff / fmax(nrm, 1e-300);
+            ks->inner_err = rel * rel;
+            if (rel <= 1e-7) ks->inner_done = 1;
             if (level == QUAD_LEVELS - 1 && !ks->inner_done) ks->status = 6;  // no convergence
         }
     }
@@ -207,7 +216,7 @@ int launch_inner_quadrature(const double2* alpha, const double2* beta, const dou
     k_quad_prep<<<1, 256, 0, st>>>(alpha, beta, gamma, ks);
     for (int level = 0; level < QUAD_LEVELS; ++level) {
         const int nt = quad_threads(level);
-        k_quad_solve<<<(nt + 127) / 128, 128, 0, st>>>(alpha, beta, gamma, ks, work, level, nt);
+        k_quad_solve<<<(nt + 31) / 32, 32, 0, st>>>(alpha, beta, gamma, ks, work, level, nt);
         int blocks = (kmax + 7) / 8;
         if (blocks > 256) blocks = 256;
         k_quad_sum<<<blocks, 256, 0, st>>>(work, T, c, ks, level, nt, partials, counter);
@@ -250,209 +259,223 @@ static NewtonWork newton_layout(double2* work, int kmax) {
     return w;
 }
 
-// S^0 = G (tridiagonal) or H (Hessenberg), row-major with ld = kmax
-__global__ void k_newton_init(const double2* alpha, const double2* beta, const double2* gamma, const double2* H,
-                              int ldH, int tri, KState* ks, NewtonWork w, int kmax) {
-    const int n = ks->kused;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ks->inner_done = (n == 0);
-        ks->inner_iters = 0;
-        ks->inner_method = 1;
-        ks->inner_err = 0.0;
-        w.scal[4] = 0.0;
-        w.bar[0] = 0u;
-        w.bar[1] = 0u;
-        *w.counter = 0u;
-    }
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n), cI = (int)(e % n);
-        double2 v = make_double2(0.0, 0.0);
-        if (tri) {
-            if (r == cI) v = alpha[r];
-            else if (r == cI + 1) v = beta[cI];
-            else if (cI == r + 1) v = gamma[r];
-        } else if (r <= cI + 1) {
-            v = H[r + (size_t)cI * ldH];  // column-major Hessenberg; zero below the subdiagonal
-        }
-        w.S[(size_t)r * kmax + cI] = v;
-    }
-}
-
-// X = S, clear pivot slots
-__global__ void k_newton_prep(KState* ks, NewtonWork w, int kmax) {
-    if (ks->inner_done || ks->status || ks->timeout) return;
-    const int n = ks->kused;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n), cI = (int)(e % n);
-        w.X[(size_t)r * kmax + cI] = w.S[(size_t)r * kmax + cI];
-    }
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n; e += gridDim.x * blockDim.x) {
-        w.slot[e] = 0ull;
-        if (e < n) w.invr[e] = -1;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) w.scal[0] = 0.0;
-}
-
 __device__ __forceinline__ unsigned long long pivkey(double mag, int row) {
     // non-negative float bits are monotone; ties prefer the smaller row
     const float f = (float)mag;
     return ((unsigned long long)__float_as_uint(f) << 32) | (unsigned long long)(0x7fffffff - row);
 }
 
-// In-place Gauss-Jordan inversion of X (n x n) with partial pivoting; rows are
-// owned cyclically by the CTAs; the pivot row chosen at step p is pivrow[p]
-// and invr[pivrow[p]] = p.  Inverse: S^-1[a][b] = X[pivrow[a]][invr[b]].
-// Data another CTA wrote during this kernel is read with L1-bypassing loads.
-__global__ void __launch_bounds__(256) k_gj_invert(KState* ks, NewtonWork w, int kmax) {
+// Roberts' iteration in one cooperative kernel: every iteration copies S to X,
+// inverts X in place by Gauss-Jordan elimination with partial pivoting (rows
+// owned cyclically by the blocks, the pivot row chosen at step p is pivrow[p],
+// S^-1[a][b] = X[pivrow[a]][invr[b]]), then S <- (mu S + S^-1 / mu) / 2 with
+// |det S|^(-1/n) scaling of the first iterates.  All blocks add the per-block
+// partial sums in the same order, so they take the same convergence decision.
+// With `fallback` the kernel only runs when the quadrature did not converge.
+__global__ void __launch_bounds__(256) k_newton_coop(const double2* alpha, const double2* beta,
+                                                     const double2* gamma, const double2* H, int ldH, int tri,
+                                                     KState* ks, NewtonWork w, double2* c, int kmax, int max_it,
+                                                     int fallback) {
     extern __shared__ double2 prow[];
     __shared__ unsigned long long best;
-    if (ks->inner_done || ks->status || ks->timeout) return;
-    const int n = ks->kused;
-    const int G = gridDim.x;
+    __shared__ double red[32];
     const long long max_spins = 20000000;
     int* err = &ks->timeout;
-    if (threadIdx.x == 0) {
-        best = 0ull;
-        for (int r = blockIdx.x; r < n; r += G) {
-            const double2 v = w.X[(size_t)r * kmax];
-            const unsigned long long k = pivkey(hypot(v.x, v.y), r);
-            if (k > best) best = k;
-        }
-        if (best) atomicMax(&w.slot[0], best);
+    // uniform entry decision (all blocks read the same state before anyone writes it)
+    const int st0 = ks->status;
+    const int done0 = ks->inner_done;
+    if (ks->timeout) return;
+    if (fallback) {
+        if (done0 || (st0 != 0 && st0 != 6)) return;
+    } else if (st0) {
+        return;
     }
+    const int n = ks->kused;
+    const int G = gridDim.x;
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
     grid_barrier(w.bar, err, 1, max_spins);
-    for (int p = 0; p < n; ++p) {
-        const unsigned long long key = __ldcg(&w.slot[p]);
-        if (key == 0ull) {  // no pivot candidate (cannot happen for p < n): report, never index
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ks->status, 5);
-            return;
-        }
-        const int r = 0x7fffffff - (int)(key & 0xffffffffull);
-        if (r < 0 || r >= n) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ks->status, 5);
-            return;
-        }
-        // phase A: the owner scales the pivot row in place
-        if (r % G == (int)blockIdx.x) {
-            const double2 pv = w.X[(size_t)r * kmax + p];
-            const cx<double> ip = cdiv(mk(1.0, 0.0), d2c(pv));
-            __syncthreads();
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                if (j == p) w.X[(size_t)r * kmax + j] = c2d(ip);
-                else w.X[(size_t)r * kmax + j] = c2d(ip * d2c(w.X[(size_t)r * kmax + j]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ks->status = 0;
+        ks->inner_done = (n == 0);
+        ks->inner_iters = 0;
+        ks->inner_method = 1;
+        ks->inner_err = 0.0;
+    }
+    if (n == 0) return;
+    // rows are owned by block (row % G) for S and X alike, so a block only reads rows
+    // written by other blocks (the pivot row, the scrambled inverse) through L2
+    for (int r = blockIdx.x; r < n; r += G)
+        for (int cI = threadIdx.x; cI < n; cI += blockDim.x) {
+            double2 v = make_double2(0.0, 0.0);
+            if (tri) {
+                if (r == cI) v = alpha[r];
+                else if (r == cI + 1) v = beta[cI];
+                else if (cI == r + 1) v = gamma[r];
+            } else if (r <= cI + 1) {
+                v = H[r + (size_t)cI * ldH];  // column-major Hessenberg; zero below the subdiagonal
             }
-            if (threadIdx.x == 0) {
-                w.pivrow[p] = r;
-                w.invr[r] = p;
-                const double a = hypot(pv.x, pv.y);
-                if (a == 0.0) atomicExch(&ks->status, 5);
-                atomicAdd(&w.scal[0], log(a));
-            }
+            w.S[(size_t)r * kmax + cI] = v;
         }
-        grid_barrier(w.bar, err, 1, max_spins);
-        if (*(volatile int*)err) return;  // a wait gave up: leave (the host reports OVL_ETIMEOUT)
-        for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(w.X + (size_t)r * kmax + j);
-        if (threadIdx.x == 0) best = 0ull;
-        __syncthreads();
-        const cx<double> pp = d2c(prow[p]);
-        for (int i = blockIdx.x; i < n; i += G) {
-            if (i == r) continue;
-            const cx<double> f = d2c(w.X[(size_t)i * kmax + p]);
-            const bool cand = (p + 1 < n) && (w.invr[i] < 0);  // own row: coherent
-            __syncthreads();  // every thread has read X[i][p] before it is overwritten
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                cx<double> x;
-                if (j == p) x = mk(0.0, 0.0) - f * pp;
-                else x = d2c(w.X[(size_t)i * kmax + j]) - f * d2c(prow[j]);
-                w.X[(size_t)i * kmax + j] = c2d(x);
-                if (j == p + 1 && cand) atomicMax(&best, pivkey(hypot(x.r, x.i), i));
-            }
+    bool fin = false;   // the extra unscaled step after convergence is pending
+    bool conv = false;
+    int it = 0;
+    for (; it < max_it && !conv; ++it) {
+        // X = S, clear the pivot bookkeeping (own rows)
+        for (int r = blockIdx.x; r < n; r += G) {
+            for (int cI = threadIdx.x; cI < n; cI += blockDim.x)
+                w.X[(size_t)r * kmax + cI] = w.S[(size_t)r * kmax + cI];
+            if (threadIdx.x == 0) w.invr[r] = -1;
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && best && p + 1 < n) atomicMax(&w.slot[p + 1], best);
+        for (size_t e = tid; e <= (size_t)n; e += nth) w.slot[e] = 0ull;
+        if (tid == 0) w.scal[0] = 0.0;
         grid_barrier(w.bar, err, 1, max_spins);
         if (*(volatile int*)err) return;
-    }
-}
-
-// S <- (mu S + X'/mu)/2 with X' the unscrambled inverse; convergence bookkeeping.
-__global__ void k_newton_update(KState* ks, NewtonWork w, int kmax, int it) {
-    __shared__ double red[64];
-    if (ks->inner_done || ks->status || ks->timeout) return;
-    const int n = ks->kused;
-    // determinant scaling during the first iterates, unscaled near convergence
-    const bool scale = it < 8 && w.scal[4] == 0.0;
-    const double mu = scale ? exp(-w.scal[0] / n) : 1.0;
-    double part[2] = {0.0, 0.0};
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int a = (int)(e / n), b = (int)(e % n);
-        const cx<double> s = d2c(w.S[(size_t)a * kmax + b]);
-        const cx<double> xi = d2c(w.X[(size_t)w.pivrow[a] * kmax + w.invr[b]]);
-        const cx<double> ns = mk(0.5 * (mu * s.r + xi.r / mu), 0.5 * (mu * s.i + xi.i / mu));
-        w.S[(size_t)a * kmax + b] = c2d(ns);
-        const cx<double> d = ns - s;
-        part[0] += norm2(d);
-        part[1] += norm2(ns);
-    }
-    double out[2];
-    if (grid_sum_last<2>(part, w.partials, w.counter, out, red)) {
+        // candidate pivot of column 0
         if (threadIdx.x == 0) {
-            ks->inner_iters = it + 1;
-            const double diff = sqrt(out[0]), nrm = sqrt(out[1]);
-            ks->inner_err = diff / fmax(nrm, 1e-300);
-            if (w.scal[4] != 0.0) {
-                ks->inner_done = 1;  // the extra unscaled step after convergence
-            } else if (diff <= 1e-7 * nrm) {
-                w.scal[4] = 1.0;
+            best = 0ull;
+            for (int r = blockIdx.x; r < n; r += G) {
+                const double2 v = __ldcg(w.X + (size_t)r * kmax);
+                const unsigned long long k = pivkey(hypot(v.x, v.y), r);
+                if (k > best) best = k;
+            }
+            if (best) atomicMax(&w.slot[0], best);
+        }
+        grid_barrier(w.bar, err, 1, max_spins);
+        if (*(volatile int*)err) return;
+        for (int p = 0; p < n; ++p) {
+            const unsigned long long key = __ldcg(&w.slot[p]);
+            const int r = key ? 0x7fffffff - (int)(key & 0xffffffffull) : -1;
+            if (r < 0 || r >= n) {  // cannot happen for p < n: report, never index
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ks->status, 5);
+                return;
+            }
+            // phase A: the owner scales the pivot row in place
+            if (r % G == (int)blockIdx.x) {
+                const double2 pv = w.X[(size_t)r * kmax + p];
+                const cx<double> ip = cdiv(mk(1.0, 0.0), d2c(pv));
+                __syncthreads();
+                for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                    if (j == p) w.X[(size_t)r * kmax + j] = c2d(ip);
+                    else w.X[(size_t)r * kmax + j] = c2d(ip * d2c(w.X[(size_t)r * kmax + j]));
+                }
+                if (threadIdx.x == 0) {
+                    w.pivrow[p] = r;
+                    w.invr[r] = p;
+                    const double am = hypot(pv.x, pv.y);
+                    if (am == 0.0) atomicExch(&ks->status, 5);
+                    atomicAdd(&w.scal[0], log(am));
+                }
+            }
+            grid_barrier(w.bar, err, 1, max_spins);
+            if (*(volatile int*)err) return;
+            for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(w.X + (size_t)r * kmax + j);
+            if (threadIdx.x == 0) best = 0ull;
+            __syncthreads();
+            const cx<double> pp = d2c(prow[p]);
+            for (int i = blockIdx.x; i < n; i += G) {
+                if (i == r) continue;
+                const cx<double> f = d2c(w.X[(size_t)i * kmax + p]);
+                const bool cand = (p + 1 < n) && (__ldcg(w.invr + i) < 0);
+                __syncthreads();  // every thread has read X[i][p] before it is overwritten
+                for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                    cx<double> x;
+                    if (j == p) x = mk(0.0, 0.0) - f * pp;
+                    else x = d2c(w.X[(size_t)i * kmax + j]) - f * d2c(prow[j]);
+                    w.X[(size_t)i * kmax + j] = c2d(x);
+                    if (j == p + 1 && cand) atomicMax(&best, pivkey(hypot(x.r, x.i), i));
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && best && p + 1 < n) atomicMax(&w.slot[p + 1], best);
+            grid_barrier(w.bar, err, 1, max_spins);
+            if (*(volatile int*)err) return;
+        }
+        // update S and the partial sums of |S_new - S|^2, |S_new|^2
+        const bool scale = it < 8 && !fin;
+        const double mu = scale ? exp(-__ldcg(&w.scal[0]) / n) : 1.0;
+        double d2 = 0.0, n2 = 0.0;
+        for (int aa = blockIdx.x; aa < n; aa += G) {
+            const int pr = __ldcg(w.pivrow + aa);
+            for (int bb = threadIdx.x; bb < n; bb += blockDim.x) {
+                const cx<double> sv = d2c(w.S[(size_t)aa * kmax + bb]);
+                const cx<double> xi = d2c(__ldcg(w.X + (size_t)pr * kmax + __ldcg(w.invr + bb)));
+                const cx<double> ns = mk(0.5 * (mu * sv.r + xi.r / mu), 0.5 * (mu * sv.i + xi.i / mu));
+                w.S[(size_t)aa * kmax + bb] = c2d(ns);
+                d2 += norm2(ns - sv);
+                n2 += norm2(ns);
             }
         }
+        double v2[2] = {d2, n2};
+        block_sum<2>(v2, red);
+        if (threadIdx.x == 0) {
+            w.partials[2 * blockIdx.x] = v2[0];
+            w.partials[2 * blockIdx.x + 1] = v2[1];
+        }
+        grid_barrier(w.bar, err, 1, max_spins);
+        if (*(volatile int*)err) return;
+        __shared__ double sdn[2];
+        {
+            const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+            if (wq < 2) {
+                double acc = 0.0;
+                for (int bk = lane; bk < G; bk += 32) acc += __ldcg(w.partials + 2 * bk + wq);
+                acc = warp_sum(acc);
+                if (lane == 0) sdn[wq] = acc;
+            }
+            __syncthreads();
+        }
+        const double sd = sdn[0], sn = sdn[1];
+        const double diff = sqrt(sd), nrm = sqrt(sn);
+        if (fin) conv = true;                  // the extra unscaled step after convergence
+        else if (diff <= 1e-7 * nrm) fin = true;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ks->inner_iters = it + 1;
+            ks->inner_err = diff / fmax(nrm, 1e-300);
+        }
+        grid_barrier(w.bar, err, 1, max_spins);  // nobody rewrites X or the partials before all read them
+        if (*(volatile int*)err) return;
+    }
+    for (size_t i = tid; i < (size_t)n; i += nth) {
+        const double2 sv = __ldcg(w.S + i * kmax);
+        c[i] = make_double2(ks->nR * sv.x, ks->nR * sv.y);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (conv) ks->inner_done = 1;
+        else ks->status = 6;
     }
 }
 
-__global__ void k_newton_out(KState* ks, NewtonWork w, double2* c, int kmax, int max_it) {
-    const int n = ks->kused;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !ks->inner_done && !ks->status && n > 0) ks->status = 6;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double2 s = w.S[(size_t)i * kmax];
-        c[i] = make_double2(ks->nR * s.x, ks->nR * s.y);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && ks->timeout) ks->status = 7;
+__global__ void k_newton_bar_reset(NewtonWork w) {
+    w.bar[0] = 0u;
+    w.bar[1] = 0u;
 }
 
 int launch_inner_newton(const double2* alpha, const double2* beta, const double2* gamma, const double2* H, int ldH,
                         int tri, KState* ks, double2* c, double2* work, size_t work_elems, int kmax, int num_sms,
-                        cudaStream_t st) {
+                        cudaStream_t st, int fallback) {
     if (inner_work_elems(kmax, 1) > work_elems) return -1;
     NewtonWork w = newton_layout(work, kmax);
     const int max_it = 40;
-    k_newton_init<<<num_sms, 256, 0, st>>>(alpha, beta, gamma, H, ldH, tri, ks, w, kmax);
     const size_t smem = sizeof(double2) * kmax;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_gj_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_newton_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    for (int it = 0; it < max_it; ++it) {
-        k_newton_prep<<<num_sms, 256, 0, st>>>(ks, w, kmax);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(num_sms);
-        cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_gj_invert, ks, w, kmax);
-        if (e != cudaSuccess) return (int)e;
-        k_newton_update<<<num_sms, 256, 0, st>>>(ks, w, kmax, it);
-    }
-    k_newton_out<<<(kmax + 255) / 256, 256, 0, st>>>(ks, w, c, kmax, max_it);
-    return 0;
+    k_newton_bar_reset<<<1, 1, 0, st>>>(w);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(num_sms);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_newton_coop, alpha, beta, gamma, H, ldH, tri, ks, w, c, kmax, max_it,
+                                       fallback);
+    return (int)e;
 }
 
 }  // namespace ovl

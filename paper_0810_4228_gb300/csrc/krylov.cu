@@ -45,6 +45,10 @@ void launch_state_init(KState* ks, cudaStream_t st) { k_state_init<<<1, 1, 0, st
 // ------------------------------------------------------------ 2sL update --
 // v^ = t - alpha_i v_i - gamma_{i-1} v_{i-1},  w^ = s - conj(alpha_i) w_i - conj(beta_{i-1}) w_{i-1}
 // with v_i = sv v~_i etc.; stores v~_{i+1} = v^, w~_{i+1} = w^.
+// With m > 0 the deflated directions are projected out in the same pass
+// (re-projection): v^ -= R p, w^ -= L q with p = L^dag t, q = R^dag s given in
+// pq (R, L in the precision of the vectors).  In exact arithmetic L^dag v_i = 0 and
+// R^dag w_i = 0, so this only removes what rounding brought back.
 template <class T>
 __global__ void __launch_bounds__(256) k_lanczos_step(const T* __restrict__ t, const T* __restrict__ s,
                                                       const T* __restrict__ vi, const T* __restrict__ wi,
@@ -52,10 +56,15 @@ __global__ void __launch_bounds__(256) k_lanczos_step(const T* __restrict__ t, c
                                                       T* __restrict__ vn, T* __restrict__ wn, KState* ks,
                                                       const double2* alpha, double2* beta, double2* gamma,
                                                       double2* vscale, int step, double* partials,
-                                                      unsigned int* counter, size_t n) {
+                                                      unsigned int* counter, size_t n, const T* __restrict__ Rp,
+                                                      const T* __restrict__ Lp, const double2* __restrict__ pq,
+                                                      int m) {
     using R = typename Elem<T>::R;
     __shared__ double red[128];
+    __shared__ cx<R> pqs[2 * 64];
     if (ks->done || ks->status) return;
+    for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) pqs[j] = mk(R(pq[j].x), R(pq[j].y));
+    __syncthreads();
     const cx<double> a = d2c(alpha[step]);
     const cx<double> ca = a * d2c(ks->sv);
     const cx<double> da = conj(a) * d2c(ks->sw);
@@ -73,6 +82,10 @@ __global__ void __launch_bounds__(256) k_lanczos_step(const T* __restrict__ t, c
         if (step > 0) {
             v = v - cg_ * Elem<T>::ld(vim1, e);
             w = w - db_ * Elem<T>::ld(wim1, e);
+        }
+        for (int j = 0; j < m; ++j) {
+            v = v - pqs[j] * Elem<T>::ld(Rp + (size_t)j * n, e);
+            w = w - pqs[m + j] * Elem<T>::ld(Lp + (size_t)j * n, e);
         }
         Elem<T>::st(vn, e, v);
         Elem<T>::st(wn, e, w);
@@ -110,19 +123,22 @@ __global__ void __launch_bounds__(256) k_lanczos_step(const T* __restrict__ t, c
 void launch_lanczos_step(int prec, const void* t, const void* s, const void* vi, const void* wi, const void* vim1,
                          const void* wim1, void* vnext, void* wnext, KState* ks, const double2* alpha, double2* beta,
                          double2* gamma, double2* vscale, int step, int kmax, double* partials,
-                         unsigned int* counter, size_t n, cudaStream_t st) {
+                         unsigned int* counter, size_t n, cudaStream_t st, const void* Rp, const void* Lp,
+                         const double2* pq, int m) {
     (void)kmax;
     const int T = 256, B = grid_for(n, T, 1024);
     if (prec == 0)
         k_lanczos_step<double2><<<B, T, 0, st>>>((const double2*)t, (const double2*)s, (const double2*)vi,
                                                  (const double2*)wi, (const double2*)vim1, (const double2*)wim1,
                                                  (double2*)vnext, (double2*)wnext, ks, alpha, beta, gamma, vscale,
-                                                 step, partials, counter, n);
+                                                 step, partials, counter, n, (const double2*)Rp, (const double2*)Lp,
+                                                 pq, m);
     else
         k_lanczos_step<float2><<<B, T, 0, st>>>((const float2*)t, (const float2*)s, (const float2*)vi,
                                                 (const float2*)wi, (const float2*)vim1, (const float2*)wim1,
                                                 (float2*)vnext, (float2*)wnext, ks, alpha, beta, gamma, vscale,
-                                                step, partials, counter, n);
+                                                step, partials, counter, n, (const float2*)Rp, (const float2*)Lp,
+                                                pq, m);
 }
 
 // ---------------------------------------------------------- many-vector dot --
@@ -183,6 +199,47 @@ __global__ void k_multidot2(const double2* __restrict__ part, int nblk, int nvec
             h[l] = make_double2(re, im);
         }
     }
+}
+
+// FP32 vectors and FP32 basis: products and the per-lane partial sums in FP32, the
+// reduction across lanes and blocks in FP64 (used for re-projection in the FP32 pass,
+// where FP32 accuracy is all that is needed).
+__global__ void __launch_bounds__(256) k_multidot1_f32(const float2* __restrict__ V, size_t ld, int nvec,
+                                                       const float2* __restrict__ x, double2* __restrict__ part,
+                                                       size_t n, const KState* ks) {
+    __shared__ float2 xs[MD_CHUNK];
+    if (ks && (ks->done || ks->status)) return;
+    const size_t base = (size_t)blockIdx.x * MD_CHUNK;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = threadIdx.x; q < MD_CHUNK; q += blockDim.x) {
+        const size_t e = base + q;
+        xs[q] = e < n ? x[e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int l = wid; l < nvec; l += nw) {
+        const float2* Vl = V + (size_t)l * ld;
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int q = lane; q < MD_CHUNK; q += 32) {
+            const size_t e = base + q;
+            if (e < n) {
+                const float2 v = __ldg(Vl + e), xx = xs[q];
+                re += v.x * xx.x + v.y * xx.y;
+                im += v.x * xx.y - v.y * xx.x;
+            }
+        }
+        double dr = warp_sum((double)re), di = warp_sum((double)im);
+        if (lane == 0) part[(size_t)l * gridDim.x + blockIdx.x] = make_double2(dr, di);
+    }
+}
+
+void launch_multidot_f32(const float2* V, size_t ld, int nvec, const float2* x, double2* h, double* partials,
+                         size_t n, cudaStream_t st, const KState* ks) {
+    if (nvec <= 0) return;
+    const int nb = (int)((n + MD_CHUNK - 1) / MD_CHUNK);
+    double2* part = reinterpret_cast<double2*>(partials);
+    k_multidot1_f32<<<nb, 256, 0, st>>>(V, ld, nvec, x, part, n, ks);
+    k_multidot2<<<(nvec + 7) / 8, 256, 0, st>>>(part, nb, nvec, h, 0, ks);
 }
 
 int multidot_blocks(size_t n) { return (int)((n + MD_CHUNK - 1) / MD_CHUNK); }
@@ -364,16 +421,6 @@ void launch_deflate_split(const double2* b, const double2* R, const double2* L, 
 }
 
 // -------------------------------------------------------------- conversions --
-__global__ void k_convert_f64_f32(const double2* __restrict__ x, float2* __restrict__ y, size_t n) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const double2 v = x[e];
-        y[e] = make_float2((float)v.x, (float)v.y);
-    }
-}
-void launch_convert_f64_f32(const double2* x, float2* y, size_t n, cudaStream_t st) {
-    k_convert_f64_f32<<<grid_for(n, 256, 2048), 256, 0, st>>>(x, y, n);
-}
-
 // v_1 = x / |x| (FP64, |x| = nR from the deflation split), optionally y += c[0] * v_1
 __global__ void k_scale_start(const double2* __restrict__ x, double2* __restrict__ v, double2* __restrict__ y,
                               const double2* __restrict__ c, const KState* ks, size_t n) {

@@ -233,6 +233,24 @@ __device__ __forceinline__ void store_spinor(float4* __restrict__ x, int V, int 
     }
 }
 
+// L2-coherent variants (ld.global.cg) for vectors that other blocks of the same
+// kernel write (persistent kernels): the read-only and L1 paths may hold stale lines.
+__device__ __forceinline__ void load_spinor_cg(const double2* x, int V, int i, Spinor<double>& p) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        double2 v = __ldcg(x + (size_t)c * V + i);
+        p.s[c / 3][c % 3] = mk(v.x, v.y);
+    }
+}
+__device__ __forceinline__ void load_spinor_cg(const float4* x, int V, int i, Spinor<float>& p) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float4 v = __ldcg(x + (size_t)c * V + i);
+        p.s[(2 * c) / 3][(2 * c) % 3] = mk(v.x, v.y);
+        p.s[(2 * c + 1) / 3][(2 * c + 1) % 3] = mk(v.z, v.w);
+    }
+}
+
 __device__ __forceinline__ void load_link(const double2* __restrict__ U, int V, int nu, int i, Link<double>& L) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {

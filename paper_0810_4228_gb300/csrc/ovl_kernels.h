@@ -55,6 +55,8 @@ void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim
                          double mu, double kappa, const KState* ks, const double2* alpha, const double2* beta,
                          const double2* gamma, const double2* c, int step, const Geom& g, cudaStream_t st);
 int dslash_grid(const Geom& g, int threads);
+// nvec FP64 device-layout vectors to the FP32 device layout (component pairs in float4)
+void launch_native_f64_to_f32(const double2* x, void* y, const Geom& g, int nvec, cudaStream_t st);
 // stencil thread layout: -1 automatic (by volume), 0 one thread per site, 1 direction split
 void set_dslash_variant(int mode);
 
@@ -62,10 +64,16 @@ void set_dslash_variant(int mode);
 void launch_state_init(KState* ks, cudaStream_t st);
 // 2sL recurrence of Sec. 4, Eq. 4.2 with fused reductions (w^^dag v^, |v^|^2, |w^|^2);
 // the last block sets beta[step], gamma[step], the scales and vscale[step+1].
+// With m > 0, v^ -= R p and w^ -= L q (p = pq[0..m), q = pq[m..2m)) in the same pass (re-projection of
+// the deflated directions); R, L in the vectors' precision, m <= 64.
 void launch_lanczos_step(int prec, const void* t, const void* s, const void* vi, const void* wi,
                          const void* vim1, const void* wim1, void* vnext, void* wnext, KState* ks,
                          const double2* alpha, double2* beta, double2* gamma, double2* vscale, int step, int kmax,
-                         double* partials, unsigned int* counter, size_t n, cudaStream_t st);
+                         double* partials, unsigned int* counter, size_t n, cudaStream_t st,
+                         const void* Rp = nullptr, const void* Lp = nullptr, const double2* pq = nullptr, int m = 0);
+// h[l] = V_l^dag x for FP32 V and x (FP32 products, FP64 reduction)
+void launch_multidot_f32(const float2* V, size_t ld, int nvec, const float2* x, double2* h, double* partials,
+                         size_t n, cudaStream_t st, const KState* ks = nullptr);
 // h[l] (+)= V_l^dag x for l < nvec (V_l = V + l*ld), deterministic two-stage reduction.
 int multidot_blocks(size_t n);
 void launch_multidot(const double2* V, size_t ld, int nvec, const double2* x, double2* h, int acc,
@@ -84,13 +92,23 @@ void launch_arnoldi_normalize(double2* t, const KState* ks, size_t n, cudaStream
 void launch_deflate_split(const double2* b, const double2* R, const double2* L, const double2* lam, int m,
                           const double2* pq, double2* bR, double2* bL, double2* y, KState* ks, double2* vscale,
                           double* partials, unsigned int* counter, size_t n, cudaStream_t st);
-void launch_convert_f64_f32(const double2* x, float2* y, size_t n, cudaStream_t st);
 // v = sv * x; if y: y += c[0] * v
 void launch_scale_start(const double2* x, double2* v, double2* y, const double2* c, const KState* ks, size_t n,
                         cudaStream_t st);
 // y += sum_{l < kused} c_l vscale_l V_l
 void launch_combine(const double2* V, size_t ld, const double2* vscale, const double2* c, const KState* ks,
                     int kmax, double2* y, size_t n, cudaStream_t st);
+
+// ---- persistent.cu
+bool persistent_ok(const Geom& g, int num_sms);
+int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const w[3], KState* ks, double2* alpha,
+                            double2* beta, double2* gamma, const float2* R32, const float2* L32, int m, double mu,
+                            double kappa, int k, double* partials, unsigned int* bar, const Geom& g, int num_sms,
+                            cudaStream_t st);
+int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y, const KState* ks,
+                            const double2* alpha, const double2* beta, const double2* gamma, const double2* c,
+                            double mu, double kappa, unsigned int* bar, int* err, const Geom& g, int num_sms,
+                            cudaStream_t st);
 
 // ---- inner_sign.cu
 // c[0..n) = nR * sgn(G) e_1 for the tridiagonal G (alpha, beta, gamma) of size ks->kused, by the
@@ -100,9 +118,10 @@ int launch_inner_quadrature(const double2* alpha, const double2* beta, const dou
                             unsigned int* counter, cudaStream_t st);
 // c = nR * sgn(M) e_1 by Roberts' iteration (Sec. 2) with determinant scaling, M dense n x n
 // (n = ks->kused) built from the tridiagonal (tri = 1) or taken as the Hessenberg H (ld = ldH).
+// fallback = 1: run only if the quadrature before it did not converge (status 6 is then cleared).
 int launch_inner_newton(const double2* alpha, const double2* beta, const double2* gamma, const double2* H,
                         int ldH, int tri, KState* ks, double2* c, double2* work, size_t work_elems, int kmax,
-                        int num_sms, cudaStream_t st);
+                        int num_sms, cudaStream_t st, int fallback = 0);
 size_t inner_work_elems(int kmax, int method);
 
 }  // namespace ovl

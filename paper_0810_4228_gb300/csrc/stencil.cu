@@ -12,100 +12,11 @@
 // format keeps rows 0 and 1 and rebuilds row 2 = conj(row0 x row1) in registers.
 // The e^{+-mu} factors, kappa and the antiperiodic time phase are applied as
 // real scalars to the projected half spinor, so links stay in SU(3).
-#include "ovl_kernels.h"
+#include <algorithm>
+
+#include "stencil_impl.cuh"
 
 namespace ovl {
-
-template <class R> struct VecT;
-template <> struct VecT<double> { using T = double2; };
-template <> struct VecT<float> { using T = float4; };
-
-template <int LF> struct LinkReal { using R = float; };
-template <> struct LinkReal<LINK_F64> { using R = double; };
-
-template <int LF, class R>
-__device__ __forceinline__ void load_link_any(const void* U, int V, int nu, int i, Link<R>& L) {
-    if constexpr (LF == LINK_F64) load_link((const double2*)U, V, nu, i, L);
-    else if constexpr (LF == LINK_F32_12) load_link12((const float4*)U, V, nu, i, L);
-    else load_link18((const float2*)U, V, nu, i, L);
-}
-
-// Hop coefficients of one input: -kappa * (e^{+-mu} for time) for the forward
-// (T^+) and backward (T^-) hop of each direction.
-template <class R> struct HopCoef { R f[4], b[4]; };
-
-template <class R> __host__ HopCoef<R> make_coef(double mu, double kappa) {
-    HopCoef<R> h;
-    for (int nu = 0; nu < 3; ++nu) h.f[nu] = h.b[nu] = R(-kappa);
-    h.f[3] = R(-kappa * exp(mu));
-    h.b[3] = R(-kappa * exp(-mu));
-    return h;
-}
-
-// Accumulate the eight hops of direction NU for NIN inputs sharing the links.
-template <int NU, int LF, class R, int NIN>
-__device__ __forceinline__ void hops_dir(const Geom& g, const Coord& c, int i, const void* U,
-                                         const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
-                                         const HopCoef<R> (&hc)[NIN]) {
-    Link<R> L;
-    Spinor<R> p;
-    Half<R> h, uh;
-    // forward: (1 + gamma_nu) U_{x,nu} psi(x + nu)
-    {
-        const int f = neighbour(g, c, NU, +1);
-        const R ph = (NU == 3 && c.x[3] == g.L[3] - 1) ? R(g.bc_t) : R(1);
-        load_link_any<LF>(U, g.V, NU, i, L);
-#pragma unroll
-        for (int n = 0; n < NIN; ++n) {
-            load_spinor(x[n], g.V, f, p);
-            project<NU, +1>(p, h);
-            mul_link(L, h, uh);
-            recon_acc<NU, +1>(acc[n], uh, hc[n].f[NU] * ph);
-        }
-    }
-    // backward: (1 - gamma_nu) U_{x-nu,nu}^dag psi(x - nu)
-    {
-        const int b = neighbour(g, c, NU, -1);
-        const R ph = (NU == 3 && c.x[3] == 0) ? R(g.bc_t) : R(1);
-        load_link_any<LF>(U, g.V, NU, b, L);
-#pragma unroll
-        for (int n = 0; n < NIN; ++n) {
-            load_spinor(x[n], g.V, b, p);
-            project<NU, -1>(p, h);
-            mul_link_dag(L, h, uh);
-            recon_acc<NU, -1>(acc[n], uh, hc[n].b[NU] * ph);
-        }
-    }
-}
-
-template <int LF, class R, int NIN>
-__device__ __forceinline__ void apply_site(const Geom& g, int i, const void* U,
-                                           const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
-                                           const HopCoef<R> (&hc)[NIN]) {
-    const Coord c = site_coord(g, i);
-#pragma unroll
-    for (int n = 0; n < NIN; ++n)
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) acc[n].s[s][a] = mk(R(0), R(0));
-    hops_dir<0, LF, R, NIN>(g, c, i, U, x, acc, hc);
-    hops_dir<1, LF, R, NIN>(g, c, i, U, x, acc, hc);
-    hops_dir<2, LF, R, NIN>(g, c, i, U, x, acc, hc);
-    hops_dir<3, LF, R, NIN>(g, c, i, U, x, acc, hc);
-}
-
-// add the diagonal term and apply gamma5 = diag(1, 1, -1, -1)
-template <class R>
-__device__ __forceinline__ void finish_site(Spinor<R>& acc, const Spinor<R>& self, bool g5) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            cx<R> z = acc.s[s][a] + self.s[s][a];
-            acc.s[s][a] = (g5 && s >= 2) ? -z : z;
-        }
-}
 
 __device__ __forceinline__ int site_of_thread(const Geom& g) {
     const int half = blockDim.x >> 1;
@@ -125,23 +36,6 @@ int dslash_grid(const Geom& g, int threads) { return (g.Vh + threads / 2 - 1) / 
 // the fused epilogue.  Four times the threads, a quarter of the dependent
 // loads per thread.
 static constexpr int DS_SITES = 32;
-
-template <class R> __device__ __forceinline__ cx<R> ld_comp(const typename VecT<R>::T* x, int V, int i, int q);
-template <> __device__ __forceinline__ cx<double> ld_comp<double>(const double2* x, int V, int i, int q) {
-    const double2 v = __ldg(x + (size_t)q * V + i);
-    return mk(v.x, v.y);
-}
-template <> __device__ __forceinline__ cx<float> ld_comp<float>(const float4* x, int V, int i, int q) {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(x) + ((size_t)(q >> 1) * V + i) * 2 + (q & 1));
-    return mk(v.x, v.y);
-}
-template <class R> __device__ __forceinline__ void st_comp(typename VecT<R>::T* x, int V, int i, int q, cx<R> z);
-template <> __device__ __forceinline__ void st_comp<double>(double2* x, int V, int i, int q, cx<double> z) {
-    x[(size_t)q * V + i] = make_double2(z.r, z.i);
-}
-template <> __device__ __forceinline__ void st_comp<float>(float4* x, int V, int i, int q, cx<float> z) {
-    reinterpret_cast<float2*>(x)[((size_t)(q >> 1) * V + i) * 2 + (q & 1)] = make_float2(z.r, z.i);
-}
 
 // partial spinors of the four directions: smem[dir][input][site][12]
 template <int LF, int NIN>
@@ -506,6 +400,26 @@ void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim
     const int T = 256, B = dslash_grid(g, T);
     k_dslash_regen<<<B, T, 0, st>>>(U, vi, vim1, vip1, y, make_coef<double>(mu, kappa), ks, alpha, beta, gamma, c,
                                     step, g);
+}
+
+// FP64 device-layout vectors (double2 [12][V]) to the FP32 device layout (float4 [6][V],
+// components 2c, 2c+1 in one float4): nvec consecutive vectors of 12V complex each.
+__global__ void k_native_f64_to_f32(const double2* __restrict__ x, float4* __restrict__ y, int V, int nvec) {
+    const size_t tot = (size_t)nvec * 6 * V;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t vec = e / ((size_t)6 * V);
+        const size_t r = e - vec * 6 * V;
+        const int c2 = (int)(r / V), i = (int)(r - (size_t)c2 * V);
+        const double2* xv = x + vec * 12 * (size_t)V;
+        const double2 a = xv[(size_t)(2 * c2) * V + i], b = xv[(size_t)(2 * c2 + 1) * V + i];
+        y[vec * 6 * (size_t)V + (size_t)c2 * V + i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
+}
+
+void launch_native_f64_to_f32(const double2* x, void* y, const Geom& g, int nvec, cudaStream_t st) {
+    const size_t tot = (size_t)nvec * 6 * g.V;
+    int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+    k_native_f64_to_f32<<<blocks, 256, 0, st>>>(x, (float4*)y, g.V, nvec);
 }
 
 // ---------------------------------------------------------------- layouts --

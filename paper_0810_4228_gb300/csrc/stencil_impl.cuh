@@ -1,0 +1,168 @@
+// Device templates of the Wilson stencil shared by the stencil kernels and the
+// persistent Krylov kernels: hop coefficients, the eight hops of one direction
+// (spin projection, SU(3) multiply, reconstruction; Sec. 1, Eq. 1.2), and
+// component access in the FP64 / FP32 device layouts.
+#pragma once
+
+#include "ovl_kernels.h"
+
+namespace ovl {
+
+template <class R> struct VecT;
+template <> struct VecT<double> { using T = double2; };
+template <> struct VecT<float> { using T = float4; };
+
+template <int LF> struct LinkReal { using R = float; };
+template <> struct LinkReal<LINK_F64> { using R = double; };
+
+template <int LF, class R>
+__device__ __forceinline__ void load_link_any(const void* U, int V, int nu, int i, Link<R>& L) {
+    if constexpr (LF == LINK_F64) load_link((const double2*)U, V, nu, i, L);
+    else if constexpr (LF == LINK_F32_12) load_link12((const float4*)U, V, nu, i, L);
+    else load_link18((const float2*)U, V, nu, i, L);
+}
+
+// Hop coefficients of one input: -kappa * (e^{+-mu} for time) for the forward
+// (T^+) and backward (T^-) hop of each direction.
+template <class R> struct HopCoef { R f[4], b[4]; };
+
+template <class R> __host__ HopCoef<R> make_coef(double mu, double kappa) {
+    HopCoef<R> h;
+    for (int nu = 0; nu < 3; ++nu) h.f[nu] = h.b[nu] = R(-kappa);
+    h.f[3] = R(-kappa * exp(mu));
+    h.b[3] = R(-kappa * exp(-mu));
+    return h;
+}
+
+template <bool CG, class P, class R>
+__device__ __forceinline__ void load_spinor_any(const P* x, int V, int i, Spinor<R>& p) {
+    if constexpr (CG) load_spinor_cg(x, V, i, p);
+    else load_spinor(x, V, i, p);
+}
+
+// The forward hop (1 + gamma_nu) U_{x,nu} psi(x + nu) of direction NU for NIN inputs
+// sharing the link (CG: L2-coherent vector loads, for vectors written by other
+// blocks of the same kernel).
+template <int NU, int LF, class R, int NIN, bool CG = false>
+__device__ __forceinline__ void hop_fwd(const Geom& g, const Coord& c, int i, const void* U,
+                                        const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                        const HopCoef<R> (&hc)[NIN]) {
+    Link<R> L;
+    Spinor<R> p;
+    Half<R> h, uh;
+    const int f = neighbour(g, c, NU, +1);
+    const R ph = (NU == 3 && c.x[3] == g.L[3] - 1) ? R(g.bc_t) : R(1);
+    load_link_any<LF>(U, g.V, NU, i, L);
+#pragma unroll
+    for (int n = 0; n < NIN; ++n) {
+        load_spinor_any<CG>(x[n], g.V, f, p);
+        project<NU, +1>(p, h);
+        mul_link(L, h, uh);
+        recon_acc<NU, +1>(acc[n], uh, hc[n].f[NU] * ph);
+    }
+}
+
+// The backward hop (1 - gamma_nu) U_{x-nu,nu}^dag psi(x - nu).
+template <int NU, int LF, class R, int NIN, bool CG = false>
+__device__ __forceinline__ void hop_bwd(const Geom& g, const Coord& c, int i, const void* U,
+                                        const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                        const HopCoef<R> (&hc)[NIN]) {
+    Link<R> L;
+    Spinor<R> p;
+    Half<R> h, uh;
+    const int b = neighbour(g, c, NU, -1);
+    const R ph = (NU == 3 && c.x[3] == 0) ? R(g.bc_t) : R(1);
+    load_link_any<LF>(U, g.V, NU, b, L);
+#pragma unroll
+    for (int n = 0; n < NIN; ++n) {
+        load_spinor_any<CG>(x[n], g.V, b, p);
+        project<NU, -1>(p, h);
+        mul_link_dag(L, h, uh);
+        recon_acc<NU, -1>(acc[n], uh, hc[n].b[NU] * ph);
+    }
+}
+
+// Both hops of direction NU.
+template <int NU, int LF, class R, int NIN, bool CG = false>
+__device__ __forceinline__ void hops_dir(const Geom& g, const Coord& c, int i, const void* U,
+                                         const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                         const HopCoef<R> (&hc)[NIN]) {
+    hop_fwd<NU, LF, R, NIN, CG>(g, c, i, U, x, acc, hc);
+    hop_bwd<NU, LF, R, NIN, CG>(g, c, i, U, x, acc, hc);
+}
+
+// One of the eight hops, h = 0..7: direction h & 3, forward for h < 4 (uniform per warp).
+template <int LF, class R, int NIN, bool CG = false>
+__device__ __forceinline__ void one_hop(int h, const Geom& g, const Coord& c, int i, const void* U,
+                                        const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                        const HopCoef<R> (&hc)[NIN]) {
+    switch (h) {
+        case 0: hop_fwd<0, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        case 1: hop_fwd<1, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        case 2: hop_fwd<2, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        case 3: hop_fwd<3, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        case 4: hop_bwd<0, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        case 5: hop_bwd<1, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        case 6: hop_bwd<2, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+        default: hop_bwd<3, LF, R, NIN, CG>(g, c, i, U, x, acc, hc); break;
+    }
+}
+
+template <int LF, class R, int NIN>
+__device__ __forceinline__ void apply_site(const Geom& g, int i, const void* U,
+                                           const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                           const HopCoef<R> (&hc)[NIN]) {
+    const Coord c = site_coord(g, i);
+#pragma unroll
+    for (int n = 0; n < NIN; ++n)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[n].s[s][a] = mk(R(0), R(0));
+    hops_dir<0, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<1, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<2, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<3, LF, R, NIN>(g, c, i, U, x, acc, hc);
+}
+
+// add the diagonal term and apply gamma5 = diag(1, 1, -1, -1)
+template <class R>
+__device__ __forceinline__ void finish_site(Spinor<R>& acc, const Spinor<R>& self, bool g5) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<R> z = acc.s[s][a] + self.s[s][a];
+            acc.s[s][a] = (g5 && s >= 2) ? -z : z;
+        }
+}
+
+template <class R> __device__ __forceinline__ cx<R> ld_comp(const typename VecT<R>::T* x, int V, int i, int q);
+template <> __device__ inline cx<double> ld_comp<double>(const double2* x, int V, int i, int q) {
+    const double2 v = __ldg(x + (size_t)q * V + i);
+    return mk(v.x, v.y);
+}
+template <> __device__ inline cx<float> ld_comp<float>(const float4* x, int V, int i, int q) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(x) + ((size_t)(q >> 1) * V + i) * 2 + (q & 1));
+    return mk(v.x, v.y);
+}
+template <class R> __device__ __forceinline__ void st_comp(typename VecT<R>::T* x, int V, int i, int q, cx<R> z);
+// L2-coherent component load
+template <class R> __device__ __forceinline__ cx<R> ld_comp_cg(const typename VecT<R>::T* x, int V, int i, int q);
+template <> __device__ inline cx<double> ld_comp_cg<double>(const double2* x, int V, int i, int q) {
+    const double2 v = __ldcg(x + (size_t)q * V + i);
+    return mk(v.x, v.y);
+}
+template <> __device__ inline cx<float> ld_comp_cg<float>(const float4* x, int V, int i, int q) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(x) + ((size_t)(q >> 1) * V + i) * 2 + (q & 1));
+    return mk(v.x, v.y);
+}
+template <> __device__ inline void st_comp<double>(double2* x, int V, int i, int q, cx<double> z) {
+    x[(size_t)q * V + i] = make_double2(z.r, z.i);
+}
+template <> __device__ inline void st_comp<float>(float4* x, int V, int i, int q, cx<float> z) {
+    reinterpret_cast<float2*>(x)[((size_t)(q >> 1) * V + i) * 2 + (q & 1)] = make_float2(z.r, z.i);
+}
+
+
+}  // namespace ovl

@@ -25,7 +25,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ESINGULAR, ENOCONV, ETIMEOUT, ESTATE = ra
 ARNOLDI, LANCZOS2 = 0, 1
 GAMMA5, DAGGER, NATIVE, HOST, F32, F32_FULL = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 OVERLAP, MIXED, TWO_PASS, INNER_NEWTON, NO_GRAPH, PROFILE = 0x100, 0x200, 0x400, 0x1000, 0x2000, 0x4000
-STENCIL_SITE, STENCIL_SPLIT = 0x10000, 0x20000
+STENCIL_SITE, STENCIL_SPLIT, REPROJ, STEPWISE = 0x10000, 0x20000, 0x8000, 0x40000
 
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EBREAKDOWN",
              ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
@@ -33,7 +33,7 @@ _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EB
 EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
            "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
-           "ovl_profile_get", "ovl_profile_reset"]
+           "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad"]
 
 
 class OvlError(RuntimeError):
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "ovl_profile_get": (I, [P, ctypes.POINTER(KStat), I, ctypes.POINTER(I)]),
         "ovl_get_deflation": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D), P, P, I]),
         "ovl_deflation_eigs": (I, [P, D, D, I, I, D, I, I, ctypes.POINTER(EigInfo)]),
+        "ovl_dw_grad": (I, [P, D, D, P, P, P, ctypes.POINTER(D), I]),
         "ovl_profile_reset": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -216,6 +217,13 @@ class Context:
         device tensor alpha_dev (2 float64) and nothing is synchronised."""
         self._check(self._lib.ovl_apply_pair_noalloc(self._h, mu, kappa, prec, _ptr(v), _ptr(w), _ptr(t), _ptr(s),
                                                       _ptr(alpha_dev)))
+
+    def dw_grad(self, mu: float, kappa: float, x, g, grad_U=None):
+        """(grad_U, grad_mu) of a real l(y), y = A x, from g = dl/dy*; canonical device tensors."""
+        gm = ctypes.c_double()
+        self._check(self._lib.ovl_dw_grad(self._h, mu, kappa, _ptr(x), _ptr(g),
+                                          _ptr(grad_U) if grad_U is not None else None, ctypes.byref(gm), 0))
+        return grad_U, gm.value
 
     def set_deflation(self, mu: float, kappa: float, lam, R, L):
         """Install m critical eigenpairs: lam (m,) complex, R and L (m, 12V) complex128."""

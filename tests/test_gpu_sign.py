@@ -147,12 +147,15 @@ def test_zero_source(ovl, c4):
     assert np.abs(y).max() == 0.0
 
 
-@pytest.mark.parametrize("flags,tol", [("TWO_PASS", 1e-10), ("MIXED", 1e-8)])
+@pytest.mark.parametrize("flags,tol", [("TWO_PASS", 1e-10), ("MIXED", 1e-8), ("MIXED|STEPWISE", 1e-8)])
 def test_two_pass(ovl, c4, flags, tol):
     """Two-pass 2sL (Sec. 5): FP64 or FP32 pass 1 for the coefficients, FP64
-    regeneration of the basis in pass 2."""
+    regeneration of the basis in pass 2 (persistent kernels, or one kernel per step)."""
     ctx = _ctx(ovl, c4["dims"], c4["U"])
-    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 400, c4["mu"], c4["b"], flags=getattr(ovl, flags))
+    fl = 0
+    for f in flags.split("|"):
+        fl |= getattr(ovl, f)
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 400, c4["mu"], c4["b"], flags=fl)
     assert info["status"] == 0
     assert rel(y, c4["ref"]) < tol
 
@@ -178,6 +181,11 @@ def test_repeat_is_deterministic(ovl, c4):
     y1, _ = _solve(ovl, ctx, ovl.LANCZOS2, 150, c4["mu"], c4["b"], flags=ovl.MIXED)
     y2, _ = _solve(ovl, ctx, ovl.LANCZOS2, 150, c4["mu"], c4["b"], flags=ovl.MIXED)
     assert np.array_equal(y1, y2)
+    # the persistent and the per-step kernels run the same FP32 recurrence (their
+    # reductions add in different orders, so compare before rounding is amplified)
+    y4, _ = _solve(ovl, ctx, ovl.LANCZOS2, 30, c4["mu"], c4["b"], flags=ovl.MIXED)
+    y3, _ = _solve(ovl, ctx, ovl.LANCZOS2, 30, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.STEPWISE)
+    assert rel(y3, y4) < 1e-6
 
 
 @pytest.mark.parametrize("gauge", [False, True])
@@ -222,3 +230,51 @@ def test_small_ragged_lattices(ovl, dims):
     k = 40
     yl, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, 0.3, b)
     assert rel(yl, K.sign_lanczos2(A.dot, Ad.dot, b, k)) < 1e-8
+
+
+@pytest.mark.parametrize("k", [5, 20, 60])
+def test_mixed_pass1_matches_fp64(ovl, c4, k):
+    """Before loss of bi-orthogonality the FP32 pass 1 runs the same process as the
+    FP64 one (same start vectors in the FP32 device layout): the two-pass mixed
+    result equals the FP64 result to FP32 rounding."""
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y64, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, c4["mu"], c4["b"])
+    y32, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, c4["mu"], c4["b"], flags=ovl.MIXED)
+    assert rel(y32, y64) < 1e-5
+
+
+def test_mixed_deflated_matches_dense(ovl, c4):
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:20]
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(X[:, idx].T.copy()), torch_c128(Xi[idx, :].conj().copy()))
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 300, c4["mu"], c4["b"], flags=ovl.MIXED)
+    assert info["status"] == 0
+    assert rel(y, c4["ref"]) < 1e-8
+
+
+def test_mixed_deflated_reprojection_option(ovl, c4):
+    """Re-projection of the deflated directions in the FP32 pass (optional): the
+    result stays within the FP32 bound of the projected operator."""
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:20]
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(X[:, idx].T.copy()), torch_c128(Xi[idx, :].conj().copy()))
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 300, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.REPROJ)
+    assert rel(y, c4["ref"]) < 1e-6
+
+
+def test_newton_fallback_on_hard_spectrum(ovl):
+    """Ritz values close to the imaginary axis (2^3 x 4, eps = 1.0, min |Re lambda| ~ 0.03):
+    whatever inner method finishes, the result matches the dense sign."""
+    from oracle import sign as S
+    dims = (2, 2, 2, 4)
+    U = synth.gauge_field(dims, 1.0, 31)
+    A = W.a_operator(U, dims, 0.3, KAPPA)
+    b = synth.gaussian_source(dims, 7)
+    ref = S.sign_spectral(A.toarray()) @ b
+    ctx = _ctx(ovl, dims, U)
+    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 300, 0.3, b)
+    yn, infon = _solve(ovl, ctx, ovl.LANCZOS2, 300, 0.3, b, flags=ovl.INNER_NEWTON)
+    assert rel(yn, y) < 1e-9
+    assert rel(y, ref) < 1e-5
