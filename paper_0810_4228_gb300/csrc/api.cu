@@ -366,8 +366,9 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
             int lr = 0;
             prof(c, KC_PASS2, [&] {
                 double2* rr[3] = {c->R64[0], c->R64[1], c->R64[2]};
-                lr = ovl::launch_pass2_persistent(c->U64, rr, c->y64, ks, c->alpha, c->beta, c->gamma, c->cvec, mu,
-                                                  kappa, c->bar, &ks->timeout, g, c->num_sms, st);
+                lr = ovl::launch_pass2_persistent(c->U64, rr, c->y64, ks, c->alpha, c->beta, c->gamma, c->cvec,
+                                                  c->H, c->kcap, mu, kappa, c->bar, &ks->timeout, g, c->num_sms,
+                                                  st);
             });
             if (lr) return fail(c, OVL_ECUDA, std::string("persistent pass 2 launch: ") +
                                                    cudaGetErrorString((cudaError_t)lr));

@@ -105,10 +105,11 @@ int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const
                             double2* beta, double2* gamma, const float2* R32, const float2* L32, int m, double mu,
                             double kappa, int k, double* partials, unsigned int* bar, const Geom& g, int num_sms,
                             cudaStream_t st);
+// coef_work: 4 (kmax + 1) double2 of scratch for the per-step regeneration coefficients
 int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y, const KState* ks,
                             const double2* alpha, const double2* beta, const double2* gamma, const double2* c,
-                            double mu, double kappa, unsigned int* bar, int* err, const Geom& g, int num_sms,
-                            cudaStream_t st);
+                            double2* coef_work, int kmax, double mu, double kappa, unsigned int* bar, int* err,
+                            const Geom& g, int num_sms, cudaStream_t st);
 
 // ---- inner_sign.cu
 // c[0..n) = nR * sgn(G) e_1 for the tridiagonal G (alpha, beta, gamma) of size ks->kused, by the
