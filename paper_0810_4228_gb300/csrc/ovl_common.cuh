@@ -366,4 +366,27 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err, int co
     __syncthreads();
 }
 
+// Bounded grid barrier with a monotonic arrival counter (zeroed before the launch): the n-th
+// barrier of a launch waits for G n arrivals, so no reset and no second atomic are needed.
+// The arrival is a GPU-scope release and the poll a GPU-scope acquire: the block's writes
+// before the barrier (ordered to thread 0 by __syncthreads) are visible to every block after it.
+__device__ __forceinline__ void grid_barrier_mono(unsigned int* ctr, unsigned int target, int* err, int code,
+                                                  long long max_spins) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
+        long long spins = 0;
+        while (true) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (++spins > max_spins) {
+                atomicExch(err, code);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace ovl

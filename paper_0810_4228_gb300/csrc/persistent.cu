@@ -18,7 +18,8 @@
 // scalars are FP64 and formed by a single warp -- GB300's FP64 pipe is narrow,
 // so scalar algebra repeated by every warp would cost more than the stencil.  Every block adds the per-block partials
 // in the same fixed order, so all blocks hold bit-identical coefficients.
-// Pass 2 regenerates the basis in FP64 with one barrier per step.
+// Pass 2 regenerates the basis in FP64 with one barrier per step.  The barriers
+// count arrivals on a counter zeroed before each launch.
 #include <algorithm>
 
 #include "stencil_impl.cuh"
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(32 * PW1) k_pass1_persistent(P1Args a) {
     cx<double> beta_prev = mk(0.0, 0.0), gamma_prev = mk(0.0, 0.0);
     double anorm2 = ks->anorm * ks->anorm;
     int kused = 0, bd = -1;
+    unsigned int nbar = 0;
 
     // own-site start vectors into slot 0, zero previous vectors
     {
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(32 * PW1) k_pass1_persistent(P1Args a) {
             // p_j at 4 + 2j, q_j at 4 + 2m + 2j: reduce into the block's slots 4 + 4j.. and move
             block_reduce_ff<4, PW1>(pr, redf, a.partA + (size_t)blockIdx.x * NA + 4 + 4 * j);
         }
-        grid_barrier(a.bar, err, 1, PSPIN);
+        grid_barrier_mono(a.bar, (unsigned)G * (++nbar), err, 1, PSPIN);
         if (*(volatile int*)err) return;
         // ---- scalars (warp 0): alpha_i, the recurrence coefficients of phase C
         if (wid == 0) {
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(32 * PW1) k_pass1_persistent(P1Args a) {
             }
         }
         block_reduce_ff<4, PW1>(pc, redf, a.partC + (size_t)blockIdx.x * 4);
-        grid_barrier(a.bar, err, 1, PSPIN);
+        grid_barrier_mono(a.bar, (unsigned)G * (++nbar), err, 1, PSPIN);
         if (*(volatile int*)err) return;
         if (wid == 0) {
             warp_sum_partials(a.partC, 4, 4, G, oc);
@@ -423,8 +425,9 @@ struct RegenCoef {
 };
 
 __global__ void k_pass2_coef(const KState* ks, const double2* alpha, const double2* beta, const double2* gamma,
-                             const double2* c, RegenCoef* out, int kmax) {
+                             const double2* c, RegenCoef* out, int kmax, unsigned int* bar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) bar[0] = 0u;  // arrival counter of the pass-2 barriers
     if (i + 1 >= kmax || i + 1 >= ks->kused) return;
     const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(beta[i]));
     RegenCoef r;
@@ -479,6 +482,7 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
     __syncthreads();
     RegenCoef cf;
     if (kused > 1) cf = a.cf[0];
+    unsigned int nbar = 0;
     for (int i = 0; i + 1 < kused; ++i) {
         const int cur = i & 1, prv = cur ^ 1;
         const double2* vi = a.v[i % 3];
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
             __syncthreads();
         }
         if (i + 2 < kused) {
-            grid_barrier(a.bar, a.err, 1, PSPIN);
+            grid_barrier_mono(a.bar, (unsigned)G * (++nbar), a.err, 1, PSPIN);
             if (*(volatile int*)a.err) return;
         }
     }
@@ -609,7 +613,7 @@ int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y,
                             double2* coef_work, int kmax, double mu, double kappa, unsigned int* bar, int* err,
                             const Geom& g, int num_sms, cudaStream_t st) {
     RegenCoef* cfw = reinterpret_cast<RegenCoef*>(coef_work);
-    k_pass2_coef<<<(kmax + 127) / 128, 128, 0, st>>>(ks, alpha, beta, gamma, c, cfw, kmax);
+    k_pass2_coef<<<(kmax + 127) / 128, 128, 0, st>>>(ks, alpha, beta, gamma, c, cfw, kmax, bar);
     P2Args a;
     a.U = U64;
     for (int q = 0; q < 3; ++q) a.v[q] = v[q];
