@@ -164,6 +164,26 @@ int ovl_apply_pair_noalloc(ovl_ctx* ctx, double mu, double kappa, int prec,
 int ovl_dw_grad(ovl_ctx* ctx, double mu, double kappa, const void* x, const void* g, void* grad_U,
                 double* grad_mu, int flags);
 
+/* Derivatives of l = Re <g, y>, y = sgn(A) b (Sec. 1, Eq. 1.3), A = gamma5 D_w(mu; U) (Eq. 1.2),
+ * for the upstream gradient g = g_y in PyTorch's convention (dl = Re <g_z, dz> for every
+ * complex z).  The derivative of the exact function: with the resolvent form of sgn,
+ * dl/dtheta = -(1/pi) int e^u sum_+- Re <R_+-^dag g, (dA/dtheta) R_+- b> du, R_+- = (A +- i e^u)^-1,
+ * and one k-step FP64 two-sided Lanczos process (Sec. 4, Eq. 4.2) started from v_1 = b / |b|,
+ * w_1 = g / conj(g^dag v_1) approximates R b in K_k(A, b) and R^dag g in K_k(A^dag, g).
+ * The installed deflation set is not used (its eigenvectors would depend on U and mu).
+ * Writes, each may be NULL:
+ *   y       sgn(A) b                           (canonical complex128 [V][12], device)
+ *   grad_U  g_U                                (canonical complex128 [V][4][3][3], device)
+ *   grad_mu dl/dmu                             (host double)
+ *   grad_b  g_b = sgn(A)^dag g                 (canonical complex128 [V][12], device)
+ * b, g: canonical complex128 device vectors.  The two Krylov bases (k + 1 vectors each) and
+ * k more vectors stay in device memory for the call.  Errors as ovl_sign_krylov;
+ * OVL_EBREAKDOWN also if g^dag b = 0 (the process cannot start); OVL_ENOCONV if the
+ * quadrature of the k x k part does not settle.  flags: 0 (reserved).  info: as
+ * ovl_sign_krylov (may be NULL).  Synchronises the context's stream. */
+int ovl_sign_grad(ovl_ctx* ctx, int k, double mu, double kappa, const void* b, const void* g, void* y,
+                  void* grad_U, double* grad_mu, void* grad_b, int flags, ovl_info* info);
+
 /* Convert a canonical complex128 vector (device) into the device layout (prec 0 or 1)
  * and back. */
 int ovl_pack(ovl_ctx* ctx, const void* canon, void* native, int prec);

@@ -457,6 +457,7 @@ int ovl_destroy(ovl_ctx* c) {
     dfree(&c->t32), dfree(&c->s32), dfree(&c->ks), dfree(&c->counter), dfree(&c->bar), dfree(&c->stage_in),
         dfree(&c->stage_out);
     dfree(&c->nat_a), dfree(&c->nat_b), dfree(&c->pq);
+    dfree(&c->gwork), dfree(&c->tadj);
     for (int i = 0; i < 3; ++i) dfree(&c->W64[i]), dfree(&c->R64[i]), dfree(&c->v32[i]), dfree(&c->w32[i]);
     delete c;
     return OVL_OK;

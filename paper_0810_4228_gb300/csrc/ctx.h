@@ -83,6 +83,13 @@ struct ovl_ctx {
 
     ovl_priv::GraphEntry graph;
 
+    // gradient of the Krylov sign (grad_krylov.cu): basis checkpoints and adjoint vectors, and the
+    // scratch of the small-problem adjoint
+    void* gwork = nullptr;
+    size_t gwork_bytes = 0;
+    double2* tadj = nullptr;
+    size_t tadj_elems = 0;
+
     // per-kernel profile (OVL_PROFILE)
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -100,6 +107,8 @@ int ensure_base(ovl_ctx* c);
 int ensure_solve(ovl_ctx* c, int k);
 void drop_graph(ovl_ctx* c);
 bool host_inverse(std::vector<std::complex<double>>& A, int m);
+// queue one solve of the C ABI's sign_krylov (b already packed into c->b64)
+int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int flags);
 // install m eigenpairs already in the device layout (R, L: m device vectors each, lam: host)
 int install_deflation(ovl_ctx* c, double mu, double kappa, int m, const double* lambda, const double2* Rdev,
                       const double2* Ldev);

@@ -33,7 +33,7 @@ _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EB
 EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
            "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
-           "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad"]
+           "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad"]
 
 
 class OvlError(RuntimeError):
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "ovl_get_deflation": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D), P, P, I]),
         "ovl_deflation_eigs": (I, [P, D, D, I, I, D, I, I, ctypes.POINTER(EigInfo)]),
         "ovl_dw_grad": (I, [P, D, D, P, P, P, ctypes.POINTER(D), I]),
+        "ovl_sign_grad": (I, [P, I, D, D, P, P, P, P, ctypes.POINTER(D), P, I, ctypes.POINTER(Info)]),
         "ovl_profile_reset": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -224,6 +225,19 @@ class Context:
         self._check(self._lib.ovl_dw_grad(self._h, mu, kappa, _ptr(x), _ptr(g),
                                           _ptr(grad_U) if grad_U is not None else None, ctypes.byref(gm), 0))
         return grad_U, gm.value
+
+    def sign_grad(self, k: int, mu: float, kappa: float, b, g, y=None, grad_U=None, grad_b=None):
+        """Derivatives of Re <g, sgn(A) b> with respect to mu, U and b (k-step FP64 two-sided Lanczos
+        from (b, g), no deflation); canonical device tensors.  Returns (grad_mu, info); y, grad_U,
+        grad_b are written when given."""
+        gm = ctypes.c_double()
+        info = Info()
+        r = self._lib.ovl_sign_grad(self._h, int(k), mu, kappa, _ptr(b), _ptr(g),
+                                    _ptr(y) if y is not None else None,
+                                    _ptr(grad_U) if grad_U is not None else None, ctypes.byref(gm),
+                                    _ptr(grad_b) if grad_b is not None else None, 0, ctypes.byref(info))
+        self._check(r)
+        return gm.value, info.as_dict()
 
     def set_deflation(self, mu: float, kappa: float, lam, R, L):
         """Install m critical eigenpairs: lam (m,) complex, R and L (m, 12V) complex128."""
