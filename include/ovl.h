@@ -164,6 +164,30 @@ int ovl_apply_pair_noalloc(ovl_ctx* ctx, double mu, double kappa, int prec,
 int ovl_dw_grad(ovl_ctx* ctx, double mu, double kappa, const void* x, const void* g, void* grad_U,
                 double* grad_mu, int flags);
 
+/* ---- batched solves (one launch sequence for many right-hand sides and configurations) ----
+ * A batch groups nctx contexts (each with its own lattice size, gauge field and installed
+ * deflation set) and nrhs[j] right-hand sides for context j.  Every sequence (context, rhs)
+ * runs the two-sided Lanczos solve of ovl_sign_krylov (Sec. 4, Eq. 4.2-4.5), but each batched
+ * kernel covers all sequences in one launch, with per-sequence reductions, and the whole solve
+ * is captured as one CUDA graph (re-captured when k, mu, kappa or the precision change).
+ * Precision: OVL_MIXED = FP32 pass 1 and FP64 regeneration pass (Sec. 5); otherwise FP64 one
+ * pass with the basis stored.  The contexts must share one stream (the first's); the batch
+ * owns its workspace (for n = 12 V summed over sequences: about 8 n FP32 + 7 n FP64 complex
+ * values mixed, (k + 9) n FP64 otherwise). */
+typedef struct ovl_batch ovl_batch;
+int ovl_batch_create(ovl_batch** out, ovl_ctx* const* ctxs, int nctx, const int* nrhs);
+int ovl_batch_destroy(ovl_batch* batch);
+const char* ovl_batch_last_error(const ovl_batch* batch);
+/* b[j], out[j]: nrhs[j] canonical complex128 vectors of context j, one after another (device,
+ * or host with OVL_HOST).  flags: OVL_MIXED, OVL_OVERLAP, OVL_HOST, OVL_NO_GRAPH.  info: one
+ * entry per sequence in (context, rhs) order (may be NULL).  Returns the first failing
+ * sequence's status (the others' results are still written). */
+int ovl_batch_solve(ovl_batch* batch, int k, double mu, double kappa, const void* const* b, void* const* out,
+                    int flags, ovl_info* info);
+/* create + solve + destroy (no graph reuse); errors are reported on ctxs[0]. */
+int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int k, double mu, double kappa,
+                            const void* const* b, void* const* out, int flags, ovl_info* info);
+
 /* Derivatives of l = Re <g, y>, y = sgn(A) b (Sec. 1, Eq. 1.3), A = gamma5 D_w(mu; U) (Eq. 1.2),
  * for the upstream gradient g = g_y in PyTorch's convention (dl = Re <g_z, dz> for every
  * complex z).  The derivative of the exact function: with the resolvent form of sgn,

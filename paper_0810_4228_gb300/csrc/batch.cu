@@ -1,0 +1,713 @@
+// Batched two-sided Lanczos solves: several right-hand sides on several gauge
+// configurations (lattices of different sizes) in one sequence of launches,
+// captured once as a CUDA graph.
+//
+// A sequence is one (configuration, right-hand side) pair.  Each batched kernel
+// covers every sequence in one launch: its blocks are a concatenation of
+// per-sequence block ranges (a device table maps a block to its sequence), so
+// lattices of any size share the GPU in every step.  Reductions are per
+// sequence: block partials and a ticket counter of their own, the last block
+// of a sequence sums its partials in a fixed order and sets the coefficients
+// (Sec. 4, Eq. 4.2).  A finished sequence (lucky breakdown, k reached) skips
+// the rest of its work uniformly.  The links of a configuration are read by all
+// of its right-hand sides in the same step and stay in L2 between them.
+//
+// Mixed precision (OVL_MIXED): pass 1 in FP32 with 12-real links (in-block sums
+// of exact FP32 products in compensated pairs), pass 2 regenerates the basis
+// in FP64 from the pass-1 coefficients and accumulates y (Sec. 5).  Otherwise
+// FP64 throughout: one pass with the basis stored and the combination
+// y = sum_i c_i v_i at the end.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "stencil_impl.cuh"
+
+namespace ovl {
+
+struct BSeq {
+    Geom g;
+    size_t n;                 // 12 V
+    const void* U;            // pass-1 links: FP32-12 (float4) or FP64 (double2)
+    const double2* U64;       // FP64 links (regeneration)
+    void* v[3];               // pass-1 ring (FP32 float4 pairs or FP64); unused with a stored basis
+    void* w[3];
+    void* t;
+    void* s;
+    double2* V;               // FP64 one-pass: stored basis, k + 1 vectors (else null)
+    double2* r[3];            // FP64 regeneration ring (two-pass)
+    double2* y;
+    KState* ks;
+    double2* alpha;
+    double2* beta;
+    double2* gamma;
+    double2* cvec;
+    double2* vscale;
+    double2* part;            // [nblk][4] block partials of the batched kernels
+    unsigned int* cnt;        // ticket of this sequence
+    int blk0, nblk;           // block range in the batched launches (blocks of BT sites)
+};
+
+namespace {
+
+constexpr int BT = 128;  // sites per block
+
+template <class R> struct BVec;
+template <> struct BVec<float> { using T = float4; };
+template <> struct BVec<double> { using T = double2; };
+
+// in-block accumulators: compensated FP32 pairs for FP32 data, plain FP64 for FP64 data
+struct AccF {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void acc_add(AccF& a, float p, float pe) {
+    const float s = __fadd_rn(a.hi, p);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ void acc_prod(AccF& a, float x, float y, float sg = 1.f) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    acc_add(a, sg * p, sg * pe);
+}
+__device__ __forceinline__ double acc_val(const AccF& a) { return (double)a.hi + (double)a.lo; }
+struct AccD {
+    double v = 0.0;
+};
+__device__ __forceinline__ void acc_prod(AccD& a, double x, double y, double sg = 1.0) { a.v += sg * x * y; }
+__device__ __forceinline__ double acc_val(const AccD& a) { return a.v; }
+
+template <class R> struct AccOf;
+template <> struct AccOf<float> { using T = AccF; };
+template <> struct AccOf<double> { using T = AccD; };
+
+template <class A, class R>
+__device__ __forceinline__ void acc_cdot(A* a, cx<R> x, cx<R> y) {  // += conj(x) y
+    acc_prod(a[0], x.r, y.r);
+    acc_prod(a[0], x.i, y.i);
+    acc_prod(a[1], x.r, y.i);
+    acc_prod(a[1], x.i, y.r, R(-1));
+}
+template <class A, class R>
+__device__ __forceinline__ void acc_norm2(A& a, cx<R> x) {
+    acc_prod(a, x.r, x.r);
+    acc_prod(a, x.i, x.i);
+}
+
+// Per-sequence reduction of NQ values: block sums into part[local] (FP64), then the last block of
+// the sequence (ticket) adds the partials of its nblk blocks in a fixed order.  Returns true in the
+// last block; out[] is valid in thread 0 there.
+template <int NQ>
+__device__ bool seq_reduce(const double (&v)[NQ], double2* part, unsigned int* cnt, int local, int nblk,
+                           double (&out)[NQ]) {
+    __shared__ double red[NQ][BT / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const double x = warp_sum(v[q]);
+        if (lane == 0) red[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < BT / 32; ++w) s += red[q][w];
+            part[(size_t)local * 4 + q] = make_double2(s, 0.0);
+        }
+        __threadfence();
+        const unsigned int t = atomicAdd(cnt, 1u);
+        last = (t == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        acc[q] = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += BT) acc[q] += __ldcg(&part[(size_t)b * 4 + q].x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const double x = warp_sum(acc[q]);
+        if (lane == 0) red[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < BT / 32; ++w) s += red[q][w];
+            out[q] = s;
+        }
+        *cnt = 0u;
+    }
+    return true;
+}
+
+template <class R>
+__device__ __forceinline__ void* vslot(const BSeq& q, int j, bool wvec) {
+    if (!wvec && q.V) return q.V + (size_t)j * q.n;
+    return wvec ? q.w[j % 3] : q.v[j % 3];
+}
+
+// t = sv A v~_i, s = sw A^dag w~_i at every site of every running sequence; alpha_i = w_i^dag t
+template <int LF, class R>
+__global__ void __launch_bounds__(BT) k_b_pair(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
+                                               int klast, HopCoef<R> hv, HopCoef<R> hw) {
+    using VT = typename BVec<R>::T;
+    const BSeq& q = S[bseq[blockIdx.x]];
+    KState* ks = q.ks;
+    if (ks->done || ks->status) return;
+    const int local = blockIdx.x - q.blk0;
+    const int site = local * BT + threadIdx.x;
+    const cx<R> sv = mk((R)ks->sv.x, (R)ks->sv.y), sw = mk((R)ks->sw.x, (R)ks->sw.y);
+    const VT* vi = (const VT*)vslot<R>(q, i, false);
+    const VT* wi = (const VT*)vslot<R>(q, i, true);
+    typename AccOf<R>::T a[3];
+    if (site < q.g.V) {
+        const VT* const xs[2] = {vi, wi};
+        const HopCoef<R> hcs[2] = {hv, hw};
+        Spinor<R> acc[2], self[2];
+        apply_site<LF, R, 2>(q.g, site, q.U, xs, acc, hcs);
+        load_spinor(vi, q.g.V, site, self[0]);
+        load_spinor(wi, q.g.V, site, self[1]);
+        finish_site(acc[0], self[0], true);
+        finish_site(acc[1], self[1], true);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[0].s[sp][c] = sv * acc[0].s[sp][c];
+                acc[1].s[sp][c] = sw * acc[1].s[sp][c];
+                acc_cdot(a, self[1].s[sp][c], acc[0].s[sp][c]);
+                acc_norm2(a[2], acc[0].s[sp][c]);
+            }
+        store_spinor((VT*)q.t, q.g.V, site, acc[0]);
+        store_spinor((VT*)q.s, q.g.V, site, acc[1]);
+    }
+    const double v3[3] = {acc_val(a[0]), acc_val(a[1]), acc_val(a[2])};
+    double o[3];
+    if (seq_reduce<3>(v3, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
+        const cx<double> alpha = cdot(d2c(ks->sw), mk(o[0], o[1]));  // conj(sw) w~^dag t
+        q.alpha[i] = c2d(alpha);
+        ks->anorm = fmax(ks->anorm, sqrt(o[2]));
+        ks->kused = i + 1;
+        if (i >= klast) ks->done = 1;
+    }
+}
+
+// v^ = t - alpha v_i - gamma_{i-1} v_{i-1}, w^ = s - conj(alpha) w_i - conj(beta_{i-1}) w_{i-1};
+// w^^dag v^, |v^|^2, |w^|^2 -> beta_i, gamma_i, the scales, breakdown checks (Eq. 4.2)
+template <class R>
+__global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i) {
+    using VT = typename BVec<R>::T;
+    const BSeq& q = S[bseq[blockIdx.x]];
+    KState* ks = q.ks;
+    if (ks->done || ks->status) return;
+    __shared__ cx<R> cf[4];
+    if (threadIdx.x == 0) {
+        const cx<double> a = d2c(q.alpha[i]);
+        const cx<double> ca = a * d2c(ks->sv), da = conj(a) * d2c(ks->sw);
+        const cx<double> cg = i > 0 ? d2c(q.gamma[i - 1]) * d2c(ks->svp) : mk(0.0, 0.0);
+        const cx<double> db = i > 0 ? conj(d2c(q.beta[i - 1])) * d2c(ks->swp) : mk(0.0, 0.0);
+        cf[0] = mk((R)ca.r, (R)ca.i);
+        cf[1] = mk((R)da.r, (R)da.i);
+        cf[2] = mk((R)cg.r, (R)cg.i);
+        cf[3] = mk((R)db.r, (R)db.i);
+    }
+    __syncthreads();
+    const int local = blockIdx.x - q.blk0;
+    const int site = local * BT + threadIdx.x;
+    typename AccOf<R>::T a[4];
+    if (site < q.g.V) {
+        Spinor<R> t, s, vi, wi, vm, wm;
+        load_spinor((const VT*)q.t, q.g.V, site, t);
+        load_spinor((const VT*)q.s, q.g.V, site, s);
+        load_spinor((const VT*)vslot<R>(q, i, false), q.g.V, site, vi);
+        load_spinor((const VT*)vslot<R>(q, i, true), q.g.V, site, wi);
+        if (i > 0) {
+            load_spinor((const VT*)vslot<R>(q, i - 1, false), q.g.V, site, vm);
+            load_spinor((const VT*)vslot<R>(q, i - 1, true), q.g.V, site, wm);
+        }
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<R> x = t.s[sp][c] - cf[0] * vi.s[sp][c];
+                cx<R> y = s.s[sp][c] - cf[1] * wi.s[sp][c];
+                if (i > 0) {
+                    x = x - cf[2] * vm.s[sp][c];
+                    y = y - cf[3] * wm.s[sp][c];
+                }
+                t.s[sp][c] = x;
+                s.s[sp][c] = y;
+                acc_cdot(a, y, x);
+                acc_norm2(a[2], x);
+                acc_norm2(a[3], y);
+            }
+        store_spinor((VT*)vslot<R>(q, i + 1, false), q.g.V, site, t);
+        store_spinor((VT*)vslot<R>(q, i + 1, true), q.g.V, site, s);
+    }
+    const double v4[4] = {acc_val(a[0]), acc_val(a[1]), acc_val(a[2]), acc_val(a[3])};
+    double o[4];
+    if (seq_reduce<4>(v4, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
+        const double nv = sqrt(o[2]), nw = sqrt(o[3]);
+        const cx<double> delta = mk(o[0], o[1]);
+        if (nv <= 1e-13 * fmax(ks->anorm, 1e-300)) {
+            ks->done = 1;  // lucky breakdown
+        } else if (sqrt(norm2(delta)) <= 1e-14 * nv * nw) {
+            ks->done = 1;  // serious breakdown
+            ks->bdstep = i + 1;
+        } else {
+            const cx<double> gm = mk(o[0] / nv, o[1] / nv);
+            q.beta[i] = make_double2(nv, 0.0);
+            q.gamma[i] = c2d(gm);
+            ks->svp = ks->sv;
+            ks->swp = ks->sw;
+            ks->sv = make_double2(1.0 / nv, 0.0);
+            ks->sw = c2d(cdiv(mk(1.0, 0.0), conj(gm)));
+            q.vscale[i + 1] = ks->sv;
+        }
+    }
+}
+
+// FP64 regeneration (Sec. 5): r_{i+1} = ((A - alpha_i) r_i - gamma_{i-1} r_{i-1}) / beta_i,
+// y += c_{i+1} r_{i+1}
+__global__ void __launch_bounds__(BT) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
+                                                HopCoef<double> hc) {
+    const BSeq& q = S[bseq[blockIdx.x]];
+    const KState* ks = q.ks;
+    if (ks->status || i + 1 >= ks->kused) return;
+    __shared__ cx<double> cf[4];
+    if (threadIdx.x == 0) {
+        const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(q.beta[i]));
+        cf[0] = ib;
+        cf[1] = ib * d2c(q.alpha[i]);
+        cf[2] = i > 0 ? ib * d2c(q.gamma[i - 1]) : mk(0.0, 0.0);
+        cf[3] = d2c(q.cvec[i + 1]);
+    }
+    __syncthreads();
+    const int site = (blockIdx.x - q.blk0) * BT + threadIdx.x;
+    if (site >= q.g.V) return;
+    const double2* ri = q.r[i % 3];
+    const double2* const xs[1] = {ri};
+    const HopCoef<double> hcs[1] = {hc};
+    Spinor<double> acc[1], self, rm;
+    apply_site<LINK_F64, double, 1>(q.g, site, q.U64, xs, acc, hcs);
+    load_spinor(ri, q.g.V, site, self);
+    finish_site(acc[0], self, true);
+    if (i > 0) load_spinor(q.r[(i + 2) % 3], q.g.V, site, rm);
+    double2* rn = q.r[(i + 1) % 3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cx<double> z = cf[0] * acc[0].s[sp][c] - cf[1] * self.s[sp][c];
+            if (i > 0) z = z - cf[2] * rm.s[sp][c];
+            const size_t e = (size_t)(3 * sp + c) * q.g.V + site;
+            rn[e] = c2d(z);
+            cx<double> yy = d2c(q.y[e]);
+            cfma(yy, cf[3], z);
+            q.y[e] = c2d(yy);
+        }
+}
+
+}  // namespace
+}  // namespace ovl
+
+// ------------------------------------------------------------------ host side --
+struct ovl_batch {
+    std::vector<ovl_ctx*> ctx;
+    std::vector<int> nrhs;
+    std::vector<int> seq_ctx;   // context of each sequence
+    int nseq = 0;
+    int kcap = 0;
+    int mode = -1;              // 1 mixed, 0 FP64 one-pass
+    cudaStream_t st = nullptr;
+    cudaStream_t cap_st = nullptr;
+    // device memory
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    ovl::BSeq* dseq = nullptr;
+    int* dbseq = nullptr;
+    int nblocks = 0;
+    std::vector<ovl::BSeq> hseq;
+    std::vector<double2*> b64, bR, bL, pq;
+    ovl::KState* ks = nullptr;
+    double2 *alpha = nullptr, *beta = nullptr, *gamma = nullptr, *cvec = nullptr, *vscale = nullptr;
+    double2* inner = nullptr;
+    size_t inner_stride = 0;
+    double* qpart = nullptr;
+    size_t qpart_stride = 0;
+    unsigned int* qcnt = nullptr;
+    double* part = nullptr;      // scratch of the per-sequence prologue kernels
+    unsigned int* counter = nullptr;
+    double2* stage = nullptr;    // host transfers
+    // graph
+    cudaGraphExec_t exec = nullptr;
+    int g_k = -1, g_flags = 0;
+    double g_mu = 0, g_kappa = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(ovl_batch* b, int code, const std::string& m) {
+    if (b) b->err = m;
+    return code;
+}
+
+void bfree(ovl_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    if (b->mem) cudaFree(b->mem);
+    b->mem = nullptr;
+    b->mem_bytes = 0;
+    b->mode = -1;
+}
+
+// Carve the batch's device memory for mode (1 mixed, 0 FP64 one-pass) and Krylov size kmax.
+int balloc(ovl_batch* b, int mode, int kmax) {
+    if (b->mem && b->mode == mode && b->kcap >= kmax) return OVL_OK;
+    bfree(b);
+    const int ns = b->nseq;
+    const size_t kk = (size_t)kmax + 2;
+    const size_t inner_stride = std::max(ovl::inner_work_elems(kmax, 0), ovl::inner_work_elems(kmax, 1));
+    const size_t qpart_stride = 8192;
+    // byte sizes, every piece 256-aligned
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t total = 0;
+    std::vector<size_t> seq_bytes(ns);
+    int nblocks = 0;
+    for (int s = 0; s < ns; ++s) {
+        const ovl_ctx* c = b->ctx[b->seq_ctx[s]];
+        const size_t n = c->n;
+        const int nblk = (c->g.V + ovl::BT - 1) / ovl::BT;
+        nblocks += nblk;
+        size_t z = 0;
+        z += 4 * al(n * sizeof(double2));                        // b, bR, bL, y
+        z += 3 * al(n * sizeof(double2));                        // regeneration ring
+        if (mode == 1) z += 8 * al(n * sizeof(float2));          // FP32 v, w rings, t, s
+        else z += (kk + 5) * al(n * sizeof(double2));           // FP64 basis, w ring, t, s
+        z += al((size_t)nblk * 4 * sizeof(double2)) + al(128 * sizeof(double2));  // partials, pq
+        seq_bytes[s] = z;
+        total += z;
+    }
+    total += al(ns * sizeof(ovl::KState)) + 5 * al(ns * kk * sizeof(double2)) +
+             al((size_t)ns * inner_stride * sizeof(double2)) + al((size_t)ns * qpart_stride * sizeof(double)) +
+             al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks * sizeof(int)) +
+             al((size_t)(1 << 20) * sizeof(double)) + al(64 * sizeof(unsigned int));
+    if (cudaMalloc(&b->mem, total) != cudaSuccess) {
+        b->mem = nullptr;
+        return bfail(b, OVL_ENOMEM, "batch workspace");
+    }
+    b->mem_bytes = total;
+    char* p = (char*)b->mem;
+    auto take = [&](size_t bytes) { char* r = p; p += al(bytes); return (void*)r; };
+    b->ks = (ovl::KState*)take(ns * sizeof(ovl::KState));
+    b->alpha = (double2*)take(ns * kk * sizeof(double2));
+    b->beta = (double2*)take(ns * kk * sizeof(double2));
+    b->gamma = (double2*)take(ns * kk * sizeof(double2));
+    b->cvec = (double2*)take(ns * kk * sizeof(double2));
+    b->vscale = (double2*)take(ns * kk * sizeof(double2));
+    b->inner = (double2*)take((size_t)ns * inner_stride * sizeof(double2));
+    b->inner_stride = inner_stride;
+    b->qpart = (double*)take((size_t)ns * qpart_stride * sizeof(double));
+    b->qpart_stride = qpart_stride;
+    b->qcnt = (unsigned int*)take(ns * 64 * sizeof(unsigned int));
+    b->dseq = (ovl::BSeq*)take(ns * sizeof(ovl::BSeq));
+    b->dbseq = (int*)take(nblocks * sizeof(int));
+    b->part = (double*)take((size_t)(1 << 20) * sizeof(double));
+    b->counter = (unsigned int*)take(64 * sizeof(unsigned int));
+    b->hseq.assign(ns, ovl::BSeq());
+    b->b64.assign(ns, nullptr), b->bR.assign(ns, nullptr), b->bL.assign(ns, nullptr), b->pq.assign(ns, nullptr);
+    std::vector<int> table;
+    table.reserve(nblocks);
+    int blk0 = 0;
+    for (int s = 0; s < ns; ++s) {
+        ovl_ctx* c = b->ctx[b->seq_ctx[s]];
+        const size_t n = c->n;
+        ovl::BSeq& q = b->hseq[s];
+        std::memset(&q, 0, sizeof(q));
+        q.g = c->g;
+        q.n = n;
+        q.U = mode == 1 ? (const void*)c->U12 : (const void*)c->U64;
+        q.U64 = c->U64;
+        b->b64[s] = (double2*)take(n * sizeof(double2));
+        b->bR[s] = (double2*)take(n * sizeof(double2));
+        b->bL[s] = (double2*)take(n * sizeof(double2));
+        q.y = (double2*)take(n * sizeof(double2));
+        for (int j = 0; j < 3; ++j) q.r[j] = (double2*)take(n * sizeof(double2));
+        if (mode == 1) {
+            for (int j = 0; j < 3; ++j) q.v[j] = take(n * sizeof(float2)), q.w[j] = take(n * sizeof(float2));
+            q.t = take(n * sizeof(float2));
+            q.s = take(n * sizeof(float2));
+            q.V = nullptr;
+        } else {
+            q.V = (double2*)take(kk * n * sizeof(double2));
+            for (int j = 0; j < 3; ++j) q.w[j] = take(n * sizeof(double2)), q.v[j] = nullptr;
+            q.t = take(n * sizeof(double2));
+            q.s = take(n * sizeof(double2));
+        }
+        q.ks = b->ks + s;
+        q.alpha = b->alpha + s * kk;
+        q.beta = b->beta + s * kk;
+        q.gamma = b->gamma + s * kk;
+        q.cvec = b->cvec + s * kk;
+        q.vscale = b->vscale + s * kk;
+        q.nblk = (c->g.V + ovl::BT - 1) / ovl::BT;
+        q.part = (double2*)take((size_t)q.nblk * 4 * sizeof(double2));
+        b->pq[s] = (double2*)take(128 * sizeof(double2));
+        q.cnt = b->qcnt + s;  // the inner quadrature's counters follow at qcnt + nseq
+        q.blk0 = blk0;
+        for (int j = 0; j < q.nblk; ++j) table.push_back(s);
+        blk0 += q.nblk;
+    }
+    b->nblocks = blk0;
+    if (cudaMemcpy(b->dseq, b->hseq.data(), ns * sizeof(ovl::BSeq), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dbseq, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->qcnt, 0, ns * 64 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(b->counter, 0, 64 * sizeof(unsigned int)) != cudaSuccess) {
+        bfree(b);
+        return bfail(b, OVL_ECUDA, "batch set-up copies");
+    }
+    b->mode = mode;
+    b->kcap = kmax;
+    return OVL_OK;
+}
+
+// Everything between the packed sources and the unpacked results, on stream st.
+int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaStream_t st) {
+    const bool mixed = b->mode == 1;
+    const int ns = b->nseq;
+    for (int s = 0; s < ns; ++s) {
+        ovl_ctx* c = b->ctx[b->seq_ctx[s]];
+        const ovl::BSeq& q = b->hseq[s];
+        const size_t n = q.n;
+        ovl::launch_state_init(q.ks, st);
+        const int m = c->m;
+        if (m > 0) {
+            ovl::launch_multidot(c->L, n, m, b->b64[s], b->pq[s], 0, b->part, n, st);
+            ovl::launch_multidot(c->R, n, m, b->b64[s], b->pq[s] + m, 0, b->part, n, st);
+        }
+        ovl::launch_deflate_split(b->b64[s], c->R, c->L, c->lam, m, b->pq[s], b->bR[s], b->bL[s], q.y, q.ks,
+                                  q.vscale, b->part, b->counter, n, st);
+        if (mixed) {
+            ovl::launch_native_f64_to_f32(b->bR[s], q.v[0], q.g, 1, st);
+            ovl::launch_native_f64_to_f32(b->bL[s], q.w[0], q.g, 1, st);
+        } else {
+            cudaMemcpyAsync(q.V, b->bR[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(q.w[0], b->bL[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    // pass 1 (all sequences per launch)
+    const int nb = b->nblocks;
+    for (int i = 0; i < k; ++i) {
+        if (mixed) {
+            ovl::k_b_pair<ovl::LINK_F32_12, float><<<nb, ovl::BT, 0, st>>>(
+                b->dseq, b->dbseq, i, k - 1, ovl::make_coef<float>(mu, kappa), ovl::make_coef<float>(-mu, kappa));
+            if (i + 1 < k) ovl::k_b_lstep<float><<<nb, ovl::BT, 0, st>>>(b->dseq, b->dbseq, i);
+        } else {
+            ovl::k_b_pair<ovl::LINK_F64, double><<<nb, ovl::BT, 0, st>>>(
+                b->dseq, b->dbseq, i, k - 1, ovl::make_coef<double>(mu, kappa), ovl::make_coef<double>(-mu, kappa));
+            if (i + 1 < k) ovl::k_b_lstep<double><<<nb, ovl::BT, 0, st>>>(b->dseq, b->dbseq, i);
+        }
+    }
+    // inner sign of every sequence at once; Roberts' iteration where the quadrature did not settle
+    const size_t kk = (size_t)b->kcap + 2;
+    if (ovl::launch_inner_quadrature_batched(ns, b->alpha, b->beta, b->gamma, b->ks, b->cvec, kk, b->inner,
+                                             b->inner_stride, b->kcap, b->qpart, b->qpart_stride, b->qcnt + ns, st))
+        return bfail(b, OVL_ECUDA, "batched inner sign launch");
+    for (int s = 0; s < ns; ++s) {
+        ovl_ctx* c = b->ctx[b->seq_ctx[s]];
+        const ovl::BSeq& q = b->hseq[s];
+        if (ovl::launch_inner_newton(q.alpha, q.beta, q.gamma, nullptr, 0, 1, q.ks, q.cvec,
+                                     b->inner + (size_t)s * b->inner_stride, b->inner_stride, b->kcap, c->num_sms, st,
+                                     1))
+            return bfail(b, OVL_ECUDA, "inner sign fallback launch");
+    }
+    // combination
+    if (mixed) {
+        for (int s = 0; s < ns; ++s) {
+            const ovl::BSeq& q = b->hseq[s];
+            ovl::launch_scale_start(b->bR[s], q.r[0], q.y, q.cvec, q.ks, q.n, st);
+        }
+        for (int i = 0; i + 1 < k; ++i)
+            ovl::k_b_regen<<<nb, ovl::BT, 0, st>>>(b->dseq, b->dbseq, i, ovl::make_coef<double>(mu, kappa));
+    } else {
+        for (int s = 0; s < ns; ++s) {
+            const ovl::BSeq& q = b->hseq[s];
+            ovl::launch_combine(q.V, q.n, q.vscale, q.cvec, q.ks, b->kcap, q.y, q.n, st);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? OVL_OK : bfail(b, OVL_ECUDA, "batch launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int ovl_batch_create(ovl_batch** out, ovl_ctx* const* ctxs, int nctx, const int* nrhs) {
+    if (!out || !ctxs || nctx < 1 || !nrhs) return OVL_EINVAL;
+    *out = nullptr;
+    ovl_batch* b = new ovl_batch();
+    for (int j = 0; j < nctx; ++j) {
+        if (!ctxs[j] || nrhs[j] < 0) {
+            delete b;
+            return OVL_EINVAL;
+        }
+        if (!ctxs[j]->have_gauge) {
+            delete b;
+            return OVL_ESTATE;
+        }
+        b->ctx.push_back(ctxs[j]);
+        b->nrhs.push_back(nrhs[j]);
+        for (int r = 0; r < nrhs[j]; ++r) b->seq_ctx.push_back(j);
+    }
+    b->nseq = (int)b->seq_ctx.size();
+    if (b->nseq == 0) {
+        delete b;
+        return OVL_EINVAL;
+    }
+    b->st = ctxs[0]->st;
+    *out = b;
+    return OVL_OK;
+}
+
+int ovl_batch_destroy(ovl_batch* b) {
+    if (!b) return OVL_OK;
+    if (b->st) cudaStreamSynchronize(b->st);
+    else cudaDeviceSynchronize();
+    bfree(b);
+    if (b->cap_st) cudaStreamDestroy(b->cap_st);
+    delete b;
+    return OVL_OK;
+}
+
+const char* ovl_batch_last_error(const ovl_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* const* bsrc, void* const* out,
+                    int flags, ovl_info* info) {
+    if (!b || !bsrc || !out || k < 1) return bfail(b, OVL_EINVAL, "bad argument");
+    const int mode = (flags & OVL_MIXED) ? 1 : 0;
+    int r = balloc(b, mode, k);
+    if (r) return r;
+    for (ovl_ctx* c : b->ctx) {
+        if (c->m > 0 && mode == 1 && !c->R32) return bfail(b, OVL_ESTATE, "deflation set not installed");
+        if (c->st != b->st) return bfail(b, OVL_EINVAL, "all contexts of a batch must share one stream");
+    }
+    cudaStream_t st = b->st;
+    const bool host = (flags & OVL_HOST) != 0;
+    // pack the sources (canonical -> device layout); sources of context j follow one another
+    int s = 0;
+    for (size_t j = 0; j < b->ctx.size(); ++j) {
+        ovl_ctx* c = b->ctx[j];
+        const size_t n = c->n, vb = n * sizeof(double2);
+        for (int rr = 0; rr < b->nrhs[j]; ++rr, ++s) {
+            const double2* src = (const double2*)bsrc[j] + (size_t)rr * n;
+            if (host) {
+                r = ovl_priv::ensure_base(c);
+                if (r) return bfail(b, r, c->err);
+                if (cudaMemcpyAsync(c->stage_in, src, vb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    return bfail(b, OVL_ECUDA, "source copy");
+                src = c->stage_in;
+            }
+            ovl::launch_pack_spinor(src, b->b64[s], 0, c->g, st);
+        }
+    }
+    // the solve, as a graph captured once per (k, flags, mu, kappa)
+    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH);
+    if (flags & OVL_NO_GRAPH) {
+        r = enqueue_batch(b, k, mu, kappa, flags, st);
+        if (r) return r;
+    } else {
+        if (!b->exec || b->g_k != k || b->g_flags != gflags || b->g_mu != mu || b->g_kappa != kappa) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+            if (!b->cap_st && cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+                return bfail(b, OVL_ECUDA, "capture stream");
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, OVL_ECUDA, "begin capture");
+            r = enqueue_batch(b, k, mu, kappa, flags, b->cap_st);
+            cudaError_t e = cudaStreamEndCapture(b->cap_st, &gr);
+            if (r) {
+                if (gr) cudaGraphDestroy(gr);
+                return r;
+            }
+            if (e != cudaSuccess) return bfail(b, OVL_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->exec, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) {
+                b->exec = nullptr;
+                return bfail(b, OVL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            }
+            b->g_k = k, b->g_flags = gflags, b->g_mu = mu, b->g_kappa = kappa;
+        }
+        if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return bfail(b, OVL_ECUDA, "graph launch");
+    }
+    // unpack: out = y, or D_ov b = b + gamma5 y with OVL_OVERLAP
+    s = 0;
+    for (size_t j = 0; j < b->ctx.size(); ++j) {
+        ovl_ctx* c = b->ctx[j];
+        const size_t n = c->n, vb = n * sizeof(double2);
+        for (int rr = 0; rr < b->nrhs[j]; ++rr, ++s) {
+            const double2* src = (const double2*)bsrc[j] + (size_t)rr * n;
+            double2* dst = (double2*)out[j] + (size_t)rr * n;
+            const bool ov = (flags & OVL_OVERLAP) != 0;
+            if (host) {
+                if (ov && cudaMemcpyAsync(c->stage_in, src, vb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    return bfail(b, OVL_ECUDA, "source copy");
+                ovl::launch_unpack_spinor(b->hseq[s].y, 0, c->stage_out, ov ? c->stage_in : nullptr, ov ? 1 : 0, c->g,
+                                          st);
+                if (cudaMemcpyAsync(dst, c->stage_out, vb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    return bfail(b, OVL_ECUDA, "result copy");
+            } else {
+                ovl::launch_unpack_spinor(b->hseq[s].y, 0, dst, ov ? src : nullptr, ov ? 1 : 0, c->g, st);
+            }
+        }
+    }
+    std::vector<ovl::KState> ks(b->nseq);
+    if (cudaMemcpyAsync(ks.data(), b->ks, b->nseq * sizeof(ovl::KState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return bfail(b, OVL_ECUDA, std::string("batch solve: ") + cudaGetErrorString(cudaGetLastError()));
+    int worst = OVL_OK;
+    for (int q = 0; q < b->nseq; ++q) {
+        if (info) {
+            info[q].k_used = ks[q].kused;
+            info[q].breakdown_step = ks[q].bdstep;
+            info[q].inner_iters = ks[q].inner_iters;
+            info[q].inner_method = ks[q].inner_method;
+            info[q].bperp_norm = ks[q].nR;
+            info[q].inner_err = ks[q].inner_err;
+        }
+        int code = OVL_OK;
+        if (ks[q].timeout) code = OVL_ETIMEOUT;
+        else if (ks[q].status) code = ks[q].status;
+        else if (ks[q].bdstep >= 0) code = OVL_EBREAKDOWN;
+        if (code && !worst) {
+            worst = code;
+            b->err = "sequence " + std::to_string(q) + " failed";
+        }
+    }
+    return worst;
+}
+
+int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int k, double mu, double kappa,
+                            const void* const* b, void* const* out, int flags, ovl_info* info) {
+    ovl_batch* bt = nullptr;
+    int r = ovl_batch_create(&bt, ctxs, nctx, nrhs);
+    if (r) return r;
+    r = ovl_batch_solve(bt, k, mu, kappa, b, out, flags | OVL_NO_GRAPH, info);
+    if (r && ctxs[0]) ctxs[0]->err = bt->err;
+    ovl_batch_destroy(bt);
+    return r;
+}
+
+}  // extern "C"

@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(256) k_gq_accum(const double2* __restrict__ wo
     const double hl = TADJ_H0 / (double)(1 << level);
     const double2* a = work;
     const double2* d = work + 3 * (size_t)n * nt;
-    const int p0 = blockIdx.y * GQ_T, q0 = blockIdx.x * GQ_T;
+    // one-dimensional grid (the grid reduction below counts blocks along x): tile (p, q) of M
+    const int ntq = (n + GQ_T - 1) / GQ_T;
+    const int p0 = (blockIdx.x / ntq) * GQ_T, q0 = (blockIdx.x % ntq) * GQ_T;
     const int tp = threadIdx.x >> 4, tq = threadIdx.x & 15;
     cx<double> acc = mk(0.0, 0.0);
     for (int t0 = 0; t0 < nt; t0 += GQ_C) {
@@ -574,8 +576,8 @@ extern "C" int ovl_sign_grad(ovl_ctx* c, int k, double mu, double kappa, const v
             const int nt = level == 0 ? 2 * m0 : 2 * (m0 << (level - 1));
             ovl::k_gq_solve<<<(nt + 31) / 32, 32, 0, st>>>(c->alpha, c->beta, c->gamma, kk, tscal, c->tadj, level, nt,
                                                            tstatus);
-            const dim3 gm((kk + ovl::GQ_T - 1) / ovl::GQ_T, (kk + ovl::GQ_T - 1) / ovl::GQ_T);
-            ovl::k_gq_accum<<<gm, 256, 0, st>>>(c->tadj, kk, nt, level, M, part, cnt, dn);
+            const int ntile = (kk + ovl::GQ_T - 1) / ovl::GQ_T;
+            ovl::k_gq_accum<<<ntile * ntile, 256, 0, st>>>(c->tadj, kk, nt, level, M, part, cnt, dn);
             ovl::k_gq_dsum<<<(kk + 7) / 8, 256, 0, st>>>(c->tadj, kk, nt, level, sd);
             double hd[2];
             int hst = 0;

@@ -40,6 +40,13 @@ static int quad_threads(int level) {
     return 2 * nodes;  // +- i e^u
 }
 
+// Offsets of sequence j in a batch of independent inner problems (zero for a single one): the
+// coefficient arrays, output c, the solve state, the scratch and the reduction buffers of
+// sequence j start at j times these strides.
+struct QStride {
+    size_t coef, work, part;
+};
+
 size_t inner_work_elems(int kmax, int method) {
     if (method == 0) {
         // per thread and row: 3 complex (b/d, u/d, w/d), plus T and S sums
@@ -51,8 +58,16 @@ size_t inner_work_elems(int kmax, int method) {
 
 // ---------------------------------------------------------- quadrature --
 // log of a Gershgorin bound on |lambda_max(G)| -> ks->red[7].x
-__global__ void k_quad_prep(const double2* alpha, const double2* beta, const double2* gamma, KState* ks) {
+__global__ void k_quad_prep(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,
+                            QStride qs) {
     __shared__ double red[32];
+    {
+        const size_t j = blockIdx.x;
+        alpha += j * qs.coef;
+        beta += j * qs.coef;
+        gamma += j * qs.coef;
+        ks += j;
+    }
     const int n = ks->kused;
     double m = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -80,7 +95,15 @@ __global__ void k_quad_prep(const double2* alpha, const double2* beta, const dou
 // scratch column of the thread (row-major over rows, thread fastest).
 __global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* __restrict__ beta,
                              const double2* __restrict__ gamma, KState* ks, double2* __restrict__ work, int level,
-                             int nthreads) {
+                             int nthreads, QStride qs) {
+    {
+        const size_t j = blockIdx.y;
+        alpha += j * qs.coef;
+        beta += j * qs.coef;
+        gamma += j * qs.coef;
+        ks += j;
+        work += j * qs.work;
+    }
     if (ks->inner_done || ks->status || ks->timeout) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nthreads) return;
@@ -156,8 +179,17 @@ __global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* _
 
 // T_l = (l == 0 ? 0 : T_{l-1}/2) + (h_l/pi) sum_threads x ; convergence on |T_l - T_{l-1}|.
 __global__ void k_quad_sum(const double2* __restrict__ work, double2* __restrict__ T, double2* __restrict__ c,
-                           KState* ks, int level, int nthreads, double* partials, unsigned int* counter) {
+                           KState* ks, int level, int nthreads, double* partials, unsigned int* counter, QStride qs) {
     __shared__ double red[96];
+    {
+        const size_t j = blockIdx.y;
+        work += j * qs.work;
+        T += j * qs.work;
+        c += j * qs.coef;
+        ks += j;
+        partials += j * qs.part;
+        counter += j;
+    }
     if (ks->inner_done || ks->status || ks->timeout) return;
     const int n = ks->kused;
     const double hl = QUAD_H0 / (double)(1 << level);
@@ -207,20 +239,36 @@ __global__ void k_quad_sum(const double2* __restrict__ work, double2* __restrict
     }
 }
 
+static void quad_launch(const double2* alpha, const double2* beta, const double2* gamma, KState* ks, double2* c,
+                        double2* work, int kmax, double* partials, unsigned int* counter, int nseq, QStride qs,
+                        cudaStream_t st) {
+    const int tmax = quad_threads(QUAD_LEVELS - 1);
+    double2* T = work + (size_t)tmax * kmax * 3;
+    k_quad_prep<<<nseq, 256, 0, st>>>(alpha, beta, gamma, ks, qs);
+    for (int level = 0; level < QUAD_LEVELS; ++level) {
+        const int nt = quad_threads(level);
+        k_quad_solve<<<dim3((nt + 31) / 32, nseq), 32, 0, st>>>(alpha, beta, gamma, ks, work, level, nt, qs);
+        int blocks = (kmax + 7) / 8;
+        if (blocks > 256) blocks = 256;
+        k_quad_sum<<<dim3(blocks, nseq), 256, 0, st>>>(work, T, c, ks, level, nt, partials, counter, qs);
+    }
+}
+
 int launch_inner_quadrature(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,
                             double2* c, double2* work, size_t work_elems, int kmax, double* partials,
                             unsigned int* counter, cudaStream_t st) {
-    const int tmax = quad_threads(QUAD_LEVELS - 1);
     if (inner_work_elems(kmax, 0) > work_elems) return -1;
-    double2* T = work + (size_t)tmax * kmax * 3;
-    k_quad_prep<<<1, 256, 0, st>>>(alpha, beta, gamma, ks);
-    for (int level = 0; level < QUAD_LEVELS; ++level) {
-        const int nt = quad_threads(level);
-        k_quad_solve<<<(nt + 31) / 32, 32, 0, st>>>(alpha, beta, gamma, ks, work, level, nt);
-        int blocks = (kmax + 7) / 8;
-        if (blocks > 256) blocks = 256;
-        k_quad_sum<<<blocks, 256, 0, st>>>(work, T, c, ks, level, nt, partials, counter);
-    }
+    quad_launch(alpha, beta, gamma, ks, c, work, kmax, partials, counter, 1, QStride{0, 0, 0}, st);
+    return 0;
+}
+
+int launch_inner_quadrature_batched(int nseq, const double2* alpha, const double2* beta, const double2* gamma,
+                                    KState* ks, double2* c, size_t coef_stride, double2* work, size_t work_stride,
+                                    int kmax, double* partials, size_t part_stride, unsigned int* counters,
+                                    cudaStream_t st) {
+    if (inner_work_elems(kmax, 0) > work_stride || nseq < 1) return -1;
+    quad_launch(alpha, beta, gamma, ks, c, work, kmax, partials, counters, nseq,
+                QStride{coef_stride, work_stride, part_stride}, st);
     return 0;
 }
 

@@ -117,6 +117,13 @@ int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y,
 int launch_inner_quadrature(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,
                             double2* c, double2* work, size_t work_elems, int kmax, double* partials,
                             unsigned int* counter, cudaStream_t st);
+// the same for nseq independent problems at once; sequence j's alpha, beta, gamma, c start at
+// j coef_stride, its state at ks + j, its scratch at j work_stride (>= inner_work_elems(kmax, 0)),
+// its reduction buffers at j part_stride and counters + j.
+int launch_inner_quadrature_batched(int nseq, const double2* alpha, const double2* beta, const double2* gamma,
+                                    KState* ks, double2* c, size_t coef_stride, double2* work, size_t work_stride,
+                                    int kmax, double* partials, size_t part_stride, unsigned int* counters,
+                                    cudaStream_t st);
 // c = nR * sgn(M) e_1 by Roberts' iteration (Sec. 2) with determinant scaling, M dense n x n
 // (n = ks->kused) built from the tridiagonal (tri = 1) or taken as the Hessenberg H (ld = ldH).
 // fallback = 1: run only if the quadrature before it did not converge (status 6 is then cleared).

@@ -33,7 +33,8 @@ _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EB
 EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
            "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
-           "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad"]
+           "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad", "ovl_batch_create",
+           "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_sign_krylov_batched"]
 
 
 class OvlError(RuntimeError):
@@ -96,6 +97,12 @@ def load(path: str = LIB_PATH):
         "ovl_dw_grad": (I, [P, D, D, P, P, P, ctypes.POINTER(D), I]),
         "ovl_sign_grad": (I, [P, I, D, D, P, P, P, P, ctypes.POINTER(D), P, I, ctypes.POINTER(Info)]),
         "ovl_profile_reset": (I, [P]),
+        "ovl_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I, ctypes.POINTER(I)]),
+        "ovl_batch_destroy": (I, [P]),
+        "ovl_batch_last_error": (ctypes.c_char_p, [P]),
+        "ovl_batch_solve": (I, [P, I, D, D, ctypes.POINTER(P), ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
+        "ovl_sign_krylov_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, D, D, ctypes.POINTER(P),
+                                        ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -309,3 +316,51 @@ class Context:
         d = info.as_dict()
         d["status"] = r
         return out, d
+
+
+class Batch:
+    """Batched two-sided Lanczos solves over several contexts (lattices) and right-hand sides:
+    ``nrhs[j]`` sources for ``contexts[j]``, solved together (one captured graph)."""
+
+    def __init__(self, contexts, nrhs):
+        self._lib = load()
+        self.contexts = list(contexts)
+        self.nrhs = [int(r) for r in nrhs]
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        nr = (ctypes.c_int * len(self.nrhs))(*self.nrhs)
+        r = self._lib.ovl_batch_create(ctypes.byref(h), arr, len(self.contexts), nr)
+        if r:
+            raise OvlError(r, "ovl_batch_create failed")
+        self._h = h
+
+    @property
+    def nseq(self) -> int:
+        return sum(self.nrhs)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ovl_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, k: int, mu: float, kappa: float, sources, outs=None, flags: int = 0):
+        """sources[j]: (nrhs[j], 12 V_j) complex128 (CUDA tensors or host arrays); returns
+        (outs, infos, status) with one info dict per sequence in (context, rhs) order."""
+        import torch
+        if outs is None:
+            outs = [np.empty_like(b) if isinstance(b, np.ndarray) else torch.empty_like(b) for b in sources]
+        if any(_is_host(b) for b in sources):
+            flags |= HOST
+        bp = (ctypes.c_void_p * len(sources))(*[_ptr(b) for b in sources])
+        op = (ctypes.c_void_p * len(outs))(*[_ptr(o) for o in outs])
+        infos = (Info * self.nseq)()
+        r = self._lib.ovl_batch_solve(self._h, int(k), mu, kappa, bp, op, flags, infos)
+        if r and r != EBREAKDOWN:
+            raise OvlError(r, self._lib.ovl_batch_last_error(self._h).decode())
+        return outs, [i.as_dict() for i in infos], r

@@ -1,0 +1,197 @@
+"""Batched two-sided Lanczos solves (several right-hand sides on several lattices
+of different sizes in one graph-captured launch sequence) against the dense
+oracle, against the single-sequence solve, and on the edge cases of a batch."""
+import numpy as np
+import pytest
+
+from gpu_common import KAPPA, config4, rel, torch_c128
+from oracle import sign as S
+from oracle import wilson as W
+from paper_0810_4228_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ovl():
+    from paper_0810_4228_gb300 import ovl as O
+    O.load()
+    return O
+
+
+@pytest.fixture(scope="module")
+def mid():
+    """A lattice of 192 sites (one full and one partial block) with its dense sign."""
+    dims, mu = (4, 4, 2, 6), 0.3
+    U = synth.gauge_field(dims, 0.5, 3050)
+    A = W.a_operator(U, dims, mu, KAPPA).toarray()
+    return dict(dims=dims, U=U, mu=mu, sgn=S.sign_spectral(A))
+
+
+@pytest.fixture(scope="module")
+def small():
+    """A ragged lattice smaller than one block (V = 72) with its dense sign."""
+    dims, mu = (2, 3, 2, 6), 0.3
+    U = synth.gauge_field(dims, 0.5, 3000)
+    A = W.a_operator(U, dims, mu, KAPPA).toarray()
+    return dict(dims=dims, U=U, mu=mu, sgn=S.sign_spectral(A))
+
+
+def _ctx(O, dims, U):
+    c = O.Context(dims)
+    c.set_gauge(torch_c128(U))
+    return c
+
+
+def _sources(dims, seed, nrhs):
+    return synth.gaussian_source(dims, seed, nrhs=nrhs)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_matches_dense(ovl, mid, mixed):
+    """Two lattices (4^4 and 4^2 x 2 x 6), 3 + 2 sources, every result against the dense oracle."""
+    c4 = config4()
+    assert c4["mu"] == mid["mu"]
+    ca, cb = _ctx(ovl, c4["dims"], c4["U"]), _ctx(ovl, mid["dims"], mid["U"])
+    ba = _sources(c4["dims"], 3100, 3)
+    bb = _sources(mid["dims"], 3101, 2)
+    bt = ovl.Batch([ca, cb], [3, 2])
+    outs, infos, st = bt.solve(500, c4["mu"], KAPPA, [torch_c128(ba), torch_c128(bb)],
+                               flags=ovl.MIXED if mixed else 0)
+    assert st == 0 and len(infos) == 5
+    tol = 1e-8 if mixed else 1e-10
+    ya, yb = outs[0].cpu().numpy(), outs[1].cpu().numpy()
+    sgn4 = c4["X"] @ (S.csign(c4["lam"])[:, None] * c4["Xi"])
+    for r in range(3):
+        assert rel(ya[r], sgn4 @ ba[r]) < tol
+    for r in range(2):
+        assert rel(yb[r], mid["sgn"] @ bb[r]) < tol
+    bt.close()
+
+
+def test_batch_equals_single_solves(ovl, small):
+    """Each sequence of an FP64 batch equals the single-sequence FP64 solve of the same source
+    (both converged; the kernels differ, so rounding differs)."""
+    c4 = config4()
+    ca = _ctx(ovl, c4["dims"], c4["U"])
+    ba = _sources(c4["dims"], 3200, 2)
+    bt = ovl.Batch([ca], [2])
+    outs, _, _ = bt.solve(300, c4["mu"], KAPPA, [torch_c128(ba)])
+    for r in range(2):
+        y1, _ = ca.sign_krylov(ovl.LANCZOS2, 300, c4["mu"], KAPPA, torch_c128(ba[r]))
+        assert rel(outs[0][r].cpu().numpy(), y1.cpu().numpy()) < 1e-11
+    bt.close()
+
+
+@pytest.mark.parametrize("k", [3, 25])
+def test_batch_same_process_small_k(ovl, small, k):
+    """Before loss of bi-orthogonality the batched FP64 process and the oracle's two-sided
+    Lanczos agree to rounding."""
+    from oracle import krylov as K
+    dims = small["dims"]
+    U = small["U"]
+    A = W.a_operator(U, dims, small["mu"], KAPPA)
+    Ad = A.conj().T.tocsr()
+    b = _sources(dims, 3300, 1)
+    c = _ctx(ovl, dims, U)
+    bt = ovl.Batch([c], [1])
+    outs, infos, _ = bt.solve(k, small["mu"], KAPPA, [torch_c128(b)])
+    assert infos[0]["k_used"] == k
+    assert rel(outs[0][0].cpu().numpy(), K.sign_lanczos2(A.dot, Ad.dot, b[0], k)) < 1e-11
+    bt.close()
+
+
+def test_batch_deflated_overlap_host(ovl):
+    """Deflation installed on the context, D_ov output, host buffers, mixed precision."""
+    c4 = config4()
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:20]
+    ca = _ctx(ovl, c4["dims"], c4["U"])
+    ca.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(X[:, idx].T.copy()), torch_c128(Xi[idx, :].conj().copy()))
+    ba = _sources(c4["dims"], 3400, 2)
+    bt = ovl.Batch([ca], [2])
+    outs, infos, st = bt.solve(300, c4["mu"], KAPPA, [np.ascontiguousarray(ba)], flags=ovl.MIXED | ovl.OVERLAP)
+    assert st == 0
+    sgn4 = X @ (S.csign(lam)[:, None] * Xi)
+    g5 = np.tile(np.array([1, 1, 1, 1, 1, 1, -1, -1, -1, -1, -1, -1.0]), c4["A"].shape[0] // 12)
+    for r in range(2):
+        ref = ba[r] + g5 * (sgn4 @ ba[r])
+        assert rel(outs[0][r], ref) < 1e-8
+    bt.close()
+
+
+def test_batch_graph_replay_and_recapture(ovl, small):
+    """Replaying the captured graph gives identical results; a new k captures a new graph."""
+    dims, U = small["dims"], small["U"]
+    c = _ctx(ovl, dims, U)
+    b = torch_c128(_sources(dims, 3500, 3))
+    bt = ovl.Batch([c], [3])
+    y1 = bt.solve(60, small["mu"], KAPPA, [b])[0][0].clone()
+    y2 = bt.solve(60, small["mu"], KAPPA, [b])[0][0].clone()
+    y3 = bt.solve(80, small["mu"], KAPPA, [b])[0][0].clone()
+    y4 = bt.solve(60, small["mu"], KAPPA, [b], flags=ovl.NO_GRAPH)[0][0].clone()
+    y5 = bt.solve(80, small["mu"], KAPPA, [b], flags=ovl.NO_GRAPH)[0][0].clone()
+    assert bool((y1 == y2).all()) and bool((y1 == y4).all()) and bool((y3 == y5).all())
+    assert not bool((y1 == y3).all())
+    bt.close()
+
+
+def _oracle_2sl(small, b, k):
+    from oracle import krylov as K
+    A = W.a_operator(small["U"], small["dims"], small["mu"], KAPPA)
+    return K.sign_lanczos2(A.dot, A.conj().T.tocsr().dot, b, k)
+
+
+def test_batch_zero_source_among_others(ovl, small):
+    dims, U = small["dims"], small["U"]
+    c = _ctx(ovl, dims, U)
+    b = _sources(dims, 3600, 3)
+    b[1] = 0
+    bt = ovl.Batch([c], [3])
+    outs, infos, st = bt.solve(25, small["mu"], KAPPA, [torch_c128(b)])
+    y = outs[0].cpu().numpy()
+    assert st == 0 and infos[1]["k_used"] == 0
+    assert not np.any(y[1])
+    for q in (0, 2):
+        assert rel(y[q], _oracle_2sl(small, b[q], 25)) < 1e-11
+    bt.close()
+
+
+def test_one_shot_batched_call(ovl, small):
+    import ctypes
+    dims, U = small["dims"], small["U"]
+    c = _ctx(ovl, dims, U)
+    b = torch_c128(_sources(dims, 3700, 2))
+    out = torch_c128(np.zeros((2, 12 * 72)))
+    lib = ovl.load()
+    ctxs = (ctypes.c_void_p * 1)(c._h.value)
+    nr = (ctypes.c_int * 1)(2)
+    bp = (ctypes.c_void_p * 1)(b.data_ptr())
+    op = (ctypes.c_void_p * 1)(out.data_ptr())
+    r = lib.ovl_sign_krylov_batched(ctxs, 1, nr, 25, small["mu"], KAPPA, bp, op, 0, None)
+    assert r == 0
+    y = out.cpu().numpy()
+    bh = b.cpu().numpy()
+    for q in range(2):
+        assert rel(y[q], _oracle_2sl(small, bh[q], 25)) < 1e-11
+
+
+def test_batch_uneven_lattices_point_sources(ovl):
+    """12 point sources on each of three lattices of different sizes (6^4, 4^3 x 6, 2^2 x 4 x 6),
+    mixed precision at k = 700, against single FP64 solves of the same sources at k = 1000 (point
+    sources need a larger k than Gaussian ones)."""
+    mu = 0.2
+    dims_list = [(6, 6, 6, 6), (4, 4, 4, 6), (2, 2, 4, 6)]
+    ctxs, srcs = [], []
+    for j, d in enumerate(dims_list):
+        ctxs.append(_ctx(ovl, d, synth.gauge_field(d, 1.0, 3800 + j)))
+        srcs.append(synth.point_sources(d, site=0))
+    bt = ovl.Batch(ctxs, [12] * 3)
+    outs, infos, st = bt.solve(700, mu, KAPPA, [torch_c128(s) for s in srcs], flags=ovl.MIXED)
+    assert st == 0 and len(infos) == 36
+    for j in range(3):
+        for r in (0, 5, 11):
+            y1, _ = ctxs[j].sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, torch_c128(srcs[j][r]))
+            e = rel(outs[j][r].cpu().numpy(), y1.cpu().numpy())
+            assert e < 1e-8, (j, r, e)
+    bt.close()
