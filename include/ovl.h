@@ -170,8 +170,9 @@ int ovl_dw_grad(ovl_ctx* ctx, double mu, double kappa, const void* x, const void
  * runs the two-sided Lanczos solve of ovl_sign_krylov (Sec. 4, Eq. 4.2-4.5), but each batched
  * kernel covers all sequences in one launch, with per-sequence reductions, and the whole solve
  * is captured as one CUDA graph (re-captured when k, mu, kappa or the precision change).
- * Precision: OVL_MIXED = FP32 pass 1 and FP64 regeneration pass (Sec. 5); otherwise FP64 one
- * pass with the basis stored.  The contexts must share one stream (the first's); the batch
+ * Precision: OVL_MIXED = FP32 pass 1 and FP64 regeneration pass (Sec. 5); otherwise FP64, one
+ * pass with the basis stored, or two passes with OVL_TWO_PASS or when the stored basis would
+ * exceed 32 GiB.  The contexts must share one stream (the first's); the batch
  * owns its workspace (for n = 12 V summed over sequences: about 8 n FP32 + 7 n FP64 complex
  * values mixed, (k + 9) n FP64 otherwise). */
 typedef struct ovl_batch ovl_batch;
@@ -179,11 +180,17 @@ int ovl_batch_create(ovl_batch** out, ovl_ctx* const* ctxs, int nctx, const int*
 int ovl_batch_destroy(ovl_batch* batch);
 const char* ovl_batch_last_error(const ovl_batch* batch);
 /* b[j], out[j]: nrhs[j] canonical complex128 vectors of context j, one after another (device,
- * or host with OVL_HOST).  flags: OVL_MIXED, OVL_OVERLAP, OVL_HOST, OVL_NO_GRAPH.  info: one
- * entry per sequence in (context, rhs) order (may be NULL).  Returns the first failing
+ * or host with OVL_HOST).  flags: OVL_MIXED, OVL_TWO_PASS, OVL_OVERLAP, OVL_HOST, OVL_NO_GRAPH,
+ * OVL_PROFILE.  info: one
+ * entry per sequence in (context, rhs) order (may be NULL).  OVL_PROFILE: eager launches with
+ * per-phase events (see ovl_batch_profile).  Returns the first failing
  * sequence's status (the others' results are still written). */
 int ovl_batch_solve(ovl_batch* batch, int k, double mu, double kappa, const void* const* b, void* const* out,
                     int flags, ovl_info* info);
+/* Totals of the solves run with OVL_PROFILE (eager launches, CUDA events around each phase):
+ * ms3[0] pass 1 (the Krylov recurrence), ms3[1] the inner sign, ms3[2] the regeneration pass or the
+ * combination; *nsolves the number of such solves.  reset != 0 clears the totals. */
+int ovl_batch_profile(ovl_batch* batch, double* ms3, int* nsolves, int reset);
 /* create + solve + destroy (no graph reuse); errors are reported on ctxs[0]. */
 int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int k, double mu, double kappa,
                             const void* const* b, void* const* out, int flags, ovl_info* info);

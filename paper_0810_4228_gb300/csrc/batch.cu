@@ -16,7 +16,8 @@
 // of exact FP32 products in compensated pairs), pass 2 regenerates the basis
 // in FP64 from the pass-1 coefficients and accumulates y (Sec. 5).  Otherwise
 // FP64 throughout: one pass with the basis stored and the combination
-// y = sum_i c_i v_i at the end.
+// y = sum_i c_i v_i at the end, or, with OVL_TWO_PASS or when the basis would
+// exceed 32 GiB, an FP64 pass 1 followed by the FP64 regeneration pass.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -328,7 +329,7 @@ struct ovl_batch {
     std::vector<int> seq_ctx;   // context of each sequence
     int nseq = 0;
     int kcap = 0;
-    int mode = -1;              // 1 mixed, 0 FP64 one-pass
+    int mode = -1;              // 1 mixed, 0 FP64 one pass (basis stored), 2 FP64 two pass
     cudaStream_t st = nullptr;
     cudaStream_t cap_st = nullptr;
     // device memory
@@ -349,6 +350,10 @@ struct ovl_batch {
     double* part = nullptr;      // scratch of the per-sequence prologue kernels
     unsigned int* counter = nullptr;
     double2* stage = nullptr;    // host transfers
+    // per-phase profile (OVL_PROFILE): pass 1, inner sign, pass 2 / combination
+    double prof_ms[3] = {0.0, 0.0, 0.0};
+    int prof_n = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // graph
     cudaGraphExec_t exec = nullptr;
     int g_k = -1, g_flags = 0;
@@ -372,7 +377,7 @@ void bfree(ovl_batch* b) {
     b->mode = -1;
 }
 
-// Carve the batch's device memory for mode (1 mixed, 0 FP64 one-pass) and Krylov size kmax.
+// Carve the batch's device memory for mode (1 mixed, 0 FP64 one pass, 2 FP64 two pass) and Krylov size kmax.
 int balloc(ovl_batch* b, int mode, int kmax) {
     if (b->mem && b->mode == mode && b->kcap >= kmax) return OVL_OK;
     bfree(b);
@@ -394,7 +399,8 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         z += 4 * al(n * sizeof(double2));                        // b, bR, bL, y
         z += 3 * al(n * sizeof(double2));                        // regeneration ring
         if (mode == 1) z += 8 * al(n * sizeof(float2));          // FP32 v, w rings, t, s
-        else z += (kk + 5) * al(n * sizeof(double2));           // FP64 basis, w ring, t, s
+        else if (mode == 0) z += (kk + 5) * al(n * sizeof(double2));  // FP64 basis, w ring, t, s
+        else z += 8 * al(n * sizeof(double2));                  // FP64 v, w rings, t, s
         z += al((size_t)nblk * 4 * sizeof(double2)) + al(128 * sizeof(double2));  // partials, pq
         seq_bytes[s] = z;
         total += z;
@@ -449,11 +455,16 @@ int balloc(ovl_batch* b, int mode, int kmax) {
             q.t = take(n * sizeof(float2));
             q.s = take(n * sizeof(float2));
             q.V = nullptr;
-        } else {
+        } else if (mode == 0) {
             q.V = (double2*)take(kk * n * sizeof(double2));
             for (int j = 0; j < 3; ++j) q.w[j] = take(n * sizeof(double2)), q.v[j] = nullptr;
             q.t = take(n * sizeof(double2));
             q.s = take(n * sizeof(double2));
+        } else {
+            for (int j = 0; j < 3; ++j) q.v[j] = take(n * sizeof(double2)), q.w[j] = take(n * sizeof(double2));
+            q.t = take(n * sizeof(double2));
+            q.s = take(n * sizeof(double2));
+            q.V = nullptr;
         }
         q.ks = b->ks + s;
         q.alpha = b->alpha + s * kk;
@@ -485,7 +496,9 @@ int balloc(ovl_batch* b, int mode, int kmax) {
 // Everything between the packed sources and the unpacked results, on stream st.
 int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaStream_t st) {
     const bool mixed = b->mode == 1;
+    const bool twopass = b->mode != 0;
     const int ns = b->nseq;
+    const bool prof = (flags & OVL_PROFILE) != 0;
     for (int s = 0; s < ns; ++s) {
         ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const ovl::BSeq& q = b->hseq[s];
@@ -502,12 +515,13 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
             ovl::launch_native_f64_to_f32(b->bR[s], q.v[0], q.g, 1, st);
             ovl::launch_native_f64_to_f32(b->bL[s], q.w[0], q.g, 1, st);
         } else {
-            cudaMemcpyAsync(q.V, b->bR[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(q.V ? (void*)q.V : q.v[0], b->bR[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
             cudaMemcpyAsync(q.w[0], b->bL[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
         }
     }
     // pass 1 (all sequences per launch)
     const int nb = b->nblocks;
+    if (prof) cudaEventRecord(b->ev[0], st);
     for (int i = 0; i < k; ++i) {
         if (mixed) {
             ovl::k_b_pair<ovl::LINK_F32_12, float><<<nb, ovl::BT, 0, st>>>(
@@ -520,6 +534,7 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
         }
     }
     // inner sign of every sequence at once; Roberts' iteration where the quadrature did not settle
+    if (prof) cudaEventRecord(b->ev[1], st);
     const size_t kk = (size_t)b->kcap + 2;
     if (ovl::launch_inner_quadrature_batched(ns, b->alpha, b->beta, b->gamma, b->ks, b->cvec, kk, b->inner,
                                              b->inner_stride, b->kcap, b->qpart, b->qpart_stride, b->qcnt + ns, st))
@@ -533,7 +548,8 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
             return bfail(b, OVL_ECUDA, "inner sign fallback launch");
     }
     // combination
-    if (mixed) {
+    if (prof) cudaEventRecord(b->ev[2], st);
+    if (twopass) {
         for (int s = 0; s < ns; ++s) {
             const ovl::BSeq& q = b->hseq[s];
             ovl::launch_scale_start(b->bR[s], q.r[0], q.y, q.cvec, q.ks, q.n, st);
@@ -546,6 +562,7 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
             ovl::launch_combine(q.V, q.n, q.vscale, q.cvec, q.ks, b->kcap, q.y, q.n, st);
         }
     }
+    if (prof) cudaEventRecord(b->ev[3], st);
     return cudaGetLastError() == cudaSuccess ? OVL_OK : bfail(b, OVL_ECUDA, "batch launch");
 }
 
@@ -586,6 +603,8 @@ int ovl_batch_destroy(ovl_batch* b) {
     else cudaDeviceSynchronize();
     bfree(b);
     if (b->cap_st) cudaStreamDestroy(b->cap_st);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
     delete b;
     return OVL_OK;
 }
@@ -595,7 +614,11 @@ const char* ovl_batch_last_error(const ovl_batch* b) { return b ? b->err.c_str()
 int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* const* bsrc, void* const* out,
                     int flags, ovl_info* info) {
     if (!b || !bsrc || !out || k < 1) return bfail(b, OVL_EINVAL, "bad argument");
-    const int mode = (flags & OVL_MIXED) ? 1 : 0;
+    // FP64: the basis is stored when it fits a fixed budget, else the regeneration pass is used
+    size_t ntot = 0;
+    for (int q = 0; q < b->nseq; ++q) ntot += b->ctx[b->seq_ctx[q]]->n;
+    const bool fits = ((size_t)k + 2) * ntot * sizeof(double2) <= ((size_t)32 << 30);
+    const int mode = (flags & OVL_MIXED) ? 1 : ((flags & OVL_TWO_PASS) || !fits) ? 2 : 0;
     int r = balloc(b, mode, k);
     if (r) return r;
     for (ovl_ctx* c : b->ctx) {
@@ -621,8 +644,13 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
             ovl::launch_pack_spinor(src, b->b64[s], 0, c->g, st);
         }
     }
-    // the solve, as a graph captured once per (k, flags, mu, kappa)
-    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH);
+    // the solve, as a graph captured once per (k, flags, mu, kappa); per-phase events need eager launches
+    if (flags & OVL_PROFILE) {
+        flags |= OVL_NO_GRAPH;
+        for (cudaEvent_t& e : b->ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) return bfail(b, OVL_ECUDA, "profile events");
+    }
+    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH | OVL_TWO_PASS);
     if (flags & OVL_NO_GRAPH) {
         r = enqueue_batch(b, k, mu, kappa, flags, st);
         if (r) return r;
@@ -677,6 +705,14 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
     if (cudaMemcpyAsync(ks.data(), b->ks, b->nseq * sizeof(ovl::KState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return bfail(b, OVL_ECUDA, std::string("batch solve: ") + cudaGetErrorString(cudaGetLastError()));
+    if (flags & OVL_PROFILE) {
+        for (int j = 0; j < 3; ++j) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, b->ev[j], b->ev[j + 1]);
+            b->prof_ms[j] += ms;
+        }
+        b->prof_n += 1;
+    }
     int worst = OVL_OK;
     for (int q = 0; q < b->nseq; ++q) {
         if (info) {
@@ -697,6 +733,18 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
         }
     }
     return worst;
+}
+
+int ovl_batch_profile(ovl_batch* b, double* ms3, int* nsolves, int reset) {
+    if (!b) return OVL_EINVAL;
+    if (ms3)
+        for (int j = 0; j < 3; ++j) ms3[j] = b->prof_ms[j];
+    if (nsolves) *nsolves = b->prof_n;
+    if (reset) {
+        for (int j = 0; j < 3; ++j) b->prof_ms[j] = 0.0;
+        b->prof_n = 0;
+    }
+    return OVL_OK;
 }
 
 int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int k, double mu, double kappa,

@@ -34,7 +34,8 @@ EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl
            "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
            "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad", "ovl_batch_create",
-           "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_sign_krylov_batched"]
+           "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_batch_profile",
+           "ovl_sign_krylov_batched"]
 
 
 class OvlError(RuntimeError):
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
         "ovl_batch_destroy": (I, [P]),
         "ovl_batch_last_error": (ctypes.c_char_p, [P]),
         "ovl_batch_solve": (I, [P, I, D, D, ctypes.POINTER(P), ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
+        "ovl_batch_profile": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "ovl_sign_krylov_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, D, D, ctypes.POINTER(P),
                                         ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
     }
@@ -364,3 +366,11 @@ class Batch:
         if r and r != EBREAKDOWN:
             raise OvlError(r, self._lib.ovl_batch_last_error(self._h).decode())
         return outs, [i.as_dict() for i in infos], r
+
+    def profile(self, reset: bool = True):
+        """Per-phase totals of the OVL_PROFILE solves: {'pass1', 'inner_sign', 'pass2_or_combine'} in ms,
+        and the number of solves."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int()
+        self._lib.ovl_batch_profile(self._h, ms, ctypes.byref(n), 1 if reset else 0)
+        return {"pass1": ms[0], "inner_sign": ms[1], "pass2_or_combine": ms[2]}, n.value

@@ -47,8 +47,8 @@ def _sources(dims, seed, nrhs):
     return synth.gaussian_source(dims, seed, nrhs=nrhs)
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_batch_matches_dense(ovl, mid, mixed):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_two_pass", "mixed"])
+def test_batch_matches_dense(ovl, mid, mode):
     """Two lattices (4^4 and 4^2 x 2 x 6), 3 + 2 sources, every result against the dense oracle."""
     c4 = config4()
     assert c4["mu"] == mid["mu"]
@@ -56,10 +56,10 @@ def test_batch_matches_dense(ovl, mid, mixed):
     ba = _sources(c4["dims"], 3100, 3)
     bb = _sources(mid["dims"], 3101, 2)
     bt = ovl.Batch([ca, cb], [3, 2])
-    outs, infos, st = bt.solve(500, c4["mu"], KAPPA, [torch_c128(ba), torch_c128(bb)],
-                               flags=ovl.MIXED if mixed else 0)
+    flags = {"fp64": 0, "fp64_two_pass": ovl.TWO_PASS, "mixed": ovl.MIXED}[mode]
+    outs, infos, st = bt.solve(500, c4["mu"], KAPPA, [torch_c128(ba), torch_c128(bb)], flags=flags)
     assert st == 0 and len(infos) == 5
-    tol = 1e-8 if mixed else 1e-10
+    tol = 1e-8 if mode == "mixed" else 1e-10
     ya, yb = outs[0].cpu().numpy(), outs[1].cpu().numpy()
     sgn4 = c4["X"] @ (S.csign(c4["lam"])[:, None] * c4["Xi"])
     for r in range(3):
