@@ -82,6 +82,12 @@ typedef struct ovl_ctx ovl_ctx;
                                     differs from A at the 1e-8 level, which then bounds the accuracy */
 #define OVL_STEPWISE     0x40000 /* sign_krylov MIXED: one kernel per recurrence step instead of the
                                     persistent cooperative kernels (default on small lattices)   */
+#define OVL_PASS2_F64    0x80000 /* MIXED: regeneration pass in native FP64                       */
+#define OVL_PASS2_DF     0x100000 /* MIXED: regeneration pass in double-float arithmetic (FP32 pairs,
+                                    about 48 significant bits, on the FP32 pipe).  Default: double-
+                                    float in batched solves, FP64 in single solves (one source per
+                                    tile is latency bound, where double-float's longer dependency
+                                    chains cost more than the narrow FP64 pipe)                   */
 #define OVL_NO_GRAPH     0x2000  /* sign_krylov: launch kernels directly, no CUDA graph     */
 #define OVL_STENCIL_SITE  0x10000 /* apply_Dw: force one thread per site (default: by volume)    */
 #define OVL_STENCIL_SPLIT 0x20000 /* apply_Dw: force the direction-split layout (4 threads/site)   */

@@ -366,7 +366,8 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
             int lr = 0;
             prof(c, KC_PASS2, [&] {
                 double2* rr[3] = {c->R64[0], c->R64[1], c->R64[2]};
-                lr = ovl::launch_pass2_persistent(c->U64, rr, c->y64, ks, c->alpha, c->beta, c->gamma, c->cvec,
+                const float4* udf = (mixed && (flags & OVL_PASS2_DF)) ? c->Udf : nullptr;
+                lr = ovl::launch_pass2_persistent(c->U64, udf, rr, c->y64, ks, c->alpha, c->beta, c->gamma, c->cvec,
                                                   c->H, c->kcap, mu, kappa, c->bar, &ks->timeout, g, c->num_sms,
                                                   st);
             });
@@ -451,7 +452,7 @@ int ovl_destroy(ovl_ctx* c) {
     free_solve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
-    dfree(&c->U64), dfree(&c->U12), dfree(&c->U18);
+    dfree(&c->U64), dfree(&c->U12), dfree(&c->U18), dfree(&c->Udf);
     dfree(&c->R), dfree(&c->L), dfree(&c->lam), dfree(&c->R32), dfree(&c->L32);
     dfree(&c->b64), dfree(&c->y64), dfree(&c->bR), dfree(&c->bL), dfree(&c->t64), dfree(&c->s64);
     dfree(&c->t32), dfree(&c->s32), dfree(&c->ks), dfree(&c->counter), dfree(&c->bar), dfree(&c->stage_in),
@@ -482,7 +483,7 @@ int ovl_set_gauge(ovl_ctx* c, const void* U, int flags) {
     const size_t V = c->g.V;
     int r;
     if ((r = dalloc(c, &c->U64, V * 36 * sizeof(double2))) || (r = dalloc(c, &c->U12, V * 12 * sizeof(float4))) ||
-        (r = dalloc(c, &c->U18, V * 36 * sizeof(float2))))
+        (r = dalloc(c, &c->U18, V * 36 * sizeof(float2))) || (r = dalloc(c, &c->Udf, V * 36 * sizeof(float4))))
         return r;
     const double2* src = (const double2*)U;
     double2* tmp = nullptr;
@@ -491,7 +492,7 @@ int ovl_set_gauge(ovl_ctx* c, const void* U, int flags) {
         CUDA_TRY(c, cudaMemcpyAsync(tmp, U, V * 36 * sizeof(double2), cudaMemcpyHostToDevice, c->st));
         src = tmp;
     }
-    ovl::launch_pack_gauge(src, c->U64, c->U12, c->U18, c->g, c->st);
+    ovl::launch_pack_gauge(src, c->U64, c->U12, c->U18, c->Udf, c->g, c->st);
     CUDA_TRY(c, cudaGetLastError());
     if (tmp) {
         CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -655,7 +656,7 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
     ovl::launch_pack_spinor(bin, c->b64, 0, c->g, c->st);
     CUDA_TRY(c, cudaGetLastError());
 
-    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_STEPWISE);
+    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_STEPWISE | OVL_PASS2_F64 | OVL_PASS2_DF);
     bool ran = false;
     c->prof_on = (flags & OVL_PROFILE) != 0;
     if (!(flags & (OVL_NO_GRAPH | OVL_PROFILE))) {

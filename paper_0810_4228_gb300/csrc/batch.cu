@@ -14,7 +14,8 @@
 //
 // Mixed precision (OVL_MIXED): pass 1 in FP32 with 12-real links (in-block sums
 // of exact FP32 products in compensated pairs), pass 2 regenerates the basis
-// in FP64 from the pass-1 coefficients and accumulates y (Sec. 5).  Otherwise
+// from the pass-1 coefficients and accumulates y (Sec. 5) in double-float
+// arithmetic (df32.cuh; native FP64 with OVL_PASS2_F64).  Otherwise
 // FP64 throughout: one pass with the basis stored and the combination
 // y = sum_i c_i v_i at the end, or, with OVL_TWO_PASS or when the basis would
 // exceed 32 GiB, an FP64 pass 1 followed by the FP64 regeneration pass.
@@ -33,6 +34,7 @@ struct BSeq {
     size_t n;                 // 12 V
     const void* U;            // pass-1 links: FP32-12 (float4) or FP64 (double2)
     const double2* U64;       // FP64 links (regeneration)
+    const void* Udf;          // double-float links (regeneration of mixed solves)
     void* v[3];               // pass-1 ring (FP32 float4 pairs or FP64); unused with a stored basis
     void* w[3];
     void* t;
@@ -49,11 +51,13 @@ struct BSeq {
     double2* part;            // [nblk][4] block partials of the batched kernels
     unsigned int* cnt;        // ticket of this sequence
     int blk0, nblk;           // block range in the batched launches (blocks of BT sites)
+    int tile0, ntile;         // tile range in the tiled launches (tiles of TT sites)
 };
 
 namespace {
 
 constexpr int BT = 128;  // sites per block
+constexpr int TT = 32;   // sites per tile of the direction-split kernels (one warp per direction)
 
 template <class R> struct BVec;
 template <> struct BVec<float> { using T = float4; };
@@ -278,45 +282,73 @@ __global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, cons
     }
 }
 
-// FP64 regeneration (Sec. 5): r_{i+1} = ((A - alpha_i) r_i - gamma_{i-1} r_{i-1}) / beta_i,
-// y += c_{i+1} r_{i+1}
-__global__ void __launch_bounds__(BT) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
-                                                HopCoef<double> hc) {
-    const BSeq& q = S[bseq[blockIdx.x]];
+// Regeneration (Sec. 5): r_{i+1} = ((A - alpha_i) r_i - gamma_{i-1} r_{i-1}) / beta_i, y += c_{i+1} r_{i+1},
+// in FP64 (R = double) or double-float (R = df; ring and y converted beforehand).  One block per
+// 32-site tile of a sequence: warp w applies both hops of direction w to the tile's sites, the
+// four partial sums meet in shared memory, and 128 threads (site, spin) finish three components each.
+template <class R> __device__ __forceinline__ cx<R> cvt_coef(cx<double> z);
+template <> __device__ __forceinline__ cx<double> cvt_coef<double>(cx<double> z) { return z; }
+template <> __device__ __forceinline__ cx<df> cvt_coef<df>(cx<double> z) { return mk(df(z.r), df(z.i)); }
+
+template <class R, int LF>
+__global__ void __launch_bounds__(4 * TT) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
+                                                    HopCoef<R> hc) {
+    using VT = typename VecT<R>::T;
+    __shared__ cx<R> dirpart[4][TT][12];
+    __shared__ cx<R> cf[4];
+    const BSeq& q = S[tseq[blockIdx.x]];
     const KState* ks = q.ks;
     if (ks->status || i + 1 >= ks->kused) return;
-    __shared__ cx<double> cf[4];
     if (threadIdx.x == 0) {
         const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(q.beta[i]));
-        cf[0] = ib;
-        cf[1] = ib * d2c(q.alpha[i]);
-        cf[2] = i > 0 ? ib * d2c(q.gamma[i - 1]) : mk(0.0, 0.0);
-        cf[3] = d2c(q.cvec[i + 1]);
+        cf[0] = cvt_coef<R>(ib);
+        cf[1] = cvt_coef<R>(ib * d2c(q.alpha[i]));
+        cf[2] = cvt_coef<R>(i > 0 ? ib * d2c(q.gamma[i - 1]) : mk(0.0, 0.0));
+        cf[3] = cvt_coef<R>(d2c(q.cvec[i + 1]));
+    }
+    const int tile = blockIdx.x - q.tile0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const VT* ri = (const VT*)q.r[i % 3];
+    const void* U = LF == LINK_DF ? q.Udf : (const void*)q.U64;
+    {
+        const int i0 = tile * TT + lane;
+        Spinor<R> acc[1];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[0].s[s][c] = mk(R(0), R(0));
+        if (i0 < q.g.V) {
+            const Coord c = site_coord(q.g, i0);
+            const VT* const xs[1] = {ri};
+            const HopCoef<R> hcs[1] = {hc};
+            switch (wid) {
+                case 0: hops_dir<0, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
+                case 1: hops_dir<1, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
+                case 2: hops_dir<2, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
+                default: hops_dir<3, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) dirpart[wid][lane][c] = acc[0].s[c / 3][c % 3];
     }
     __syncthreads();
-    const int site = (blockIdx.x - q.blk0) * BT + threadIdx.x;
-    if (site >= q.g.V) return;
-    const double2* ri = q.r[i % 3];
-    const double2* const xs[1] = {ri};
-    const HopCoef<double> hcs[1] = {hc};
-    Spinor<double> acc[1], self, rm;
-    apply_site<LINK_F64, double, 1>(q.g, site, q.U64, xs, acc, hcs);
-    load_spinor(ri, q.g.V, site, self);
-    finish_site(acc[0], self, true);
-    if (i > 0) load_spinor(q.r[(i + 2) % 3], q.g.V, site, rm);
-    double2* rn = q.r[(i + 1) % 3];
+    const int site = threadIdx.x >> 2, sp = threadIdx.x & 3;
+    const int ii = tile * TT + site;
+    if (ii >= q.g.V) return;
+    const VT* rm = (const VT*)q.r[(i + 2) % 3];
+    VT* rn = (VT*)q.r[(i + 1) % 3];
+    VT* y = (VT*)q.y;
 #pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cx<double> z = cf[0] * acc[0].s[sp][c] - cf[1] * self.s[sp][c];
-            if (i > 0) z = z - cf[2] * rm.s[sp][c];
-            const size_t e = (size_t)(3 * sp + c) * q.g.V + site;
-            rn[e] = c2d(z);
-            cx<double> yy = d2c(q.y[e]);
-            cfma(yy, cf[3], z);
-            q.y[e] = c2d(yy);
-        }
+    for (int c3 = 0; c3 < 3; ++c3) {
+        const int c = 3 * sp + c3;
+        const cx<R> self = ld_comp_cg<R>(ri, q.g.V, ii, c);
+        cx<R> z = self + dirpart[0][site][c] + dirpart[1][site][c] + dirpart[2][site][c] + dirpart[3][site][c];
+        if (sp >= 2) z = -z;
+        z = cf[0] * z - cf[1] * self;
+        if (i > 0) z = z - cf[2] * ld_comp_cg<R>(rm, q.g.V, ii, c);
+        st_comp<R>(rn, q.g.V, ii, c, z);
+        st_comp<R>(y, q.g.V, ii, c, ld_comp_cg<R>(y, q.g.V, ii, c) + cf[3] * z);
+    }
 }
 
 }  // namespace
@@ -337,7 +369,9 @@ struct ovl_batch {
     size_t mem_bytes = 0;
     ovl::BSeq* dseq = nullptr;
     int* dbseq = nullptr;
+    int* dtseq = nullptr;
     int nblocks = 0;
+    int ntiles = 0;
     std::vector<ovl::BSeq> hseq;
     std::vector<double2*> b64, bR, bL, pq;
     ovl::KState* ks = nullptr;
@@ -389,12 +423,13 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t total = 0;
     std::vector<size_t> seq_bytes(ns);
-    int nblocks = 0;
+    int nblocks = 0, ntiles = 0;
     for (int s = 0; s < ns; ++s) {
         const ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const size_t n = c->n;
         const int nblk = (c->g.V + ovl::BT - 1) / ovl::BT;
         nblocks += nblk;
+        ntiles += (c->g.V + ovl::TT - 1) / ovl::TT;
         size_t z = 0;
         z += 4 * al(n * sizeof(double2));                        // b, bR, bL, y
         z += 3 * al(n * sizeof(double2));                        // regeneration ring
@@ -408,6 +443,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     total += al(ns * sizeof(ovl::KState)) + 5 * al(ns * kk * sizeof(double2)) +
              al((size_t)ns * inner_stride * sizeof(double2)) + al((size_t)ns * qpart_stride * sizeof(double)) +
              al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks * sizeof(int)) +
+             al(ntiles * sizeof(int)) +
              al((size_t)(1 << 20) * sizeof(double)) + al(64 * sizeof(unsigned int));
     if (cudaMalloc(&b->mem, total) != cudaSuccess) {
         b->mem = nullptr;
@@ -429,13 +465,15 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     b->qcnt = (unsigned int*)take(ns * 64 * sizeof(unsigned int));
     b->dseq = (ovl::BSeq*)take(ns * sizeof(ovl::BSeq));
     b->dbseq = (int*)take(nblocks * sizeof(int));
+    b->dtseq = (int*)take(ntiles * sizeof(int));
     b->part = (double*)take((size_t)(1 << 20) * sizeof(double));
     b->counter = (unsigned int*)take(64 * sizeof(unsigned int));
     b->hseq.assign(ns, ovl::BSeq());
     b->b64.assign(ns, nullptr), b->bR.assign(ns, nullptr), b->bL.assign(ns, nullptr), b->pq.assign(ns, nullptr);
-    std::vector<int> table;
+    std::vector<int> table, ttable;
     table.reserve(nblocks);
-    int blk0 = 0;
+    ttable.reserve(ntiles);
+    int blk0 = 0, tile0 = 0;
     for (int s = 0; s < ns; ++s) {
         ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const size_t n = c->n;
@@ -445,6 +483,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         q.n = n;
         q.U = mode == 1 ? (const void*)c->U12 : (const void*)c->U64;
         q.U64 = c->U64;
+        q.Udf = c->Udf;
         b->b64[s] = (double2*)take(n * sizeof(double2));
         b->bR[s] = (double2*)take(n * sizeof(double2));
         b->bL[s] = (double2*)take(n * sizeof(double2));
@@ -479,10 +518,16 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         q.blk0 = blk0;
         for (int j = 0; j < q.nblk; ++j) table.push_back(s);
         blk0 += q.nblk;
+        q.ntile = (c->g.V + ovl::TT - 1) / ovl::TT;
+        q.tile0 = tile0;
+        for (int j = 0; j < q.ntile; ++j) ttable.push_back(s);
+        tile0 += q.ntile;
     }
     b->nblocks = blk0;
+    b->ntiles = tile0;
     if (cudaMemcpy(b->dseq, b->hseq.data(), ns * sizeof(ovl::BSeq), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dbseq, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dtseq, ttable.data(), ttable.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->qcnt, 0, ns * 64 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(b->counter, 0, 64 * sizeof(unsigned int)) != cudaSuccess) {
         bfree(b);
@@ -550,12 +595,27 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
     // combination
     if (prof) cudaEventRecord(b->ev[2], st);
     if (twopass) {
+        // mixed: double-float regeneration unless OVL_PASS2_F64 (ring and y converted in place)
+        const int nt = b->ntiles;
+        const bool dfm = mixed && !(flags & OVL_PASS2_F64);
         for (int s = 0; s < ns; ++s) {
             const ovl::BSeq& q = b->hseq[s];
             ovl::launch_scale_start(b->bR[s], q.r[0], q.y, q.cvec, q.ks, q.n, st);
+            if (dfm) {
+                ovl::launch_f64_to_df(q.r[0], q.n, st);
+                ovl::launch_f64_to_df(q.y, q.n, st);
+            }
         }
-        for (int i = 0; i + 1 < k; ++i)
-            ovl::k_b_regen<<<nb, ovl::BT, 0, st>>>(b->dseq, b->dbseq, i, ovl::make_coef<double>(mu, kappa));
+        for (int i = 0; i + 1 < k; ++i) {
+            if (dfm)
+                ovl::k_b_regen<ovl::df, ovl::LINK_DF><<<nt, 4 * ovl::TT, 0, st>>>(b->dseq, b->dtseq, i,
+                                                                                  ovl::make_coef<ovl::df>(mu, kappa));
+            else
+                ovl::k_b_regen<double, ovl::LINK_F64><<<nt, 4 * ovl::TT, 0, st>>>(b->dseq, b->dtseq, i,
+                                                                                  ovl::make_coef<double>(mu, kappa));
+        }
+        if (dfm)
+            for (int s = 0; s < ns; ++s) ovl::launch_df_to_f64(b->hseq[s].y, b->hseq[s].n, st);
     } else {
         for (int s = 0; s < ns; ++s) {
             const ovl::BSeq& q = b->hseq[s];
@@ -650,7 +710,7 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
         for (cudaEvent_t& e : b->ev)
             if (!e && cudaEventCreate(&e) != cudaSuccess) return bfail(b, OVL_ECUDA, "profile events");
     }
-    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH | OVL_TWO_PASS);
+    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH | OVL_TWO_PASS | OVL_PASS2_F64);
     if (flags & OVL_NO_GRAPH) {
         r = enqueue_batch(b, k, mu, kappa, flags, st);
         if (r) return r;

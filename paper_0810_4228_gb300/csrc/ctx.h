@@ -46,6 +46,7 @@ struct ovl_ctx {
     double2* U64 = nullptr;
     float4* U12 = nullptr;
     float2* U18 = nullptr;
+    float4* Udf = nullptr;  // double-float links (regeneration pass of mixed solves)
     bool have_gauge = false;
 
     // deflation

@@ -112,6 +112,12 @@ OVL_HD int neighbour(const Geom& g, const Coord& c, int nu, int dir) {
 template <class R> struct Spinor { cx<R> s[4][3]; };
 template <class R> struct Half { cx<R> h[2][3]; };
 
+// S x for S = +1 or -1 (no multiplication)
+template <int S, class T> OVL_HD T sgn_mul(T x) {
+    if constexpr (S > 0) return x;
+    else return -x;
+}
+
 // Spin projection (1 + S gamma_nu) psi -> half spinor h (upper two spins of the
 // result), chiral basis gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
 // gamma_4 = [[0, 1], [1, 0]].  The lower two spins of (1 + S gamma_nu) psi are
@@ -121,17 +127,17 @@ OVL_HD void project(const Spinor<R>& p, Half<R>& h) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (NU == 0) {          // sigma_1
-            h.h[0][a] = p.s[0][a] - R(S) * times_i(p.s[3][a]);
-            h.h[1][a] = p.s[1][a] - R(S) * times_i(p.s[2][a]);
+            h.h[0][a] = p.s[0][a] - sgn_mul<S>(times_i(p.s[3][a]));
+            h.h[1][a] = p.s[1][a] - sgn_mul<S>(times_i(p.s[2][a]));
         } else if (NU == 1) {   // sigma_2
-            h.h[0][a] = p.s[0][a] - R(S) * p.s[3][a];
-            h.h[1][a] = p.s[1][a] + R(S) * p.s[2][a];
+            h.h[0][a] = p.s[0][a] - sgn_mul<S>(p.s[3][a]);
+            h.h[1][a] = p.s[1][a] + sgn_mul<S>(p.s[2][a]);
         } else if (NU == 2) {   // sigma_3
-            h.h[0][a] = p.s[0][a] - R(S) * times_i(p.s[2][a]);
-            h.h[1][a] = p.s[1][a] + R(S) * times_i(p.s[3][a]);
+            h.h[0][a] = p.s[0][a] - sgn_mul<S>(times_i(p.s[2][a]));
+            h.h[1][a] = p.s[1][a] + sgn_mul<S>(times_i(p.s[3][a]));
         } else {                // gamma_4
-            h.h[0][a] = p.s[0][a] + R(S) * p.s[2][a];
-            h.h[1][a] = p.s[1][a] + R(S) * p.s[3][a];
+            h.h[0][a] = p.s[0][a] + sgn_mul<S>(p.s[2][a]);
+            h.h[1][a] = p.s[1][a] + sgn_mul<S>(p.s[3][a]);
         }
     }
 }
@@ -145,17 +151,17 @@ OVL_HD void recon_acc(Spinor<R>& acc, const Half<R>& h, R coef) {
         acc.s[0][a] = acc.s[0][a] + h0;
         acc.s[1][a] = acc.s[1][a] + h1;
         if (NU == 0) {
-            acc.s[2][a] = acc.s[2][a] + R(S) * times_i(h1);
-            acc.s[3][a] = acc.s[3][a] + R(S) * times_i(h0);
+            acc.s[2][a] = acc.s[2][a] + sgn_mul<S>(times_i(h1));
+            acc.s[3][a] = acc.s[3][a] + sgn_mul<S>(times_i(h0));
         } else if (NU == 1) {
-            acc.s[2][a] = acc.s[2][a] + R(S) * h1;
-            acc.s[3][a] = acc.s[3][a] - R(S) * h0;
+            acc.s[2][a] = acc.s[2][a] + sgn_mul<S>(h1);
+            acc.s[3][a] = acc.s[3][a] - sgn_mul<S>(h0);
         } else if (NU == 2) {
-            acc.s[2][a] = acc.s[2][a] + R(S) * times_i(h0);
-            acc.s[3][a] = acc.s[3][a] - R(S) * times_i(h1);
+            acc.s[2][a] = acc.s[2][a] + sgn_mul<S>(times_i(h0));
+            acc.s[3][a] = acc.s[3][a] - sgn_mul<S>(times_i(h1));
         } else {
-            acc.s[2][a] = acc.s[2][a] + R(S) * h0;
-            acc.s[3][a] = acc.s[3][a] + R(S) * h1;
+            acc.s[2][a] = acc.s[2][a] + sgn_mul<S>(h0);
+            acc.s[3][a] = acc.s[3][a] + sgn_mul<S>(h1);
         }
     }
 }
@@ -204,7 +210,8 @@ OVL_HD void reconstruct_row2(Link<R>& U) {
 // FP64 links: double2 U[nu][e][V], e = 3*row + col.
 // FP32 12-real links: float4 U[nu][q][V], rows 0,1 = (u00,u01),(u02,u10),(u11,u12).
 // FP32 18-real links: float2 U[nu][e][V].
-enum LinkFmt { LINK_F64 = 0, LINK_F32_12 = 1, LINK_F32_18 = 2 };
+// Double-float links (df32.cuh): float4 U[nu][e][V] = {re.hi, re.lo, im.hi, im.lo}.
+enum LinkFmt { LINK_F64 = 0, LINK_F32_12 = 1, LINK_F32_18 = 2, LINK_DF = 3 };
 
 __device__ __forceinline__ void load_spinor(const double2* __restrict__ x, int V, int i, Spinor<double>& p) {
 #pragma unroll

@@ -34,8 +34,12 @@ struct KState {
 struct Workspace;   // defined in api.cu
 
 // ---- stencil.cu
-void launch_pack_gauge(const double2* U_canon, double2* U64, float4* U12, float2* U18, const Geom& g,
+// Udf: the double-float copy of the links (float4 {re.hi, re.lo, im.hi, im.lo} in the FP64 layout)
+void launch_pack_gauge(const double2* U_canon, double2* U64, float4* U12, float2* U18, float4* Udf, const Geom& g,
                        cudaStream_t st);
+// in place: FP64 vectors (double2) -> double-float (float4 {hi, lo, hi, lo}), n complex each; and back
+void launch_f64_to_df(void* x, size_t n, cudaStream_t st);
+void launch_df_to_f64(void* x, size_t n, cudaStream_t st);
 void launch_pack_spinor(const double2* canon, void* native, int prec, const Geom& g, cudaStream_t st);
 // out_canon = b_canon (if given) + (g5 ? gamma5 : 1) * native
 void launch_unpack_spinor(const void* native, int prec, double2* canon, const double2* b_canon, int g5,
@@ -105,8 +109,10 @@ int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const
                             double2* beta, double2* gamma, const float2* R32, const float2* L32, int m, double mu,
                             double kappa, int k, double* partials, unsigned int* bar, const Geom& g, int num_sms,
                             cudaStream_t st);
-// coef_work: 4 (kmax + 1) double2 of scratch for the per-step regeneration coefficients
-int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y, const KState* ks,
+// coef_work: 4 (kmax + 1) double2 of scratch for the per-step regeneration coefficients.
+// Udf non-null: double-float arithmetic (links Udf; v[] are converted to double-float in place, so
+// v[0] must hold the FP64 start vector and all three are left in double-float); else FP64 (links U64).
+int launch_pass2_persistent(const double2* U64, const float4* Udf, double2* const v[3], double2* y, const KState* ks,
                             const double2* alpha, const double2* beta, const double2* gamma, const double2* c,
                             double2* coef_work, int kmax, double mu, double kappa, unsigned int* bar, int* err,
                             const Geom& g, int num_sms, cudaStream_t st);

@@ -419,52 +419,68 @@ __global__ void __launch_bounds__(32 * PW1) k_pass1_persistent(P1Args a) {
 }
 
 // Per-step coefficients of the regeneration, formed once: v_{i+1} = ib (A v_i) - a' v_i - g' v_{i-1},
-// ib = 1 / beta_i, a' = ib alpha_i, g' = ib gamma_{i-1}; y += c_{i+1} v_{i+1}.
-struct RegenCoef {
-    double2 ib, a, g, c;
+// ib = 1 / beta_i, a' = ib alpha_i, g' = ib gamma_{i-1}; y += c_{i+1} v_{i+1}.  Stored in the
+// precision of the pass (double2, or double-float dfc).
+template <class VT> struct RegenCoef {
+    VT ib, a, g, c;
 };
+__device__ __forceinline__ void put(double2& o, cx<double> z) { o = c2d(z); }
+__device__ __forceinline__ void put(dfc& o, cx<double> z) { o = c2dfc(mk(df(z.r), df(z.i))); }
+__device__ __forceinline__ cx<double> get(const double2& v) { return d2c(v); }
+__device__ __forceinline__ cx<df> get(const dfc& v) { return dfc2c(v); }
 
+template <class VT>
 __global__ void k_pass2_coef(const KState* ks, const double2* alpha, const double2* beta, const double2* gamma,
-                             const double2* c, RegenCoef* out, int kmax, unsigned int* bar) {
+                             const double2* c, RegenCoef<VT>* out, int kmax, unsigned int* bar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) bar[0] = 0u;  // arrival counter of the pass-2 barriers
     if (i + 1 >= kmax || i + 1 >= ks->kused) return;
     const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(beta[i]));
-    RegenCoef r;
-    r.ib = c2d(ib);
-    r.a = c2d(ib * d2c(alpha[i]));
-    r.g = c2d(i > 0 ? ib * d2c(gamma[i - 1]) : mk(0.0, 0.0));
-    r.c = c[i + 1];
+    RegenCoef<VT> r;
+    put(r.ib, ib);
+    put(r.a, ib * d2c(alpha[i]));
+    put(r.g, i > 0 ? ib * d2c(gamma[i - 1]) : mk(0.0, 0.0));
+    put(r.c, d2c(c[i + 1]));
     out[i] = r;
 }
 
-struct P2Args {
-    const double2* U;
-    double2* v[3];
+template <class R> struct P2Args {
+    const void* U;
+    void* v[3];
     double2* y;
     const KState* ks;
-    const RegenCoef* cf;
+    const void* cf;
     unsigned int* bar;
     int* err;
-    HopCoef<double> hc;
+    HopCoef<R> hc[1];
     Geom g;
     int ntiles;
 };
 
-// pass-2 own-site state: slots 0/1 alternate as v_i and v_{i-1}, slot 2 accumulates y
+// FP64 (R = double) or double-float (R = df) pass-2 state: slots 0/1 alternate as v_i and v_{i-1},
+// slot 2 accumulates y
 __device__ __forceinline__ int st2_idx(int jt, int slot, int site, int q) { return ((jt * 3 + slot) * PT + site) * 12 + q; }
 
-// FP64 regeneration v_{i+1} = ((A - alpha_i) v_i - gamma_{i-1} v_{i-1}) / beta_i, y += c_{i+1} v_{i+1}
-__global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
+template <class R> __device__ __forceinline__ cx<R> from_f64(double2 v);
+template <> __device__ __forceinline__ cx<double> from_f64<double>(double2 v) { return d2c(v); }
+template <> __device__ __forceinline__ cx<df> from_f64<df>(double2 v) { return d2df(v); }
+__device__ __forceinline__ double2 to_f64(cx<double> z) { return c2d(z); }
+__device__ __forceinline__ double2 to_f64(cx<df> z) { return df2d(z); }
+
+// regeneration v_{i+1} = ((A - alpha_i) v_i - gamma_{i-1} v_{i-1}) / beta_i, y += c_{i+1} v_{i+1} (Sec. 5)
+template <class R, int LF>
+__global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args<R> a) {
+    using VT = typename VecT<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<double>* dirpart = reinterpret_cast<cx<double>*>(smraw);  // [PW2][PT][12]
-    cx<double>* st = dirpart + PW2 * PT * 12;                    // [tpb][3][PT][12]
+    cx<R>* dirpart = reinterpret_cast<cx<R>*>(smraw);  // [PW2][PT][12]
+    cx<R>* st = dirpart + PW2 * PT * 12;               // [tpb][3][PT][12]
     if (a.ks->status) return;
     const int kused = a.ks->kused;
     const Geom g = a.g;
     const int G = gridDim.x;
     const int tid = threadIdx.x, site = tid >> 2, sp = tid & 3;
     const int lane = tid & 31, wid = tid >> 5;
+    const RegenCoef<VT>* cfs = reinterpret_cast<const RegenCoef<VT>*>(a.cf);
     {
         int jt = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += G, ++jt) {
@@ -473,40 +489,39 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
 #pragma unroll
             for (int c3 = 0; c3 < 3; ++c3) {
                 const int q = 3 * sp + c3;
-                st[st2_idx(jt, 0, site, q)] = ok ? d2c(__ldcg(a.v[0] + (size_t)q * g.V + ii)) : mk(0.0, 0.0);
-                st[st2_idx(jt, 1, site, q)] = mk(0.0, 0.0);
-                st[st2_idx(jt, 2, site, q)] = ok ? d2c(__ldcg(a.y + (size_t)q * g.V + ii)) : mk(0.0, 0.0);
+                st[st2_idx(jt, 0, site, q)] = ok ? ld_comp_cg<R>((const VT*)a.v[0], g.V, ii, q) : mk(R(0), R(0));
+                st[st2_idx(jt, 1, site, q)] = mk(R(0), R(0));
+                st[st2_idx(jt, 2, site, q)] = ok ? from_f64<R>(__ldcg(a.y + (size_t)q * g.V + ii)) : mk(R(0), R(0));
             }
         }
     }
     __syncthreads();
-    RegenCoef cf;
-    if (kused > 1) cf = a.cf[0];
+    RegenCoef<VT> cf;
+    if (kused > 1) cf = cfs[0];
     unsigned int nbar = 0;
     for (int i = 0; i + 1 < kused; ++i) {
         const int cur = i & 1, prv = cur ^ 1;
-        const double2* vi = a.v[i % 3];
-        double2* vn = a.v[(i + 1) % 3];
-        const cx<double> ib = d2c(cf.ib), al = d2c(cf.a), gm = d2c(cf.g), cc = d2c(cf.c);
-        if (i + 2 < kused) cf = a.cf[i + 1];  // next step's coefficients, loaded ahead
+        const VT* vi = (const VT*)a.v[i % 3];
+        VT* vn = (VT*)a.v[(i + 1) % 3];
+        const cx<R> ib = get(cf.ib), al = get(cf.a), gm = get(cf.g), cc = get(cf.c);
+        if (i + 2 < kused) cf = cfs[i + 1];  // next step's coefficients, loaded ahead
         int jt = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += G, ++jt) {
             {
                 const int i0 = tile * PT + lane;
-                Spinor<double> acc[1];
+                Spinor<R> acc[1];
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) acc[0].s[s][c] = mk(0.0, 0.0);
+                    for (int c = 0; c < 3; ++c) acc[0].s[s][c] = mk(R(0), R(0));
                 if (i0 < g.V) {
                     const Coord c = site_coord(g, i0);
-                    const double2* const xs[1] = {vi};
-                    const HopCoef<double> hcs[1] = {a.hc};
+                    const VT* const xs[1] = {vi};
                     switch (wid) {
-                        case 0: hops_dir<0, LINK_F64, double, 1, true>(g, c, i0, a.U, xs, acc, hcs); break;
-                        case 1: hops_dir<1, LINK_F64, double, 1, true>(g, c, i0, a.U, xs, acc, hcs); break;
-                        case 2: hops_dir<2, LINK_F64, double, 1, true>(g, c, i0, a.U, xs, acc, hcs); break;
-                        default: hops_dir<3, LINK_F64, double, 1, true>(g, c, i0, a.U, xs, acc, hcs); break;
+                        case 0: hops_dir<0, LF, R, 1, true>(g, c, i0, a.U, xs, acc, a.hc); break;
+                        case 1: hops_dir<1, LF, R, 1, true>(g, c, i0, a.U, xs, acc, a.hc); break;
+                        case 2: hops_dir<2, LF, R, 1, true>(g, c, i0, a.U, xs, acc, a.hc); break;
+                        default: hops_dir<3, LF, R, 1, true>(g, c, i0, a.U, xs, acc, a.hc); break;
                     }
                 }
 #pragma unroll
@@ -518,18 +533,16 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
 #pragma unroll
                 for (int c3 = 0; c3 < 3; ++c3) {
                     const int q = 3 * sp + c3;
-                    const cx<double> self = st[st2_idx(jt, cur, site, q)];
-                    cx<double> z = self;
+                    const cx<R> self = st[st2_idx(jt, cur, site, q)];
+                    cx<R> z = self;
 #pragma unroll
                     for (int w4 = 0; w4 < PW2; ++w4) z = z + dirpart[(w4 * PT + site) * 12 + q];
                     if (sp >= 2) z = -z;
                     z = ib * z - al * self;
                     if (i > 0) z = z - gm * st[st2_idx(jt, prv, site, q)];
-                    vn[(size_t)q * g.V + ii] = c2d(z);
+                    st_comp<R>(vn, g.V, ii, q, z);
                     st[st2_idx(jt, prv, site, q)] = z;
-                    cx<double> yy = st[st2_idx(jt, 2, site, q)];
-                    cfma(yy, cc, z);
-                    st[st2_idx(jt, 2, site, q)] = yy;
+                    st[st2_idx(jt, 2, site, q)] = st[st2_idx(jt, 2, site, q)] + cc * z;
                 }
             }
             __syncthreads();
@@ -546,7 +559,7 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
 #pragma unroll
         for (int c3 = 0; c3 < 3; ++c3) {
             const int q = 3 * sp + c3;
-            a.y[(size_t)q * g.V + ii] = c2d(st[st2_idx(jt, 2, site, q)]);
+            a.y[(size_t)q * g.V + ii] = to_f64(st[st2_idx(jt, 2, site, q)]);
         }
     }
 }
@@ -554,7 +567,7 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args a) {
 static int persistent_grid(int ntiles, int num_sms) { return std::max(1, std::min(ntiles, num_sms)); }
 
 static size_t pass1_smem(int tpb) { return sizeof(cx<float>) * ((size_t)PW1 * 2 * PT * 12 + (size_t)tpb * 3 * 2 * PT * 12); }
-static size_t pass2_smem(int tpb) { return sizeof(cx<double>) * ((size_t)PW2 * PT * 12 + (size_t)tpb * 3 * PT * 12); }
+static size_t pass2_smem(int tpb) { return 16 * ((size_t)PW2 * PT * 12 + (size_t)tpb * 3 * PT * 12); }
 
 bool persistent_ok(const Geom& g, int num_sms) {
     // own-site state of every tile of a block fits in shared memory
@@ -608,29 +621,12 @@ int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const
     return (int)cudaLaunchKernelEx(&cfg, k_pass1_persistent, a);
 }
 
-int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y, const KState* ks,
-                            const double2* alpha, const double2* beta, const double2* gamma, const double2* c,
-                            double2* coef_work, int kmax, double mu, double kappa, unsigned int* bar, int* err,
-                            const Geom& g, int num_sms, cudaStream_t st) {
-    RegenCoef* cfw = reinterpret_cast<RegenCoef*>(coef_work);
-    k_pass2_coef<<<(kmax + 127) / 128, 128, 0, st>>>(ks, alpha, beta, gamma, c, cfw, kmax, bar);
-    P2Args a;
-    a.U = U64;
-    for (int q = 0; q < 3; ++q) a.v[q] = v[q];
-    a.y = y;
-    a.ks = ks;
-    a.cf = cfw;
-    a.bar = bar;
-    a.err = err;
-    a.hc = make_coef<double>(mu, kappa);
-    a.g = g;
-    a.ntiles = (g.V + PT - 1) / PT;
-    const int G = persistent_grid(a.ntiles, num_sms);
-    const int tpb = (a.ntiles + G - 1) / G;
-    if (tpb > PMAX_TPB) return -1;
+template <class R, int LF>
+static int launch_p2(P2Args<R> a, HopCoef<R> hc, int G, int tpb, cudaStream_t st) {
+    a.hc[0] = hc;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_pass2_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_pass2_persistent<R, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pass2_smem(PMAX_TPB));
         attr = true;
     }
@@ -644,7 +640,43 @@ int launch_pass2_persistent(const double2* U64, double2* const v[3], double2* y,
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return (int)cudaLaunchKernelEx(&cfg, k_pass2_persistent, a);
+    return (int)cudaLaunchKernelEx(&cfg, k_pass2_persistent<R, LF>, a);
+}
+
+int launch_pass2_persistent(const double2* U64, const float4* Udf, double2* const v[3], double2* y, const KState* ks,
+                            const double2* alpha, const double2* beta, const double2* gamma, const double2* c,
+                            double2* coef_work, int kmax, double mu, double kappa, unsigned int* bar, int* err,
+                            const Geom& g, int num_sms, cudaStream_t st) {
+    const bool dfm = Udf != nullptr;
+    const int ntiles = (g.V + PT - 1) / PT;
+    const int G = persistent_grid(ntiles, num_sms);
+    const int tpb = (ntiles + G - 1) / G;
+    auto fill = [&](auto& a) {
+        a.U = dfm ? (const void*)Udf : (const void*)U64;
+        for (int q = 0; q < 3; ++q) a.v[q] = v[q];
+        a.y = y;
+        a.ks = ks;
+        a.cf = coef_work;
+        a.bar = bar;
+        a.err = err;
+        a.g = g;
+        a.ntiles = ntiles;
+    };
+    if (tpb > PMAX_TPB) return -1;
+    if (dfm) {
+        k_pass2_coef<dfc><<<(kmax + 127) / 128, 128, 0, st>>>(ks, alpha, beta, gamma, c,
+                                                              reinterpret_cast<RegenCoef<dfc>*>(coef_work), kmax, bar);
+        launch_f64_to_df(v[0], (size_t)12 * g.V, st);
+        P2Args<df> a;
+        fill(a);
+        return launch_p2<df, LINK_DF>(a, make_coef<df>(mu, kappa), G, tpb, st);
+    }
+    k_pass2_coef<double2><<<(kmax + 127) / 128, 128, 0, st>>>(ks, alpha, beta, gamma, c,
+                                                               reinterpret_cast<RegenCoef<double2>*>(coef_work), kmax,
+                                                               bar);
+    P2Args<double> a;
+    fill(a);
+    return launch_p2<double, LINK_F64>(a, make_coef<double>(mu, kappa), G, tpb, st);
 }
 
 }  // namespace ovl

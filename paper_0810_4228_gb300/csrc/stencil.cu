@@ -424,7 +424,7 @@ void launch_native_f64_to_f32(const double2* x, void* y, const Geom& g, int nvec
 
 // ---------------------------------------------------------------- layouts --
 __global__ void k_pack_gauge(const double2* __restrict__ Uc, double2* __restrict__ U64, float4* __restrict__ U12,
-                             float2* __restrict__ U18, Geom g) {
+                             float2* __restrict__ U18, float4* __restrict__ Udf, Geom g) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.V) return;
     const Coord c = site_coord(g, i);
@@ -435,6 +435,8 @@ __global__ void k_pack_gauge(const double2* __restrict__ Uc, double2* __restrict
         for (int q = 0; q < 9; ++q) {
             U64[((size_t)nu * 9 + q) * g.V + i] = e[q];
             U18[((size_t)nu * 9 + q) * g.V + i] = make_float2((float)e[q].x, (float)e[q].y);
+            const dfc d = c2dfc(d2df(e[q]));
+            Udf[((size_t)nu * 9 + q) * g.V + i] = make_float4(d.rh, d.rl, d.ih, d.il);
         }
         U12[((size_t)nu * 3 + 0) * g.V + i] = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
         U12[((size_t)nu * 3 + 1) * g.V + i] = make_float4(e[2].x, e[2].y, e[3].x, e[3].y);
@@ -442,9 +444,28 @@ __global__ void k_pack_gauge(const double2* __restrict__ Uc, double2* __restrict
     }
 }
 
-void launch_pack_gauge(const double2* U_canon, double2* U64, float4* U12, float2* U18, const Geom& g,
+__global__ void k_f64_to_df(void* x, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = reinterpret_cast<double2*>(x)[e];
+        reinterpret_cast<dfc*>(x)[e] = c2dfc(d2df(v));
+    }
+}
+__global__ void k_df_to_f64(void* x, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const dfc v = reinterpret_cast<dfc*>(x)[e];
+        reinterpret_cast<double2*>(x)[e] = df2d(dfc2c(v));
+    }
+}
+void launch_f64_to_df(void* x, size_t n, cudaStream_t st) {
+    k_f64_to_df<<<(int)std::min<size_t>((n + 255) / 256, 2048), 256, 0, st>>>(x, n);
+}
+void launch_df_to_f64(void* x, size_t n, cudaStream_t st) {
+    k_df_to_f64<<<(int)std::min<size_t>((n + 255) / 256, 2048), 256, 0, st>>>(x, n);
+}
+
+void launch_pack_gauge(const double2* U_canon, double2* U64, float4* U12, float2* U18, float4* Udf, const Geom& g,
                        cudaStream_t st) {
-    k_pack_gauge<<<(g.V + 127) / 128, 128, 0, st>>>(U_canon, U64, U12, U18, g);
+    k_pack_gauge<<<(g.V + 127) / 128, 128, 0, st>>>(U_canon, U64, U12, U18, Udf, g);
 }
 
 __global__ void k_pack_spinor(const double2* __restrict__ canon, void* __restrict__ native, int prec, Geom g) {

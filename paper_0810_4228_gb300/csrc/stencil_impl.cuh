@@ -4,6 +4,7 @@
 // component access in the FP64 / FP32 device layouts.
 #pragma once
 
+#include "df32.cuh"
 #include "ovl_kernels.h"
 
 namespace ovl {
@@ -11,13 +12,16 @@ namespace ovl {
 template <class R> struct VecT;
 template <> struct VecT<double> { using T = double2; };
 template <> struct VecT<float> { using T = float4; };
+template <> struct VecT<df> { using T = dfc; };
 
 template <int LF> struct LinkReal { using R = float; };
 template <> struct LinkReal<LINK_F64> { using R = double; };
+template <> struct LinkReal<LINK_DF> { using R = df; };
 
 template <int LF, class R>
 __device__ __forceinline__ void load_link_any(const void* U, int V, int nu, int i, Link<R>& L) {
     if constexpr (LF == LINK_F64) load_link((const double2*)U, V, nu, i, L);
+    else if constexpr (LF == LINK_DF) load_link_df((const dfc*)U, V, nu, i, L);
     else if constexpr (LF == LINK_F32_12) load_link12((const float4*)U, V, nu, i, L);
     else load_link18((const float2*)U, V, nu, i, L);
 }
@@ -156,6 +160,13 @@ template <> __device__ inline cx<double> ld_comp_cg<double>(const double2* x, in
 template <> __device__ inline cx<float> ld_comp_cg<float>(const float4* x, int V, int i, int q) {
     const float2 v = __ldcg(reinterpret_cast<const float2*>(x) + ((size_t)(q >> 1) * V + i) * 2 + (q & 1));
     return mk(v.x, v.y);
+}
+template <> __device__ inline cx<df> ld_comp_cg<df>(const dfc* x, int V, int i, int q) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(x) + (size_t)q * V + i);
+    return mk(df(v.x, v.y), df(v.z, v.w));
+}
+template <> __device__ inline void st_comp<df>(dfc* x, int V, int i, int q, cx<df> z) {
+    x[(size_t)q * V + i] = c2dfc(z);
 }
 template <> __device__ inline void st_comp<double>(double2* x, int V, int i, int q, cx<double> z) {
     x[(size_t)q * V + i] = make_double2(z.r, z.i);

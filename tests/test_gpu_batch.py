@@ -195,3 +195,14 @@ def test_batch_uneven_lattices_point_sources(ovl):
             e = rel(outs[j][r].cpu().numpy(), y1.cpu().numpy())
             assert e < 1e-8, (j, r, e)
     bt.close()
+
+
+def test_batch_double_float_pass2_matches_fp64_pass2(ovl, mid):
+    c = _ctx(ovl, mid["dims"], mid["U"])
+    b = torch_c128(_sources(mid["dims"], 3900, 3))
+    bt = ovl.Batch([c], [3])
+    y_df = bt.solve(300, mid["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    y_64 = bt.solve(300, mid["mu"], KAPPA, [b], flags=ovl.MIXED | ovl.PASS2_F64)[0][0].cpu().numpy()
+    for r in range(3):
+        assert rel(y_df[r], y_64[r]) < 1e-11
+    bt.close()

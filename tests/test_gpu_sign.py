@@ -278,3 +278,13 @@ def test_newton_fallback_on_hard_spectrum(ovl):
     yn, infon = _solve(ovl, ctx, ovl.LANCZOS2, 300, 0.3, b, flags=ovl.INNER_NEWTON)
     assert rel(yn, y) < 1e-9
     assert rel(y, ref) < 1e-5
+
+
+@pytest.mark.parametrize("k", [60, 400])
+def test_double_float_pass2_matches_fp64_pass2(ovl, c4, k):
+    """The regeneration pass in double-float arithmetic (FP32 pairs) and in native FP64 follow the
+    same pass-1 coefficients: their results agree far below the 1e-8 target."""
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y_df, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.PASS2_DF)
+    y_64, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, c4["mu"], c4["b"], flags=ovl.MIXED)
+    assert rel(y_df, y_64) < 1e-11
