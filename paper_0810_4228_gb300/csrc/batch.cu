@@ -284,17 +284,18 @@ __global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, cons
 
 // Regeneration (Sec. 5): r_{i+1} = ((A - alpha_i) r_i - gamma_{i-1} r_{i-1}) / beta_i, y += c_{i+1} r_{i+1},
 // in FP64 (R = double) or double-float (R = df; ring and y converted beforehand).  One block per
-// 32-site tile of a sequence: warp w applies both hops of direction w to the tile's sites, the
-// four partial sums meet in shared memory, and 128 threads (site, spin) finish three components each.
+// 32-site tile of a sequence: warp h applies hop h (direction-uniform code) to the tile's sites, the
+// eight partial sums meet in shared memory, and 128 threads (site, spin) finish three components each.
 template <class R> __device__ __forceinline__ cx<R> cvt_coef(cx<double> z);
 template <> __device__ __forceinline__ cx<double> cvt_coef<double>(cx<double> z) { return z; }
 template <> __device__ __forceinline__ cx<df> cvt_coef<df>(cx<double> z) { return mk(df(z.r), df(z.i)); }
 
 template <class R, int LF>
-__global__ void __launch_bounds__(4 * TT) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
+__global__ void __launch_bounds__(8 * TT) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
                                                     HopCoef<R> hc) {
     using VT = typename VecT<R>::T;
-    __shared__ cx<R> dirpart[4][TT][12];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R>(*dirpart)[TT][12] = reinterpret_cast<cx<R>(*)[TT][12]>(smraw);  // [8][TT][12]
     __shared__ cx<R> cf[4];
     const BSeq& q = S[tseq[blockIdx.x]];
     const KState* ks = q.ks;
@@ -321,17 +322,13 @@ __global__ void __launch_bounds__(4 * TT) k_b_regen(const BSeq* __restrict__ S, 
             const Coord c = site_coord(q.g, i0);
             const VT* const xs[1] = {ri};
             const HopCoef<R> hcs[1] = {hc};
-            switch (wid) {
-                case 0: hops_dir<0, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
-                case 1: hops_dir<1, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
-                case 2: hops_dir<2, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
-                default: hops_dir<3, LF, R, 1>(q.g, c, i0, U, xs, acc, hcs); break;
-            }
+            hop_uniform<LF, R, 1>(wid, q.g, c, i0, U, xs, acc, hcs);
         }
 #pragma unroll
         for (int c = 0; c < 12; ++c) dirpart[wid][lane][c] = acc[0].s[c / 3][c % 3];
     }
     __syncthreads();
+    if (threadIdx.x >= 4 * TT) return;
     const int site = threadIdx.x >> 2, sp = threadIdx.x & 3;
     const int ii = tile * TT + site;
     if (ii >= q.g.V) return;
@@ -342,7 +339,9 @@ __global__ void __launch_bounds__(4 * TT) k_b_regen(const BSeq* __restrict__ S, 
     for (int c3 = 0; c3 < 3; ++c3) {
         const int c = 3 * sp + c3;
         const cx<R> self = ld_comp_cg<R>(ri, q.g.V, ii, c);
-        cx<R> z = self + dirpart[0][site][c] + dirpart[1][site][c] + dirpart[2][site][c] + dirpart[3][site][c];
+        cx<R> z = self;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) z = z + dirpart[w][site][c];
         if (sp >= 2) z = -z;
         z = cf[0] * z - cf[1] * self;
         if (i > 0) z = z - cf[2] * ld_comp_cg<R>(rm, q.g.V, ii, c);
@@ -598,6 +597,15 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
         // mixed: double-float regeneration unless OVL_PASS2_F64 (ring and y converted in place)
         const int nt = b->ntiles;
         const bool dfm = mixed && !(flags & OVL_PASS2_F64);
+        const size_t smr = (size_t)8 * ovl::TT * 12 * 16;
+        static bool rattr = false;
+        if (!rattr) {
+            cudaFuncSetAttribute(ovl::k_b_regen<ovl::df, ovl::LINK_DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smr);
+            cudaFuncSetAttribute(ovl::k_b_regen<double, ovl::LINK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smr);
+            rattr = true;
+        }
         for (int s = 0; s < ns; ++s) {
             const ovl::BSeq& q = b->hseq[s];
             ovl::launch_scale_start(b->bR[s], q.r[0], q.y, q.cvec, q.ks, q.n, st);
@@ -608,10 +616,10 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
         }
         for (int i = 0; i + 1 < k; ++i) {
             if (dfm)
-                ovl::k_b_regen<ovl::df, ovl::LINK_DF><<<nt, 4 * ovl::TT, 0, st>>>(b->dseq, b->dtseq, i,
+                ovl::k_b_regen<ovl::df, ovl::LINK_DF><<<nt, 8 * ovl::TT, smr, st>>>(b->dseq, b->dtseq, i,
                                                                                   ovl::make_coef<ovl::df>(mu, kappa));
             else
-                ovl::k_b_regen<double, ovl::LINK_F64><<<nt, 4 * ovl::TT, 0, st>>>(b->dseq, b->dtseq, i,
+                ovl::k_b_regen<double, ovl::LINK_F64><<<nt, 8 * ovl::TT, smr, st>>>(b->dseq, b->dtseq, i,
                                                                                   ovl::make_coef<double>(mu, kappa));
         }
         if (dfm)

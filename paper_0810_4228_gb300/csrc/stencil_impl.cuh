@@ -112,6 +112,70 @@ __device__ __forceinline__ void one_hop(int h, const Geom& g, const Coord& c, in
     }
 }
 
+// x times a unit: i x if imag, negated if neg (exact: no multiplication)
+template <class R>
+__device__ __forceinline__ cx<R> unit_mul(cx<R> x, bool imag, bool neg) {
+    const cx<R> y = imag ? mk(-x.i, x.r) : x;
+    return neg ? -y : y;
+}
+
+// Hop h = 0..7 (direction nu = h & 3, forward for h < 4) with nu and the sign as warp-uniform
+// runtime values: the spin projection and reconstruction of (1 +- gamma_nu) are written as selects
+// and sign flips, so every warp of a direction-split block runs the same instructions (one copy of
+// the hop in the instruction cache instead of eight).  Same arithmetic as hop_fwd / hop_bwd.
+template <int LF, class R, int NIN>
+__device__ __forceinline__ void hop_uniform(int h, const Geom& g, const Coord& c, int i, const void* U,
+                                            const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
+                                            const HopCoef<R> (&hc)[NIN]) {
+    const int nu = h & 3;
+    const bool fwd = h < 4;
+    int y[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        int v = c.x[d];
+        if (d == nu) {
+            v += fwd ? 1 : -1;
+            if (v == g.L[d]) v = 0;
+            if (v < 0) v = g.L[d] - 1;
+        }
+        y[d] = v;
+    }
+    const int nb = internal_index(g, y);
+    const bool edge = fwd ? (c.x[3] == g.L[3] - 1) : (c.x[3] == 0);
+    const R ph = (nu == 3 && edge) ? R(g.bc_t) : R(1);
+    Link<R> L;
+    load_link_any<LF>(U, g.V, nu, fwd ? i : nb, L);
+    // (1 + S gamma_nu), S = +1 forward, -1 backward, chiral basis: upper spins
+    // h0 = p0 + u0 p[2 or 3], h1 = p1 + u1 p[3 or 2]; lower spins rebuilt from (h0, h1)
+    const bool hi2 = nu >= 2, im = (nu & 1) == 0;
+    const bool n0 = (nu == 3) ? !fwd : fwd;
+    const bool n1 = (nu == 0) ? fwd : !fwd;
+    const bool nA = !fwd;
+    const bool nB = (nu == 0 || nu == 3) ? !fwd : fwd;
+#pragma unroll
+    for (int n = 0; n < NIN; ++n) {
+        Spinor<R> p;
+        load_spinor(x[n], g.V, nb, p);
+        Half<R> hh, uh;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            hh.h[0][a] = p.s[0][a] + unit_mul(hi2 ? p.s[2][a] : p.s[3][a], im, n0);
+            hh.h[1][a] = p.s[1][a] + unit_mul(hi2 ? p.s[3][a] : p.s[2][a], im, n1);
+        }
+        if (fwd) mul_link(L, hh, uh);
+        else mul_link_dag(L, hh, uh);
+        const R cf = (fwd ? (nu == 3 ? hc[n].f[3] : hc[n].f[0]) : (nu == 3 ? hc[n].b[3] : hc[n].b[0])) * ph;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const cx<R> h0 = cf * uh.h[0][a], h1 = cf * uh.h[1][a];
+            acc[n].s[0][a] = acc[n].s[0][a] + h0;
+            acc[n].s[1][a] = acc[n].s[1][a] + h1;
+            acc[n].s[2][a] = acc[n].s[2][a] + unit_mul(hi2 ? h0 : h1, im, nA);
+            acc[n].s[3][a] = acc[n].s[3][a] + unit_mul(hi2 ? h1 : h0, im, nB);
+        }
+    }
+}
+
 template <int LF, class R, int NIN>
 __device__ __forceinline__ void apply_site(const Geom& g, int i, const void* U,
                                            const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
