@@ -149,6 +149,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks of the job (the timing rule: the slowest replica sets the rate)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(total_ms_max: float, world: int, units_per_step: int, steps: int) -> float:
+    """Units solved by all replicas per second of the slowest replica's timed device time."""
+    return world * units_per_step * steps / (total_ms_max / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -416,13 +432,10 @@ def run_ours(args, world, rank, local):
                         args.warmup, args.steps, flush)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    tot = sum(t_mix)
+    tot = max_over_ranks(sum(t_mix), world, "cuda")
     if world > 1:
-        tt = torch.tensor([tot], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tot = tt.item()
         torch.distributed.barrier()
-    value = world * NRHS * args.steps / (tot / 1e3)
+    value = whole_job_rate(tot, world, NRHS, args.steps)
     print(f"[bench] batched mixed solves/s {value:.2f}, ms/step {statistics.mean(t_mix):.3f}, steps "
           f"{[round(t, 3) for t in t_mix]}", file=sys.stderr, flush=True)
 
@@ -444,7 +457,7 @@ def run_ours(args, world, rank, local):
     hout = torch.empty_like(hsrc).pin_memory()
     t_e2e = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [hsrc], [hout], flags=fl_mix), [0],
                         args.warmup, args.steps, flush)
-    e2e_val = world * NRHS * args.steps / (sum(t_e2e) / 1e3)
+    e2e_val = whole_job_rate(max_over_ranks(sum(t_e2e), world, "cuda"), world, NRHS, args.steps)
     nbytes = srcs.numel() * srcs.element_size()
 
     # ---- roofline of the dominant phase of the batched solve
