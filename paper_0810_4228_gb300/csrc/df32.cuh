@@ -66,6 +66,83 @@ OVL_HD df operator*(df a, df b) {
 OVL_HD df& operator+=(df& a, df b) { a = a + b; return a; }
 OVL_HD df& operator-=(df& a, df b) { a = a - b; return a; }
 
+// Sum of products of double-float numbers with one renormalisation at the end: every product
+// enters as its exact FP32 leading product and an FP32 error term (the cross terms of hi and lo
+// included), the leading products are added with TwoSum, the error terms in plain FP32.
+struct dfacc {
+    float s, e;
+};
+OVL_HD void dfacc_first(dfacc& A, df a, df b, bool neg) {
+    float p = DF_MUL(a.hi, b.hi);
+    float pe = DF_FMA(a.hi, b.hi, -p);
+    pe = DF_FMA(a.hi, b.lo, pe);
+    pe = DF_FMA(a.lo, b.hi, pe);
+    A.s = neg ? -p : p;
+    A.e = neg ? -pe : pe;
+}
+OVL_HD void dfacc_add(dfacc& A, df a, df b, bool neg) {
+    float p = DF_MUL(a.hi, b.hi);
+    float pe = DF_FMA(a.hi, b.hi, -p);
+    pe = DF_FMA(a.hi, b.lo, pe);
+    pe = DF_FMA(a.lo, b.hi, pe);
+    if (neg) {
+        p = -p;
+        pe = -pe;
+    }
+    const float s = DF_ADD(A.s, p);
+    const float bb = DF_SUB(s, A.s);
+    const float t = DF_ADD(DF_SUB(A.s, DF_SUB(s, bb)), DF_SUB(p, bb));
+    A.s = s;
+    A.e = DF_ADD(A.e, DF_ADD(t, pe));
+}
+OVL_HD df dfacc_value(const dfacc& A) { return df_fast2sum(A.s, A.e); }
+
+// out = U h for both half-spinor spins (Sec. 1, Eq. 1.2 hop), each output component one sum of
+// six double-float products
+template <>
+OVL_HD void mul_link<df>(const Link<df>& U, const Half<df>& h, Half<df>& o) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dfacc re, im;
+            dfacc_first(re, U.u[a][0].r, h.h[s][0].r, false);
+            dfacc_add(re, U.u[a][0].i, h.h[s][0].i, true);
+            dfacc_first(im, U.u[a][0].r, h.h[s][0].i, false);
+            dfacc_add(im, U.u[a][0].i, h.h[s][0].r, false);
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                dfacc_add(re, U.u[a][k].r, h.h[s][k].r, false);
+                dfacc_add(re, U.u[a][k].i, h.h[s][k].i, true);
+                dfacc_add(im, U.u[a][k].r, h.h[s][k].i, false);
+                dfacc_add(im, U.u[a][k].i, h.h[s][k].r, false);
+            }
+            o.h[s][a] = mk(dfacc_value(re), dfacc_value(im));
+        }
+}
+// out = U^dag h
+template <>
+OVL_HD void mul_link_dag<df>(const Link<df>& U, const Half<df>& h, Half<df>& o) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dfacc re, im;
+            dfacc_first(re, U.u[0][a].r, h.h[s][0].r, false);
+            dfacc_add(re, U.u[0][a].i, h.h[s][0].i, false);
+            dfacc_first(im, U.u[0][a].r, h.h[s][0].i, false);
+            dfacc_add(im, U.u[0][a].i, h.h[s][0].r, true);
+#pragma unroll
+            for (int k = 1; k < 3; ++k) {
+                dfacc_add(re, U.u[k][a].r, h.h[s][k].r, false);
+                dfacc_add(re, U.u[k][a].i, h.h[s][k].i, false);
+                dfacc_add(im, U.u[k][a].r, h.h[s][k].i, false);
+                dfacc_add(im, U.u[k][a].i, h.h[s][k].r, true);
+            }
+            o.h[s][a] = mk(dfacc_value(re), dfacc_value(im));
+        }
+}
+
 struct __align__(16) dfc {
     float rh, rl, ih, il;
 };
