@@ -291,7 +291,7 @@ template <> __device__ __forceinline__ cx<double> cvt_coef<double>(cx<double> z)
 template <> __device__ __forceinline__ cx<df> cvt_coef<df>(cx<double> z) { return mk(df(z.r), df(z.i)); }
 
 template <class R, int LF>
-__global__ void __launch_bounds__(8 * TT) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
+__global__ void __launch_bounds__(8 * TT, 3) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
                                                     HopCoef<R> hc) {
     using VT = typename VecT<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -328,21 +328,22 @@ __global__ void __launch_bounds__(8 * TT) k_b_regen(const BSeq* __restrict__ S, 
         for (int c = 0; c < 12; ++c) dirpart[wid][lane][c] = acc[0].s[c / 3][c % 3];
     }
     __syncthreads();
-    if (threadIdx.x >= 4 * TT) return;
-    const int site = threadIdx.x >> 2, sp = threadIdx.x & 3;
+    // epilogue: 256 threads (site, part), components part and part + 8 (< 12)
+    const int site = threadIdx.x >> 3, part = threadIdx.x & 7;
     const int ii = tile * TT + site;
     if (ii >= q.g.V) return;
     const VT* rm = (const VT*)q.r[(i + 2) % 3];
     VT* rn = (VT*)q.r[(i + 1) % 3];
     VT* y = (VT*)q.y;
 #pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) {
-        const int c = 3 * sp + c3;
+    for (int c2 = 0; c2 < 2; ++c2) {
+        const int c = part + 8 * c2;
+        if (c >= 12) break;
         const cx<R> self = ld_comp_cg<R>(ri, q.g.V, ii, c);
         cx<R> z = self;
 #pragma unroll
         for (int w = 0; w < 8; ++w) z = z + dirpart[w][site][c];
-        if (sp >= 2) z = -z;
+        if (c >= 6) z = -z;  // gamma5: spins 2, 3
         z = cf[0] * z - cf[1] * self;
         if (i > 0) z = z - cf[2] * ld_comp_cg<R>(rm, q.g.V, ii, c);
         st_comp<R>(rn, q.g.V, ii, c, z);
