@@ -103,27 +103,72 @@ __device__ __forceinline__ void acc_norm2(A& a, cx<R> x) {
     acc_prod(a, x.i, x.i);
 }
 
-// Per-sequence reduction of NQ values: block sums into part[local] (FP64), then the last block of
-// the sequence (ticket) adds the partials of its nblk blocks in a fixed order.  Returns true in the
-// last block; out[] is valid in thread 0 there.
-template <int NQ>
-__device__ bool seq_reduce(const double (&v)[NQ], double2* part, unsigned int* cnt, int local, int nblk,
-                           double (&out)[NQ]) {
-    __shared__ double red[NQ][BT / 32];
+// Pair addition for the block and sequence sums of AccF values (TwoSum of the leading parts)
+__device__ __forceinline__ AccF accf_add(AccF a, AccF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    AccF r;
+    r.hi = s;
+    r.lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    return r;
+}
+__device__ __forceinline__ AccF acc_shfl(AccF a, int o) {
+    AccF r;
+    r.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    r.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    return r;
+}
+__device__ __forceinline__ AccD accf_add(AccD a, AccD b) {
+    AccD r;
+    r.v = a.v + b.v;
+    return r;
+}
+__device__ __forceinline__ AccD acc_shfl(AccD a, int o) {
+    AccD r;
+    r.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+    return r;
+}
+__device__ __forceinline__ double2 acc_store(AccF a) { return make_double2((double)a.hi, (double)a.lo); }
+__device__ __forceinline__ double2 acc_store(AccD a) { return make_double2(a.v, 0.0); }
+__device__ __forceinline__ AccF acc_load(double2 v, AccF) {
+    AccF r;
+    r.hi = (float)v.x;
+    r.lo = (float)v.y;
+    return r;
+}
+__device__ __forceinline__ AccD acc_load(double2 v, AccD) {
+    AccD r;
+    r.v = v.x;
+    return r;
+}
+
+// Per-sequence reduction of NQ accumulators (in their own arithmetic: compensated FP32 pairs for FP32
+// data, FP64 otherwise): warp trees, the block's warps in a fixed order into part[local], then the
+// last block of the sequence (ticket) adds the partials of its nblk blocks in a fixed order.
+// Returns true in the last block; out[] (FP64) is valid in thread 0 there.
+template <int NQ, class A>
+__device__ bool seq_reduce(A (&v)[NQ], double2* part, unsigned int* cnt, int local, int nblk, double (&out)[NQ]) {
+    constexpr int NW = BT / 32;
+    __shared__ double2 red[NQ][NW];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        const double x = warp_sum(v[q]);
-        if (lane == 0) red[q][wid] = x;
+        A x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = accf_add(x, acc_shfl(x, o));
+        if (lane == 0) red[q][wid] = acc_store(x);
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        const int q = threadIdx.x;
+        A sacc = acc_load(red[q][0], A());
+        for (int w = 1; w < NW; ++w) sacc = accf_add(sacc, acc_load(red[q][w], A()));
+        part[(size_t)local * 4 + q] = acc_store(sacc);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < BT / 32; ++w) s += red[q][w];
-            part[(size_t)local * 4 + q] = make_double2(s, 0.0);
-        }
         __threadfence();
         const unsigned int t = atomicAdd(cnt, 1u);
         last = (t == (unsigned)nblk - 1);
@@ -131,25 +176,17 @@ __device__ bool seq_reduce(const double (&v)[NQ], double2* part, unsigned int* c
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    double acc[NQ];
+    // one warp per value: lanes over the blocks, then the warp tree (fixed order)
+    if (wid < NQ) {
+        A acc = acc_load(make_double2(0.0, 0.0), A());
+        for (int b = lane; b < nblk; b += 32) acc = accf_add(acc, acc_load(__ldcg(&part[(size_t)b * 4 + wid]), A()));
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        acc[q] = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += BT) acc[q] += __ldcg(&part[(size_t)b * 4 + q].x);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const double x = warp_sum(acc[q]);
-        if (lane == 0) red[q][wid] = x;
+        for (int o = 16; o > 0; o >>= 1) acc = accf_add(acc, acc_shfl(acc, o));
+        if (lane == 0) red[wid][0] = acc_store(acc);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < BT / 32; ++w) s += red[q][w];
-            out[q] = s;
-        }
+        for (int q = 0; q < NQ; ++q) out[q] = red[q][0].x + red[q][0].y;
         *cnt = 0u;
     }
     return true;
@@ -196,9 +233,8 @@ __global__ void __launch_bounds__(BT) k_b_pair(const BSeq* __restrict__ S, const
         store_spinor((VT*)q.t, q.g.V, site, acc[0]);
         store_spinor((VT*)q.s, q.g.V, site, acc[1]);
     }
-    const double v3[3] = {acc_val(a[0]), acc_val(a[1]), acc_val(a[2])};
     double o[3];
-    if (seq_reduce<3>(v3, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
+    if (seq_reduce<3>(a, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
         const cx<double> alpha = cdot(d2c(ks->sw), mk(o[0], o[1]));  // conj(sw) w~^dag t
         q.alpha[i] = c2d(alpha);
         ks->anorm = fmax(ks->anorm, sqrt(o[2]));
@@ -259,9 +295,8 @@ __global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, cons
         store_spinor((VT*)vslot<R>(q, i + 1, false), q.g.V, site, t);
         store_spinor((VT*)vslot<R>(q, i + 1, true), q.g.V, site, s);
     }
-    const double v4[4] = {acc_val(a[0]), acc_val(a[1]), acc_val(a[2]), acc_val(a[3])};
     double o[4];
-    if (seq_reduce<4>(v4, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
+    if (seq_reduce<4>(a, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
         const double nv = sqrt(o[2]), nw = sqrt(o[3]);
         const cx<double> delta = mk(o[0], o[1]);
         if (nv <= 1e-13 * fmax(ks->anorm, 1e-300)) {
