@@ -215,10 +215,9 @@ def time_solves(torch, ctx, fn, bufs, warmup, steps, flush):
     return times
 
 
-def dw_bandwidth(torch, ovl, reps=20):
+def dw_bandwidth(torch, ovl, reps=20, dims=DW_DIMS):
     """Stencil GB/s on a lattice far larger than L2 (device-layout vectors)."""
     from paper_0810_4228_gb300 import synth
-    dims = DW_DIMS
     V = dims[0] * dims[1] * dims[2] * dims[3]
     ctx = ovl.Context(dims)
     U = synth.gauge_field_torch(dims, EPS, SEED_U, device="cuda")
@@ -366,6 +365,13 @@ def run_ours(args, world, rank, local):
     from paper_0810_4228_gb300 import ovl, synth
 
     torch.cuda.set_device(local)
+    if args.dw_only:
+        ovl.load()
+        dims = tuple(int(v) for v in args.dw_dims.split(",")) if args.dw_dims else DW_DIMS
+        ddims, dV, dres = dw_bandwidth(torch, ovl, reps=args.steps, dims=dims)
+        print(json.dumps({"dw_only": True, "dims": list(ddims), "sites": dV,
+                          **{nm: {"ms": r["ms"], "GB_s": r["GB_s"]} for nm, r in dres.items()}}))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -406,9 +412,14 @@ def run_ours(args, world, rank, local):
     if args.solves_only:
         if not args.k:
             raise SystemExit("--solves-only needs --k")
-        t = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix), [0],
-                        args.warmup, args.steps, flush)
-        print(json.dumps({"solves_only": True, "k": k_mix, "ms_per_step": statistics.mean(t)}))
+        if args.single:
+            out1 = torch.empty_like(srcs[0])
+            t = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, b, out1, flags=fl_mix),
+                            [srcs[r] for r in range(NRHS)], args.warmup, args.steps, flush)
+        else:
+            t = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix),
+                            [0], args.warmup, args.steps, flush)
+        print(json.dumps({"solves_only": True, "single": args.single, "k": k_mix, "ms_per_step": statistics.mean(t)}))
         return
 
     outb = torch.empty_like(srcs)
@@ -555,6 +566,9 @@ def main():
     ap.add_argument("--no-dw", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the four-lattice point-source batch")
+    ap.add_argument("--single", action="store_true", help="with --solves-only: single-source solves instead of batches")
+    ap.add_argument("--dw-only", action="store_true", help="only the stencil bandwidth measurement (--steps repetitions)")
+    ap.add_argument("--dw-dims", default="", help="lattice of the stencil bandwidth measurement, e.g. 32,32,32,32")
     ap.add_argument("--solves-only", action="store_true",
                     help="only the timed solves (for profiler captures): needs --k, skips calibration, "
                          "profile, FP64/Arnoldi/e2e legs, the bandwidth lattice and the CPU baseline")

@@ -2,7 +2,10 @@
 // (Sec. 1, Eq. 1.1-1.2; the adjoint enters the two-sided Lanczos recurrence of
 // Sec. 4, Eq. 4.2), plus the layout conversions at the library boundary.
 //
-// One thread per lattice site.  A block covers a range of checkerboard
+// One thread per lattice site, 128-thread blocks held to 80 registers so that six
+// blocks (24 warps) share an SM: the single application is bound by HBM and its
+// DRAM traffic is already the algorithmic minimum (links and x read once, y
+// written once), so what remains is keeping enough loads in flight.  A block covers a range of checkerboard
 // indices for both parities (first half of the block parity 0, second half
 // parity 1), so neighbouring sites -- which have the opposite parity -- are
 // processed by the same block and their links/spinors are re-read from L1/L2.
@@ -211,7 +214,7 @@ static bool use_ds(const Geom& g) { return g.V < 152 * 1024; }
 
 // ------------------------------------------------------------ single apply --
 template <int LF>
-__global__ void __launch_bounds__(256) k_dslash(const void* __restrict__ U,
+__global__ void __launch_bounds__(128, 6) k_dslash(const void* __restrict__ U,
                                                 const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ x,
                                                 typename VecT<typename LinkReal<LF>::R>::T* __restrict__ y,
                                                 HopCoef<typename LinkReal<LF>::R> hc, int g5, const KState* ks,
@@ -248,7 +251,7 @@ void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, d
                                                                             make_coef<float>(mu, kappa), gamma5, ks, g);
         return;
     }
-    const int T = 256, B = dslash_grid(g, T);
+    const int T = 128, B = dslash_grid(g, T);
     if (prec == 0)
         k_dslash<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)x, (double2*)y, make_coef<double>(mu, kappa),
                                             gamma5, ks, g);
@@ -340,7 +343,7 @@ void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, v
                 make_coef<float>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
         return;
     }
-    const int T = 256, B = dslash_grid(g, T);
+    const int T = 128, B = dslash_grid(g, T);
     if (prec == 0)
         k_dslash_pair<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s,
                                                  make_coef<double>(mu, kappa), make_coef<double>(-mu, kappa), ks,
@@ -397,7 +400,7 @@ void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim
                                                                    ks, alpha, beta, gamma, c, step, g);
         return;
     }
-    const int T = 256, B = dslash_grid(g, T);
+    const int T = 128, B = dslash_grid(g, T);
     k_dslash_regen<<<B, T, 0, st>>>(U, vi, vim1, vip1, y, make_coef<double>(mu, kappa), ks, alpha, beta, gamma, c,
                                     step, g);
 }
