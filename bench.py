@@ -430,6 +430,7 @@ def run_ours(args, world, rank, local):
         _, pinfo, _ = bt.solve(k_mix, MU, KAPPA, [srcs], [outb], flags=fl_mix | ovl.PROFILE)
     prof, _ = bt.profile(reset=True)
     prof = {kk: v / nprof for kk, v in prof.items()}
+    tuned = bt.tuning()
     kused = max(i["k_used"] for i in pinfo)
     print(f"[bench] batch profile {prof}", file=sys.stderr, flush=True)
 
@@ -526,6 +527,8 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "mu": MU, "kappa": KAPPA, "eps": EPS,
                        "rhs_per_step": NRHS,
+                       "autotuned_shapes": {"pass1_sites_per_block": tuned[0], "regen_blocks_per_sm": tuned[1]}
+                       if tuned else None,
                        "method": "batched two-sided Lanczos, two-pass mixed (FP32 pass 1, FP64 pass 2)",
                        "k": k_mix, "m_deflated": args.m, "deflation_setup": eig,
                        "max_rel_err_vs_k1000_fp64": err_mix,

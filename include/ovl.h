@@ -83,6 +83,7 @@ typedef struct ovl_ctx ovl_ctx;
 #define OVL_STEPWISE     0x40000 /* sign_krylov MIXED: one kernel per recurrence step instead of the
                                     persistent cooperative kernels (default on small lattices)   */
 #define OVL_PASS2_F64    0x80000 /* MIXED: regeneration pass in native FP64                       */
+#define OVL_NO_TUNE      0x200000 /* batch_solve: keep the current launch shapes, no autotuning     */
 #define OVL_PASS2_DF     0x100000 /* MIXED: regeneration pass in double-float arithmetic (FP32 pairs,
                                     about 48 significant bits, on the FP32 pipe).  Default: double-
                                     float in batched solves, FP64 in single solves (one source per
@@ -197,6 +198,14 @@ int ovl_batch_solve(ovl_batch* batch, int k, double mu, double kappa, const void
  * ms3[0] pass 1 (the Krylov recurrence), ms3[1] the inner sign, ms3[2] the regeneration pass or the
  * combination; *nsolves the number of such solves.  reset != 0 clears the totals. */
 int ovl_batch_profile(ovl_batch* batch, double* ms3, int* nsolves, int reset);
+/* Launch shapes of the batched kernels.  The first solve in each precision times the candidates
+ * (pass-1 site blocks of 64, 128 or 256 sites; regeneration kernel at 2, 3 or 4 blocks per SM) with
+ * short eager solves of the batch itself and keeps the fastest (OVL_NO_TUNE skips this).  Writes the
+ * chosen shapes; returns OVL_ESTATE before the first tuning. */
+int ovl_batch_tuning(const ovl_batch* batch, int* pass1_block_sites, int* regen_blocks_per_sm);
+/* Pins the launch shapes (pass1_block_sites 64, 128 or 256; regen_blocks_per_sm 2, 3 or 4) and
+ * turns the autotuner off for this batch.  OVL_EINVAL for any other value (nothing changed). */
+int ovl_batch_set_tuning(ovl_batch* batch, int pass1_block_sites, int regen_blocks_per_sm);
 /* create + solve + destroy (no graph reuse); errors are reported on ctxs[0]. */
 int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int k, double mu, double kappa,
                             const void* const* b, void* const* out, int flags, ovl_info* info);

@@ -50,13 +50,15 @@ struct BSeq {
     double2* vscale;
     double2* part;            // [nblk][4] block partials of the batched kernels
     unsigned int* cnt;        // ticket of this sequence
-    int blk0, nblk;           // block range in the batched launches (blocks of BT sites)
+    int blk0[3], nblk[3];     // block range in the pass-1 launches, per site-block shape (64, 128, 256 sites)
     int tile0, ntile;         // tile range in the tiled launches (tiles of TT sites)
 };
 
 namespace {
 
-constexpr int BT = 128;  // sites per block
+// pass-1 site-block shapes (sites = threads per block), picked per batch by the autotuner
+constexpr int NSHAPE = 3;
+constexpr int SHAPE_SITES[NSHAPE] = {64, 128, 256};
 constexpr int TT = 32;   // sites per tile of the direction-split kernels (one warp per direction)
 
 template <class R> struct BVec;
@@ -79,12 +81,10 @@ __device__ __forceinline__ void acc_prod(AccF& a, float x, float y, float sg = 1
     const float pe = __fmaf_rn(x, y, -p);
     acc_add(a, sg * p, sg * pe);
 }
-__device__ __forceinline__ double acc_val(const AccF& a) { return (double)a.hi + (double)a.lo; }
 struct AccD {
     double v = 0.0;
 };
 __device__ __forceinline__ void acc_prod(AccD& a, double x, double y, double sg = 1.0) { a.v += sg * x * y; }
-__device__ __forceinline__ double acc_val(const AccD& a) { return a.v; }
 
 template <class R> struct AccOf;
 template <> struct AccOf<float> { using T = AccF; };
@@ -147,9 +147,8 @@ __device__ __forceinline__ AccD acc_load(double2 v, AccD) {
 // data, FP64 otherwise): warp trees, the block's warps in a fixed order into part[local], then the
 // last block of the sequence (ticket) adds the partials of its nblk blocks in a fixed order.
 // Returns true in the last block; out[] (FP64) is valid in thread 0 there.
-template <int NQ, class A>
+template <int NQ, int NW, class A>
 __device__ bool seq_reduce(A (&v)[NQ], double2* part, unsigned int* cnt, int local, int nblk, double (&out)[NQ]) {
-    constexpr int NW = BT / 32;
     __shared__ double2 red[NQ][NW];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -176,13 +175,14 @@ __device__ bool seq_reduce(A (&v)[NQ], double2* part, unsigned int* cnt, int loc
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    // one warp per value: lanes over the blocks, then the warp tree (fixed order)
-    if (wid < NQ) {
+    // one warp per value (a warp takes several when the block has fewer warps than values): lanes
+    // over the blocks, then the warp tree (fixed order)
+    for (int qv = wid; qv < NQ; qv += NW) {
         A acc = acc_load(make_double2(0.0, 0.0), A());
-        for (int b = lane; b < nblk; b += 32) acc = accf_add(acc, acc_load(__ldcg(&part[(size_t)b * 4 + wid]), A()));
+        for (int b = lane; b < nblk; b += 32) acc = accf_add(acc, acc_load(__ldcg(&part[(size_t)b * 4 + qv]), A()));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc = accf_add(acc, acc_shfl(acc, o));
-        if (lane == 0) red[wid][0] = acc_store(acc);
+        if (lane == 0) red[qv][0] = acc_store(acc);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -199,14 +199,15 @@ __device__ __forceinline__ void* vslot(const BSeq& q, int j, bool wvec) {
 }
 
 // t = sv A v~_i, s = sw A^dag w~_i at every site of every running sequence; alpha_i = w_i^dag t
-template <int LF, class R>
-__global__ void __launch_bounds__(BT) k_b_pair(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
+template <int LF, class R, int SH>
+__global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
                                                int klast, HopCoef<R> hv, HopCoef<R> hw) {
     using VT = typename BVec<R>::T;
     const BSeq& q = S[bseq[blockIdx.x]];
     KState* ks = q.ks;
     if (ks->done || ks->status) return;
-    const int local = blockIdx.x - q.blk0;
+    constexpr int BT = SHAPE_SITES[SH];
+    const int local = blockIdx.x - q.blk0[SH];
     const int site = local * BT + threadIdx.x;
     const cx<R> sv = mk((R)ks->sv.x, (R)ks->sv.y), sw = mk((R)ks->sw.x, (R)ks->sw.y);
     const VT* vi = (const VT*)vslot<R>(q, i, false);
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(BT) k_b_pair(const BSeq* __restrict__ S, const
         store_spinor((VT*)q.s, q.g.V, site, acc[1]);
     }
     double o[3];
-    if (seq_reduce<3>(a, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
+    if (seq_reduce<3, BT / 32>(a, q.part, q.cnt, local, q.nblk[SH], o) && threadIdx.x == 0) {
         const cx<double> alpha = cdot(d2c(ks->sw), mk(o[0], o[1]));  // conj(sw) w~^dag t
         q.alpha[i] = c2d(alpha);
         ks->anorm = fmax(ks->anorm, sqrt(o[2]));
@@ -245,8 +246,8 @@ __global__ void __launch_bounds__(BT) k_b_pair(const BSeq* __restrict__ S, const
 
 // v^ = t - alpha v_i - gamma_{i-1} v_{i-1}, w^ = s - conj(alpha) w_i - conj(beta_{i-1}) w_{i-1};
 // w^^dag v^, |v^|^2, |w^|^2 -> beta_i, gamma_i, the scales, breakdown checks (Eq. 4.2)
-template <class R>
-__global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i) {
+template <class R, int SH>
+__global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_lstep(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i) {
     using VT = typename BVec<R>::T;
     const BSeq& q = S[bseq[blockIdx.x]];
     KState* ks = q.ks;
@@ -263,7 +264,8 @@ __global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, cons
         cf[3] = mk((R)db.r, (R)db.i);
     }
     __syncthreads();
-    const int local = blockIdx.x - q.blk0;
+    constexpr int BT = SHAPE_SITES[SH];
+    const int local = blockIdx.x - q.blk0[SH];
     const int site = local * BT + threadIdx.x;
     typename AccOf<R>::T a[4];
     if (site < q.g.V) {
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(BT) k_b_lstep(const BSeq* __restrict__ S, cons
         store_spinor((VT*)vslot<R>(q, i + 1, true), q.g.V, site, s);
     }
     double o[4];
-    if (seq_reduce<4>(a, q.part, q.cnt, local, q.nblk, o) && threadIdx.x == 0) {
+    if (seq_reduce<4, BT / 32>(a, q.part, q.cnt, local, q.nblk[SH], o) && threadIdx.x == 0) {
         const double nv = sqrt(o[2]), nw = sqrt(o[3]);
         const cx<double> delta = mk(o[0], o[1]);
         if (nv <= 1e-13 * fmax(ks->anorm, 1e-300)) {
@@ -325,8 +327,8 @@ template <class R> __device__ __forceinline__ cx<R> cvt_coef(cx<double> z);
 template <> __device__ __forceinline__ cx<double> cvt_coef<double>(cx<double> z) { return z; }
 template <> __device__ __forceinline__ cx<df> cvt_coef<df>(cx<double> z) { return mk(df(z.r), df(z.i)); }
 
-template <class R, int LF>
-__global__ void __launch_bounds__(8 * TT, 3) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
+template <class R, int LF, int MINB>
+__global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
                                                     HopCoef<R> hc) {
     using VT = typename VecT<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -403,10 +405,16 @@ struct ovl_batch {
     void* mem = nullptr;
     size_t mem_bytes = 0;
     ovl::BSeq* dseq = nullptr;
-    int* dbseq = nullptr;
+    int* dbseq[ovl::NSHAPE] = {nullptr, nullptr, nullptr};
     int* dtseq = nullptr;
-    int nblocks = 0;
+    int nblocks[ovl::NSHAPE] = {0, 0, 0};
     int ntiles = 0;
+    // autotuned launch shapes: pass-1 site-block shape, blocks per SM of the regeneration kernel
+    int shape = 1;
+    int regen_minb = 3;
+    bool tuned = false;
+    bool pinned = false;        // shapes set by ovl_batch_set_tuning: never retuned
+    int tuned_mode = -1;
     std::vector<ovl::BSeq> hseq;
     std::vector<double2*> b64, bR, bL, pq;
     ovl::KState* ks = nullptr;
@@ -458,12 +466,12 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t total = 0;
     std::vector<size_t> seq_bytes(ns);
-    int nblocks = 0, ntiles = 0;
+    int nblocks[ovl::NSHAPE] = {0, 0, 0}, ntiles = 0;
     for (int s = 0; s < ns; ++s) {
         const ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const size_t n = c->n;
-        const int nblk = (c->g.V + ovl::BT - 1) / ovl::BT;
-        nblocks += nblk;
+        const int nblk = (c->g.V + ovl::SHAPE_SITES[0] - 1) / ovl::SHAPE_SITES[0];  // the most blocks
+        for (int h = 0; h < ovl::NSHAPE; ++h) nblocks[h] += (c->g.V + ovl::SHAPE_SITES[h] - 1) / ovl::SHAPE_SITES[h];
         ntiles += (c->g.V + ovl::TT - 1) / ovl::TT;
         size_t z = 0;
         z += 4 * al(n * sizeof(double2));                        // b, bR, bL, y
@@ -477,7 +485,8 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     }
     total += al(ns * sizeof(ovl::KState)) + 5 * al(ns * kk * sizeof(double2)) +
              al((size_t)ns * inner_stride * sizeof(double2)) + al((size_t)ns * qpart_stride * sizeof(double)) +
-             al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks * sizeof(int)) +
+             al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks[0] * sizeof(int)) +
+             al(nblocks[1] * sizeof(int)) + al(nblocks[2] * sizeof(int)) +
              al(ntiles * sizeof(int)) +
              al((size_t)(1 << 20) * sizeof(double)) + al(64 * sizeof(unsigned int));
     if (cudaMalloc(&b->mem, total) != cudaSuccess) {
@@ -499,16 +508,15 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     b->qpart_stride = qpart_stride;
     b->qcnt = (unsigned int*)take(ns * 64 * sizeof(unsigned int));
     b->dseq = (ovl::BSeq*)take(ns * sizeof(ovl::BSeq));
-    b->dbseq = (int*)take(nblocks * sizeof(int));
+    for (int h = 0; h < ovl::NSHAPE; ++h) b->dbseq[h] = (int*)take(nblocks[h] * sizeof(int));
     b->dtseq = (int*)take(ntiles * sizeof(int));
     b->part = (double*)take((size_t)(1 << 20) * sizeof(double));
     b->counter = (unsigned int*)take(64 * sizeof(unsigned int));
     b->hseq.assign(ns, ovl::BSeq());
     b->b64.assign(ns, nullptr), b->bR.assign(ns, nullptr), b->bL.assign(ns, nullptr), b->pq.assign(ns, nullptr);
-    std::vector<int> table, ttable;
-    table.reserve(nblocks);
+    std::vector<int> table[ovl::NSHAPE], ttable;
     ttable.reserve(ntiles);
-    int blk0 = 0, tile0 = 0;
+    int blk0[ovl::NSHAPE] = {0, 0, 0}, tile0 = 0;
     for (int s = 0; s < ns; ++s) {
         ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const size_t n = c->n;
@@ -546,22 +554,26 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         q.gamma = b->gamma + s * kk;
         q.cvec = b->cvec + s * kk;
         q.vscale = b->vscale + s * kk;
-        q.nblk = (c->g.V + ovl::BT - 1) / ovl::BT;
-        q.part = (double2*)take((size_t)q.nblk * 4 * sizeof(double2));
+        for (int h = 0; h < ovl::NSHAPE; ++h) q.nblk[h] = (c->g.V + ovl::SHAPE_SITES[h] - 1) / ovl::SHAPE_SITES[h];
+        q.part = (double2*)take((size_t)q.nblk[0] * 4 * sizeof(double2));
         b->pq[s] = (double2*)take(128 * sizeof(double2));
         q.cnt = b->qcnt + s;  // the inner quadrature's counters follow at qcnt + nseq
-        q.blk0 = blk0;
-        for (int j = 0; j < q.nblk; ++j) table.push_back(s);
-        blk0 += q.nblk;
+        for (int h = 0; h < ovl::NSHAPE; ++h) {
+            q.blk0[h] = blk0[h];
+            for (int j = 0; j < q.nblk[h]; ++j) table[h].push_back(s);
+            blk0[h] += q.nblk[h];
+        }
         q.ntile = (c->g.V + ovl::TT - 1) / ovl::TT;
         q.tile0 = tile0;
         for (int j = 0; j < q.ntile; ++j) ttable.push_back(s);
         tile0 += q.ntile;
     }
-    b->nblocks = blk0;
+    for (int h = 0; h < ovl::NSHAPE; ++h) b->nblocks[h] = blk0[h];
     b->ntiles = tile0;
     if (cudaMemcpy(b->dseq, b->hseq.data(), ns * sizeof(ovl::BSeq), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->dbseq, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dbseq[0], table[0].data(), table[0].size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dbseq[1], table[1].data(), table[1].size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dbseq[2], table[2].data(), table[2].size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dtseq, ttable.data(), ttable.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->qcnt, 0, ns * 64 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(b->counter, 0, 64 * sizeof(unsigned int)) != cudaSuccess) {
@@ -573,8 +585,44 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     return OVL_OK;
 }
 
+// One pass-1 step of every sequence with site-block shape SH.
+template <int SH>
+void pass1_step(ovl_batch* b, int i, int k, double mu, double kappa, bool mixed, cudaStream_t st) {
+    const int nb = b->nblocks[SH], T = ovl::SHAPE_SITES[SH];
+    if (mixed) {
+        ovl::k_b_pair<ovl::LINK_F32_12, float, SH><<<nb, T, 0, st>>>(
+            b->dseq, b->dbseq[SH], i, k - 1, ovl::make_coef<float>(mu, kappa), ovl::make_coef<float>(-mu, kappa));
+        if (i + 1 < k) ovl::k_b_lstep<float, SH><<<nb, T, 0, st>>>(b->dseq, b->dbseq[SH], i);
+    } else {
+        ovl::k_b_pair<ovl::LINK_F64, double, SH><<<nb, T, 0, st>>>(
+            b->dseq, b->dbseq[SH], i, k - 1, ovl::make_coef<double>(mu, kappa), ovl::make_coef<double>(-mu, kappa));
+        if (i + 1 < k) ovl::k_b_lstep<double, SH><<<nb, T, 0, st>>>(b->dseq, b->dbseq[SH], i);
+    }
+}
+
+// One regeneration step of every sequence, blocks-per-SM bound MINB.
+template <int MINB>
+void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStream_t st) {
+    const size_t smr = (size_t)8 * ovl::TT * 12 * 16;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smr);
+        cudaFuncSetAttribute(ovl::k_b_regen<double, ovl::LINK_F64, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        attr = true;
+    }
+    if (dfm)
+        ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB><<<b->ntiles, 8 * ovl::TT, smr, st>>>(
+            b->dseq, b->dtseq, i, ovl::make_coef<ovl::df>(mu, kappa));
+    else
+        ovl::k_b_regen<double, ovl::LINK_F64, MINB><<<b->ntiles, 8 * ovl::TT, smr, st>>>(
+            b->dseq, b->dtseq, i, ovl::make_coef<double>(mu, kappa));
+}
+
 // Everything between the packed sources and the unpacked results, on stream st.
 int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaStream_t st) {
+    if (k > b->kcap) return bfail(b, OVL_EINVAL, "k exceeds the batch workspace");
     const bool mixed = b->mode == 1;
     const bool twopass = b->mode != 0;
     const int ns = b->nseq;
@@ -600,17 +648,12 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
         }
     }
     // pass 1 (all sequences per launch)
-    const int nb = b->nblocks;
     if (prof) cudaEventRecord(b->ev[0], st);
     for (int i = 0; i < k; ++i) {
-        if (mixed) {
-            ovl::k_b_pair<ovl::LINK_F32_12, float><<<nb, ovl::BT, 0, st>>>(
-                b->dseq, b->dbseq, i, k - 1, ovl::make_coef<float>(mu, kappa), ovl::make_coef<float>(-mu, kappa));
-            if (i + 1 < k) ovl::k_b_lstep<float><<<nb, ovl::BT, 0, st>>>(b->dseq, b->dbseq, i);
-        } else {
-            ovl::k_b_pair<ovl::LINK_F64, double><<<nb, ovl::BT, 0, st>>>(
-                b->dseq, b->dbseq, i, k - 1, ovl::make_coef<double>(mu, kappa), ovl::make_coef<double>(-mu, kappa));
-            if (i + 1 < k) ovl::k_b_lstep<double><<<nb, ovl::BT, 0, st>>>(b->dseq, b->dbseq, i);
+        switch (b->shape) {
+            case 0: pass1_step<0>(b, i, k, mu, kappa, mixed, st); break;
+            case 1: pass1_step<1>(b, i, k, mu, kappa, mixed, st); break;
+            default: pass1_step<2>(b, i, k, mu, kappa, mixed, st); break;
         }
     }
     // inner sign of every sequence at once; Roberts' iteration where the quadrature did not settle
@@ -631,17 +674,7 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
     if (prof) cudaEventRecord(b->ev[2], st);
     if (twopass) {
         // mixed: double-float regeneration unless OVL_PASS2_F64 (ring and y converted in place)
-        const int nt = b->ntiles;
         const bool dfm = mixed && !(flags & OVL_PASS2_F64);
-        const size_t smr = (size_t)8 * ovl::TT * 12 * 16;
-        static bool rattr = false;
-        if (!rattr) {
-            cudaFuncSetAttribute(ovl::k_b_regen<ovl::df, ovl::LINK_DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smr);
-            cudaFuncSetAttribute(ovl::k_b_regen<double, ovl::LINK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smr);
-            rattr = true;
-        }
         for (int s = 0; s < ns; ++s) {
             const ovl::BSeq& q = b->hseq[s];
             ovl::launch_scale_start(b->bR[s], q.r[0], q.y, q.cvec, q.ks, q.n, st);
@@ -651,12 +684,11 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
             }
         }
         for (int i = 0; i + 1 < k; ++i) {
-            if (dfm)
-                ovl::k_b_regen<ovl::df, ovl::LINK_DF><<<nt, 8 * ovl::TT, smr, st>>>(b->dseq, b->dtseq, i,
-                                                                                  ovl::make_coef<ovl::df>(mu, kappa));
-            else
-                ovl::k_b_regen<double, ovl::LINK_F64><<<nt, 8 * ovl::TT, smr, st>>>(b->dseq, b->dtseq, i,
-                                                                                  ovl::make_coef<double>(mu, kappa));
+            switch (b->regen_minb) {
+                case 2: regen_step<2>(b, i, mu, kappa, dfm, st); break;
+                case 4: regen_step<4>(b, i, mu, kappa, dfm, st); break;
+                default: regen_step<3>(b, i, mu, kappa, dfm, st); break;
+            }
         }
         if (dfm)
             for (int s = 0; s < ns; ++s) ovl::launch_df_to_f64(b->hseq[s].y, b->hseq[s].n, st);
@@ -670,9 +702,68 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
     return cudaGetLastError() == cudaSuccess ? OVL_OK : bfail(b, OVL_ECUDA, "batch launch");
 }
 
+// Autotuner of the batched kernels' launch shapes (site-block size of the pass-1 kernels, blocks
+// per SM of the regeneration kernel): each candidate runs a short eager solve (TUNE_K steps) of the
+// whole batch with events around its phases; the fastest pass-1 and regeneration candidates are
+// kept for the batch.  The sources must already be packed.
+int autotune(ovl_batch* b, double mu, double kappa, int flags, cudaStream_t st) {
+    if (b->kcap < 8) return OVL_OK;  // too short to time; the defaults stay until a longer solve
+    const int TUNE_K = std::min(24, b->kcap);  // the workspace holds kcap steps
+    const int saved_shape = b->shape, saved_minb = b->regen_minb;
+    for (cudaEvent_t& e : b->ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) return bfail(b, OVL_ECUDA, "tuning events");
+    const int minbs[ovl::NSHAPE] = {2, 3, 4};
+    float best1 = 1e30f, best2 = 1e30f;
+    int bs = saved_shape, bm = saved_minb;
+    for (int rep = 0; rep < 2; ++rep)  // the first round warms caches and instruction memory
+        for (int c = 0; c < ovl::NSHAPE; ++c) {
+            b->shape = c;
+            b->regen_minb = minbs[c];
+            const int r = enqueue_batch(b, TUNE_K, mu, kappa, (flags | OVL_PROFILE) & ~OVL_NO_GRAPH, st);
+            if (r) return r;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return bfail(b, OVL_ECUDA, "tuning solve");
+            float t1 = 0.f, t2 = 0.f;
+            cudaEventElapsedTime(&t1, b->ev[0], b->ev[1]);
+            cudaEventElapsedTime(&t2, b->ev[2], b->ev[3]);
+            if (rep == 1) {
+                if (t1 < best1) best1 = t1, bs = c;
+                if (t2 < best2) best2 = t2, bm = minbs[c];
+            }
+        }
+    b->shape = bs;
+    b->regen_minb = bm;
+    b->tuned = true;
+    b->tuned_mode = b->mode;
+    if (b->exec) cudaGraphExecDestroy(b->exec);  // a captured graph holds the old shapes
+    b->exec = nullptr;
+    return OVL_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ovl_batch_tuning(const ovl_batch* b, int* pass1_block_sites, int* regen_blocks_per_sm) {
+    if (!b) return OVL_EINVAL;
+    if (pass1_block_sites) *pass1_block_sites = ovl::SHAPE_SITES[b->shape];
+    if (regen_blocks_per_sm) *regen_blocks_per_sm = b->regen_minb;
+    return b->tuned ? OVL_OK : OVL_ESTATE;
+}
+
+int ovl_batch_set_tuning(ovl_batch* b, int pass1_block_sites, int regen_blocks_per_sm) {
+    if (!b) return OVL_EINVAL;
+    int sh = -1;
+    for (int c = 0; c < ovl::NSHAPE; ++c)
+        if (ovl::SHAPE_SITES[c] == pass1_block_sites) sh = c;
+    if (sh < 0 || regen_blocks_per_sm < 2 || regen_blocks_per_sm > 4)
+        return bfail(b, OVL_EINVAL, "unsupported launch shape");
+    b->shape = sh;
+    b->regen_minb = regen_blocks_per_sm;
+    b->tuned = b->pinned = true;
+    if (b->exec) cudaGraphExecDestroy(b->exec);  // a captured graph holds the old shapes
+    b->exec = nullptr;
+    return OVL_OK;
+}
 
 int ovl_batch_create(ovl_batch** out, ovl_ctx* const* ctxs, int nctx, const int* nrhs) {
     if (!out || !ctxs || nctx < 1 || !nrhs) return OVL_EINVAL;
@@ -747,6 +838,11 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
             }
             ovl::launch_pack_spinor(src, b->b64[s], 0, c->g, st);
         }
+    }
+    // launch shapes: timed once per batch on its own data (short eager solves), unless OVL_NO_TUNE
+    if (!b->pinned && b->tuned_mode != mode && !(flags & OVL_NO_TUNE)) {
+        r = autotune(b, mu, kappa, flags, st);
+        if (r) return r;
     }
     // the solve, as a graph captured once per (k, flags, mu, kappa); per-phase events need eager launches
     if (flags & OVL_PROFILE) {

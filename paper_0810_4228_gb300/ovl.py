@@ -26,6 +26,7 @@ ARNOLDI, LANCZOS2 = 0, 1
 GAMMA5, DAGGER, NATIVE, HOST, F32, F32_FULL = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 OVERLAP, MIXED, TWO_PASS, INNER_NEWTON, NO_GRAPH, PROFILE = 0x100, 0x200, 0x400, 0x1000, 0x2000, 0x4000
 STENCIL_SITE, STENCIL_SPLIT, REPROJ, STEPWISE, PASS2_F64, PASS2_DF = 0x10000, 0x20000, 0x8000, 0x40000, 0x80000, 0x100000
+NO_TUNE = 0x200000
 
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EBREAKDOWN",
              ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
@@ -34,7 +35,8 @@ EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl
            "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
            "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad", "ovl_batch_create",
-           "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_batch_profile",
+           "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_batch_profile", "ovl_batch_tuning",
+           "ovl_batch_set_tuning",
            "ovl_sign_krylov_batched"]
 
 
@@ -103,6 +105,8 @@ def load(path: str = LIB_PATH):
         "ovl_batch_last_error": (ctypes.c_char_p, [P]),
         "ovl_batch_solve": (I, [P, I, D, D, ctypes.POINTER(P), ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
         "ovl_batch_profile": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
+        "ovl_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ovl_batch_set_tuning": (I, [P, I, I]),
         "ovl_sign_krylov_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, D, D, ctypes.POINTER(P),
                                         ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
     }
@@ -374,3 +378,16 @@ class Batch:
         n = ctypes.c_int()
         self._lib.ovl_batch_profile(self._h, ms, ctypes.byref(n), 1 if reset else 0)
         return {"pass1": ms[0], "inner_sign": ms[1], "pass2_or_combine": ms[2]}, n.value
+
+    def tuning(self):
+        """(pass-1 sites per block, regeneration blocks per SM) chosen by the autotuner, or None."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        r = self._lib.ovl_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(b))
+        return (a.value, b.value) if r == 0 else None
+
+    def set_tuning(self, pass1_block_sites: int, regen_blocks_per_sm: int):
+        """Pin the launch shapes (64/128/256 sites per pass-1 block, 2/3/4 regeneration blocks per SM);
+        the autotuner is then skipped."""
+        r = self._lib.ovl_batch_set_tuning(self._h, int(pass1_block_sites), int(regen_blocks_per_sm))
+        if r:
+            raise OvlError(r, self._lib.ovl_batch_last_error(self._h).decode())

@@ -206,3 +206,61 @@ def test_batch_double_float_pass2_matches_fp64_pass2(ovl, mid):
     for r in range(3):
         assert rel(y_df[r], y_64[r]) < 1e-11
     bt.close()
+
+
+def test_batch_autotuner_picks_shapes(ovl, small):
+    """The first solve times the launch-shape candidates and keeps one; OVL_NO_TUNE keeps the defaults."""
+    c = _ctx(ovl, small["dims"], small["U"])
+    b = torch_c128(_sources(small["dims"], 4000, 2))
+    bt = ovl.Batch([c], [2])
+    assert bt.tuning() is None
+    y1 = bt.solve(25, small["mu"], KAPPA, [b])[0][0].cpu().numpy()
+    sites, minb = bt.tuning()
+    assert sites in (64, 128, 256) and minb in (2, 3, 4)
+    bt2 = ovl.Batch([c], [2])
+    y2 = bt2.solve(25, small["mu"], KAPPA, [b], flags=ovl.NO_TUNE)[0][0].cpu().numpy()
+    assert bt2.tuning() is None
+    for r in range(2):
+        assert rel(y1[r], y2[r]) < 1e-12
+        assert rel(y1[r], _oracle_2sl(small, b.cpu().numpy()[r], 25)) < 1e-11
+    bt.close()
+    bt2.close()
+
+
+@pytest.mark.parametrize("sites,minb", [(64, 2), (128, 3), (256, 4), (64, 4), (256, 2)])
+def test_batch_every_pinned_shape(ovl, small, mid, sites, minb):
+    """Each pinned launch shape: FP64 two-pass at k = 25 against the oracle's two-sided Lanczos on
+    a lattice smaller than one block, and mixed precision on two lattices against the dense sign."""
+    dims, U = small["dims"], small["U"]
+    c = _ctx(ovl, dims, U)
+    b = _sources(dims, 4100, 3)
+    bt = ovl.Batch([c], [3])
+    bt.set_tuning(sites, minb)
+    assert bt.tuning() == (sites, minb)
+    y = bt.solve(25, small["mu"], KAPPA, [torch_c128(b)], flags=ovl.TWO_PASS)[0][0].cpu().numpy()
+    for r in range(3):
+        assert rel(y[r], _oracle_2sl(small, b[r], 25)) < 1e-11, r
+    bt.close()
+    c4 = config4()
+    ca, cb = _ctx(ovl, c4["dims"], c4["U"]), _ctx(ovl, mid["dims"], mid["U"])
+    ba, bb = _sources(c4["dims"], 4101, 2), _sources(mid["dims"], 4102, 2)
+    bt = ovl.Batch([ca, cb], [2, 2])
+    bt.set_tuning(sites, minb)
+    outs, _, st = bt.solve(500, c4["mu"], KAPPA, [torch_c128(ba), torch_c128(bb)], flags=ovl.MIXED)
+    assert st == 0 and bt.tuning() == (sites, minb)
+    sgn4 = c4["X"] @ (S.csign(c4["lam"])[:, None] * c4["Xi"])
+    for r in range(2):
+        assert rel(outs[0][r].cpu().numpy(), sgn4 @ ba[r]) < 1e-8
+        assert rel(outs[1][r].cpu().numpy(), mid["sgn"] @ bb[r]) < 1e-8
+    bt.close()
+
+
+def test_batch_rejects_unknown_shape(ovl, small):
+    c = _ctx(ovl, small["dims"], small["U"])
+    bt = ovl.Batch([c], [1])
+    with pytest.raises(ovl.OvlError):
+        bt.set_tuning(96, 3)
+    with pytest.raises(ovl.OvlError):
+        bt.set_tuning(128, 5)
+    assert bt.tuning() is None
+    bt.close()
