@@ -249,19 +249,23 @@ int ovl_set_deflation(ovl_ctx* ctx, double mu, double kappa, int m, const double
 /* Result of ovl_deflation_eigs. */
 typedef struct {
     int       m;             /* eigenpairs installed                                     */
-    int       iterations;    /* filtered subspace iterations (right + left side)          */
+    int       iterations;    /* Arnoldi restart cycles (right + left side)                */
     long long matvecs;       /* applications of A or A^dag                                */
     double    max_residual;  /* max |A r_j - lambda_j r_j| of the installed right pairs  */
-    double    lambda_cut;    /* |lambda| above which the last filter damped the spectrum  */
+    double    lambda_cut;    /* largest |lambda| among the m + nextra computed pairs      */
 } ovl_eiginfo;
 
 /* Deflation phase on the GPU (Sec. 3 and Sec. 5, where ARPACK plays this role): compute the
  * m + nextra eigenvalues of A = gamma5 D_w(mu) nearest 0 with right and left eigenvectors
- * (Chebyshev-filtered subspace iteration on A^2 with Rayleigh-Ritz on A and on A^dag,
- * filter degree `degree`, at most `maxit` iterations, residual |A r - lambda r| <= tol |A|),
- * keep the m of smallest |Re lambda|, and install them as by ovl_set_deflation.  Returns
- * OVL_ENOCONV if the iteration did not converge.  Uses its own temporary device memory. */
-int ovl_deflation_eigs(ovl_ctx* ctx, double mu, double kappa, int m, int nextra, double tol, int degree,
+ * (thick-restart Arnoldi on A^2 with a basis of nkrylov vectors, 0 = 10 (m + nextra) within
+ * [3 (m + nextra) + 40, 512], at
+ * most maxit restart cycles, then Rayleigh-Ritz with A and with A^dag; residual
+ * |A r - lambda r| <= tol |A|), keep the m of smallest |Re lambda|, and install them as by
+ * ovl_set_deflation.  Returns OVL_ENOCONV if the iteration did not converge (nothing
+ * installed; info, if given, then holds m = 0 and the progress: cycles, matvecs, the last
+ * residual check of the side that stopped).  Uses its own temporary device memory
+ * (about 2 nkrylov + 2 (m + nextra) vectors). */
+int ovl_deflation_eigs(ovl_ctx* ctx, double mu, double kappa, int m, int nextra, double tol, int nkrylov,
                        int maxit, ovl_eiginfo* info);
 
 /* Copy the installed (bi-orthonormalised) deflation out: *m_out = m; lambda (host, 2m

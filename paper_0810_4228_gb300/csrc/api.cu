@@ -74,6 +74,14 @@ void drop_graph(ovl_ctx* c) {
 int ensure_base(ovl_ctx* c) {
     const size_t vb = c->n * sizeof(double2);
     int r;
+    // the grid-reduction ticket and the barrier counter start at zero (the last block of every
+    // reduction resets its ticket)
+    const bool fresh = c->counter == nullptr || c->bar == nullptr;
+    if (fresh && ((r = dalloc(c, &c->counter, 64)) || (r = dalloc(c, &c->bar, 64)))) return r;
+    if (fresh) {
+        CUDA_TRY(c, cudaMemsetAsync(c->counter, 0, 64, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(c->bar, 0, 64, c->st));
+    }
     if ((r = dalloc(c, &c->b64, vb)) || (r = dalloc(c, &c->y64, vb)) || (r = dalloc(c, &c->bR, vb)) ||
         (r = dalloc(c, &c->bL, vb)) || (r = dalloc(c, &c->t64, vb)) || (r = dalloc(c, &c->s64, vb)) ||
         (r = dalloc(c, &c->t32, c->n * sizeof(float2))) || (r = dalloc(c, &c->s32, c->n * sizeof(float2))) ||

@@ -3,21 +3,29 @@
 // per gauge field and mu for all sources (Sec. 3, last paragraph; Sec. 5 uses
 // ARPACK on the CPU for this step).
 //
-// Method: Chebyshev-filtered subspace iteration on T = A^2.  The eigenvalues of
-// A nearest 0 are the smallest of T = A^2, which for gamma5 D_w(mu) at moderate
-// mu lie close to the positive real axis; a degree-d Chebyshev polynomial of T
-// on [a, b] (a = the largest Ritz value of T in the current block, b an upper
-// bound of |T|) damps everything above a and amplifies the wanted end.  Each
-// iteration filters the block, orthonormalises it (classical Gram-Schmidt
-// twice) and performs a Rayleigh-Ritz projection with A itself, whose small
-// dense eigenproblem is solved on the host (host_eig.cpp).  Ritz vectors of
-// A^dag = gamma5 D_w(-mu) give the left eigenvectors; pairs are matched by
-// lambda_left = conj(lambda_right), the m of smallest |Re lambda| are kept and
-// bi-orthonormalised (L <- L (L^dag R)^-H) when installed.
-// All vector work runs in the library's kernels; only nb x nb matrices visit
-// the host.  Not on the timed path (the paper excludes the deflation phase
-// from its timings, Sec. 5).
+// Method: thick-restart Arnoldi (Krylov-Schur form) on T = A^2.  The eigenvalues
+// of A nearest 0 are those of T of smallest modulus.  For gamma5 D_w(mu) at
+// moderate mu the spectrum of A lies close to the real axis, so T's lies in a
+// thin region along the positive real axis, and the wanted ones sit at its end
+// near 0, where Krylov methods converge.  (A Chebyshev filter on a real interval,
+// the first version of this solver, also amplifies the eigenvalues of T off the
+// real axis at the far end, Im(lambda^2) = 2 Re(lambda) Im(lambda), and stalled
+// on 16^3 x 8.)  Each cycle extends an orthonormal basis V to nkrylov vectors
+// (classical Gram-Schmidt twice, the library's Arnoldi kernels), computes the
+// Ritz pairs of the projected matrix H on the host (host_eig.cpp) and restarts
+// from the orthonormalised Ritz vectors of the want + keep smallest |theta| and
+// the last basis vector: with Q those Ritz vectors' coordinates,
+// T (V Q) = (V Q)(Q^dag H Q) + h v_next e^T Q keeps the Arnoldi relation with a
+// full last row.  Once the want smallest pairs of T have residuals
+// <= tol |T|, a Rayleigh-Ritz step with A itself on their span gives the
+// eigenpairs of A (right vectors from A, left ones from A^dag = gamma5
+// D_w(-mu)).  Pairs are matched by lambda_left = conj(lambda_right), the m of
+// smallest |Re lambda| kept and bi-orthonormalised (L <- L (L^dag R)^-H) when
+// installed.  All vector work runs in the library's kernels; only nkrylov x
+// nkrylov matrices visit the host.  Not on the timed path (the paper excludes
+// the deflation phase from its timings, Sec. 5).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <numeric>
@@ -52,22 +60,6 @@ __global__ void k_rand_fill(double2* x, size_t n, unsigned long long seed) {
     }
 }
 
-// Chebyshev step: ynext = s1 * (u - c y) - s0 * yprev   (s0 = 0 on the first step)
-// (u and yn may be the same buffer: every element is read before it is written)
-__global__ void k_cheb(const double2* u, const double2* y, const double2* yp, double2* yn, double c, double s1,
-                       double s0, size_t n) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const double2 uu = u[e], yy = y[e];
-        double2 r = make_double2(s1 * (uu.x - c * yy.x), s1 * (uu.y - c * yy.y));
-        if (s0 != 0.0) {
-            const double2 pp = yp[e];
-            r.x -= s0 * pp.x;
-            r.y -= s0 * pp.y;
-        }
-        yn[e] = r;
-    }
-}
-
 // y <- y / sqrt(h.x)   (h = y^dag y from a preceding dot product)
 __global__ void k_normalize(double2* y, const double2* h, size_t n) {
     const double inv = 1.0 / sqrt(fmax(h->x, 1e-300));
@@ -95,183 +87,299 @@ __global__ void __launch_bounds__(256) k_resid(const double2* __restrict__ t, co
 
 int grid_n(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 1024); }
 
+using cd = std::complex<double>;
+
 struct EigRun {
-    std::vector<std::complex<double>> theta;  // Ritz values (all nb)
-    std::vector<double> resid;
-    int iterations = 0;
+    std::vector<cd> theta;      // eigenvalues of A (want)
+    std::vector<double> resid;  // |A x - theta x| of the unit vectors
+    int cycles = 0;
     long long matvecs = 0;
-    double acut = 0;
+    double tnorm = 0;           // largest |theta(T)| seen (scale of T)
+    double tcut = 0;            // |theta(T)| of the want-th pair
 };
 
-// One side (dagger = 0: A, 1: A^dag): Ritz pairs of the nb-block, the first
-// `want` (smallest |theta|) converged to tol; vectors left in X (nb x n).
-int subspace_iteration(ovl_ctx* c, double mu, double kappa, int dagger, int want, int nb, double tol, int degree,
-                       int maxit, double2* X, double2* Y, double2* tmp3, EigRun& run) {
+// Columns of Q (ne x kk, column-major) made orthonormal: modified Gram-Schmidt, twice.
+bool host_orthonormalise(std::vector<cd>& Q, int ne, int kk) {
+    for (int i = 0; i < kk; ++i) {
+        cd* qi = &Q[(size_t)i * ne];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int l = 0; l < i; ++l) {
+                const cd* ql = &Q[(size_t)l * ne];
+                cd sdot = 0.0;
+                for (int r = 0; r < ne; ++r) sdot += std::conj(ql[r]) * qi[r];
+                for (int r = 0; r < ne; ++r) qi[r] -= sdot * ql[r];
+            }
+        double nn = 0.0;
+        for (int r = 0; r < ne; ++r) nn += std::norm(qi[r]);
+        nn = std::sqrt(nn);
+        if (!(nn > 1e-300)) return false;
+        for (int r = 0; r < ne; ++r) qi[r] /= nn;
+    }
+    return true;
+}
+
+// Device scratch of one run.
+struct ArnWork {
+    double2* V;      // (nk + 1) basis vectors
+    double2* W;      // nk vectors: rotated basis, then the output eigenvectors
+    double2* t0;     // one vector
+    double2* Hd;     // (nk + 1) x nk, column-major
+    double2* h1;     // nk + 2
+    double2* h2;     // nk + 2
+    double2* Qd;     // nk x nk
+    double* part;    // multidot partials for nk + 2 vectors
+    KState* ks;
+};
+
+// out_j = sum_l coef[l + j ld] V_l for j < nout (coef on the host, column-major with leading dimension ld).
+int rotate(ovl_ctx* c, const ArnWork& w, const double2* V, int nv, const std::vector<cd>& coef, int ld, int nout,
+           double2* out) {
+    const size_t n = c->n;
+    cudaStream_t st = c->st;
+    std::vector<cd> neg((size_t)nv * nout);
+    for (int j = 0; j < nout; ++j)
+        for (int l = 0; l < nv; ++l) neg[(size_t)j * nv + l] = -coef[(size_t)j * ld + l];
+    OVL_CUDA_TRY(c, cudaMemcpyAsync(w.Qd, neg.data(), sizeof(double2) * nv * nout, cudaMemcpyHostToDevice, st));
+    OVL_CUDA_TRY(c, cudaMemsetAsync(out, 0, sizeof(double2) * n * nout, st));
+    for (int j = 0; j < nout; ++j)
+        ovl::launch_multiaxpy(V, n, nv, w.Qd + (size_t)j * nv, out + (size_t)j * n, w.part, c->counter, w.ks, 0, n,
+                              st);
+    // the coefficients are read by the kernels above before the next upload
+    OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return OVL_OK;
+}
+
+// One side (dagger = 0: A, 1: A^dag): the want eigenpairs of A of smallest |lambda| with
+// |A x - lambda x| <= tol |A|; unit eigenvectors in out (want x n), eigenvalues in run.theta.
+int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int nk, int keep, double tol,
+                 int maxcycles, const ArnWork& w, double2* out, EigRun& run) {
     const size_t n = c->n;
     cudaStream_t st = c->st;
     const double m_eff = dagger ? -mu : mu;
-    double2* t0 = tmp3;
-    double2* t1 = tmp3 + n;
-    double2* t2 = tmp3 + 2 * n;
+    const int ldH = nk + 1;
     auto applyA = [&](const double2* x, double2* y) {
-        ovl::launch_dslash(c->U64, 0, x, y, m_eff, kappa, 1, c->g, st);
+        ovl::launch_dslash(c->U64, 0, x, y, m_eff, kappa, 1, c->g, st, w.ks);
         ++run.matvecs;
     };
-    // upper bound of |A|^2 by power iteration on A^dag A
-    k_rand_fill<<<grid_n(n), 256, 0, st>>>(t0, n, 0x5eedull + dagger);
-    double2* h = c->h1;
-    double sig2 = 0.0;
-    for (int it = 0; it < 30; ++it) {
-        ovl::launch_multidot(t0, n, 1, t0, h, 0, c->partials, n, st);
-        k_normalize<<<grid_n(n), 256, 0, st>>>(t0, h, n);
-        applyA(t0, t1);
-        ovl::launch_dslash(c->U64, 0, t1, t2, -m_eff, kappa, 1, c->g, st);  // A^dag
-        ++run.matvecs;
-        ovl::launch_multidot(t0, n, 1, t2, h, 0, c->partials, n, st);
-        double2 hv;
-        OVL_CUDA_TRY(c, cudaMemcpyAsync(&hv, h, sizeof(double2), cudaMemcpyDeviceToHost, st));
-        OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
-        sig2 = std::max(sig2, hv.x);
-        std::swap(t0, t2);
-    }
-    t0 = tmp3, t1 = tmp3 + n, t2 = tmp3 + 2 * n;
-    const double bup = 1.15 * sig2;
-    double acut = bup / 20.0;
-    // random start block
-    for (int j = 0; j < nb; ++j)
-        k_rand_fill<<<grid_n(n), 256, 0, st>>>(X + (size_t)j * n, n, 0x1234ull * (j + 1) + 77 * dagger);
-    std::vector<std::complex<double>> H((size_t)nb * nb), Hr((size_t)nb * nb), w, Z;
-    double2* Hd = c->inner;  // nb*nb + nb*nb scratch
-    double2* Zd = c->inner + (size_t)nb * nb;
-    KState zero;
-    std::memset(&zero, 0, sizeof(zero));
-    OVL_CUDA_TRY(c, cudaMemcpyAsync(c->ks, &zero, sizeof(KState), cudaMemcpyHostToDevice, st));
-    for (int iter = 0; iter < maxit; ++iter) {
-        run.iterations = iter + 1;
-        // filter every block vector: Y_j = p_d(A^2) X_j on [acut, bup]
-        const double cc = 0.5 * (bup + acut), ee = 0.5 * (bup - acut);
-        for (int j = 0; j < nb; ++j) {
-            const double2* x = X + (size_t)j * n;
-            double2 *yp = t0, *y = t1, *yn = t2;
-            OVL_CUDA_TRY(c, cudaMemcpyAsync(yp, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            applyA(yp, Y + (size_t)j * n);
-            applyA(Y + (size_t)j * n, y);  // y = A^2 x
-            k_cheb<<<grid_n(n), 256, 0, st>>>(y, yp, nullptr, y, cc, 1.0 / ee, 0.0, n);
-            for (int d = 1; d < degree; ++d) {
-                applyA(y, Y + (size_t)j * n);
-                applyA(Y + (size_t)j * n, yn);
-                k_cheb<<<grid_n(n), 256, 0, st>>>(yn, y, yp, yn, cc, 2.0 / ee, 1.0, n);
-                double2* tswap = yp;
-                yp = y;
-                y = yn;
-                yn = tswap;
-            }
-            OVL_CUDA_TRY(c, cudaMemcpyAsync(Y + (size_t)j * n, y, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            // classical Gram-Schmidt twice against Y_0..Y_{j-1}, then normalise
-            for (int pass = 0; pass < 2 && j > 0; ++pass) {
-                ovl::launch_multidot(Y, n, j, Y + (size_t)j * n, c->h2, 0, c->partials, n, st);
-                ovl::launch_multiaxpy(Y, n, j, c->h2, Y + (size_t)j * n, c->partials, c->counter, c->ks, 0, n, st);
-            }
-            ovl::launch_multidot(Y + (size_t)j * n, n, 1, Y + (size_t)j * n, h, 0, c->partials, n, st);
-            k_normalize<<<grid_n(n), 256, 0, st>>>(Y + (size_t)j * n, h, n);
+    auto reset_state = [&]() { return cudaMemsetAsync(w.ks, 0, sizeof(KState), st); };
+    // random unit start vector
+    OVL_CUDA_TRY(c, reset_state());
+    k_rand_fill<<<grid_n(n), 256, 0, st>>>(w.V, n, 0x1234ull + 77 * dagger);
+    ovl::launch_multidot(w.V, n, 1, w.V, w.h1, 0, w.part, n, st);
+    k_normalize<<<grid_n(n), 256, 0, st>>>(w.V, w.h1, n);
+    std::vector<cd> Hh((size_t)ldH * nk, 0.0);
+    std::vector<cd> Ar, th, Z;
+    int kk = 0;
+    double ttol = tol;
+    for (int cyc = 0; cyc < maxcycles; ++cyc) {
+        run.cycles = cyc + 1;
+        // ---- extend the basis from kk to nk vectors (T v_j = A (A v_j), CGS2 against V_0..V_j)
+        OVL_CUDA_TRY(c, reset_state());
+        for (int j = kk; j < nk; ++j) {
+            const double2* vj = w.V + (size_t)j * n;
+            double2* x = w.V + (size_t)(j + 1) * n;
+            applyA(vj, w.t0);
+            applyA(w.t0, x);
+            ovl::launch_multidot(w.V, n, j + 1, x, w.h1, 0, w.part, n, st, w.ks);
+            ovl::launch_multiaxpy(w.V, n, j + 1, w.h1, x, w.part, c->counter, w.ks, 0, n, st);
+            ovl::launch_multidot(w.V, n, j + 1, x, w.h2, 0, w.part, n, st, w.ks);
+            ovl::launch_arnoldi_orth2(w.V, n, j + 1, w.h2, x, w.Hd, ldH, w.h1, j, INT_MAX, w.part, c->counter, w.ks,
+                                      n, st);
+            ovl::launch_arnoldi_normalize(x, w.ks, n, st);
         }
-        // Rayleigh-Ritz with A: H = Y^dag A Y (column j = Y^dag (A y_j))
-        for (int j = 0; j < nb; ++j) {
-            applyA(Y + (size_t)j * n, t0);
-            ovl::launch_multidot(Y, n, nb, t0, Hd + (size_t)j * nb, 0, c->partials, n, st);
-        }
-        OVL_CUDA_TRY(c, cudaMemcpyAsync(H.data(), Hd, sizeof(double2) * nb * nb, cudaMemcpyDeviceToHost, st));
+        KState ks;
+        OVL_CUDA_TRY(c, cudaMemcpyAsync(&ks, w.ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
         OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
-        for (int i = 0; i < nb; ++i)
-            for (int j = 0; j < nb; ++j) Hr[(size_t)i * nb + j] = H[i + (size_t)j * nb];
-        if (ovl::host_eig(nb, Hr, w, Z) != 0) return fail(c, OVL_ENOCONV, "Rayleigh-Ritz eigensolver failed");
-        // order Ritz pairs by |theta|
-        std::vector<int> ord(nb);
+        if (ks.status) return fail(c, OVL_ECUDA, "eigensolver Arnoldi step");
+        const int ne = ks.done ? ks.kused : nk;  // a lucky breakdown leaves an invariant subspace
+        if (ne > kk)
+            OVL_CUDA_TRY(c, cudaMemcpyAsync(&Hh[(size_t)kk * ldH], w.Hd + (size_t)kk * ldH,
+                                            sizeof(double2) * ldH * (ne - kk), cudaMemcpyDeviceToHost, st));
+        OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
+        // the Arnoldi step writes rows 0 .. j + 1 of column j only: below that H is zero (the device
+        // buffer holds older contents there)
+        for (int j = kk; j < ne; ++j)
+            for (int r2 = j + 2; r2 < ldH; ++r2) Hh[r2 + (size_t)j * ldH] = 0.0;
+        OVL_CUDA_TRY(c, reset_state());
+        // ---- Ritz pairs of H (ne x ne), ordered by |theta|
+        Ar.assign((size_t)ne * ne, 0.0);
+        for (int i = 0; i < ne; ++i)
+            for (int jj = 0; jj < ne; ++jj) Ar[(size_t)i * ne + jj] = Hh[i + (size_t)jj * ldH];
+        std::vector<cd> Hsq = Ar;
+        if (ovl::host_eig(ne, Ar, th, Z) != 0) return fail(c, OVL_ENOCONV, "Ritz eigensolver failed");
+        std::vector<int> ord(ne);
         std::iota(ord.begin(), ord.end(), 0);
-        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(w[a]) < std::abs(w[b]); });
-        // X_j = sum_i Z[i][ord j] y_i
-        std::vector<std::complex<double>> neg((size_t)nb * nb);
-        for (int j = 0; j < nb; ++j)
-            for (int i = 0; i < nb; ++i) neg[(size_t)j * nb + i] = -Z[(size_t)i * nb + ord[j]];
-        OVL_CUDA_TRY(c, cudaMemcpyAsync(Zd, neg.data(), sizeof(double2) * nb * nb, cudaMemcpyHostToDevice, st));
-        OVL_CUDA_TRY(c, cudaMemsetAsync(X, 0, sizeof(double2) * n * nb, st));
-        for (int j = 0; j < nb; ++j)
-            ovl::launch_multiaxpy(Y, n, nb, Zd + (size_t)j * nb, X + (size_t)j * n, c->partials, c->counter, c->ks, 0,
-                                  n, st);
-        run.theta.assign(nb, 0.0);
-        run.resid.assign(nb, 0.0);
-        for (int j = 0; j < nb; ++j) run.theta[j] = w[ord[j]];
-        // residuals of the wanted pairs
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(th[a]) < std::abs(th[b]); });
+        const cd hlast = ks.done ? cd(0.0) : Hh[ne + (size_t)(ne - 1) * ldH];
+        for (int i = 0; i < ne; ++i) run.tnorm = std::max(run.tnorm, std::abs(th[i]));
+        if (ne < want) return fail(c, OVL_ENOCONV, "Krylov space smaller than the wanted eigenspace");
         double worst = 0.0;
-        for (int j = 0; j < want; ++j) {
-            applyA(X + (size_t)j * n, t0);
-            const double2 th = make_double2(run.theta[j].real(), run.theta[j].imag());
-            k_resid<<<grid_n(n), 256, 0, st>>>(t0, X + (size_t)j * n, th, c->ks, c->partials, c->counter, n);
-            double2 rv;
-            OVL_CUDA_TRY(c, cudaMemcpyAsync(&rv, &c->ks->red[0], sizeof(double2), cudaMemcpyDeviceToHost, st));
+        for (int i = 0; i < want; ++i)
+            worst = std::max(worst, std::abs(hlast) * std::abs(Z[(size_t)(ne - 1) * ne + ord[i]]));
+        run.tcut = std::abs(th[ord[want - 1]]);
+        if (worst <= ttol * run.tnorm || ks.done) {
+            // ---- Rayleigh-Ritz with A on the span of the converged Ritz vectors of T: the want
+            // smallest and those of the next keep that have converged too.  A T eigenvalue lambda^2
+            // is shared by A's lambda and -lambda (and nearly so by close pairs); a span that holds
+            // one of them without the other is not A-invariant, so partners beyond the want-th are
+            // taken along once they converge.
+            std::vector<int> sel;
+            for (int i = 0; i < std::min(want + keep, ne); ++i)
+                if (i < want || ks.done ||
+                    std::abs(hlast) * std::abs(Z[(size_t)(ne - 1) * ne + ord[i]]) <= ttol * run.tnorm)
+                    sel.push_back(ord[i]);
+            const int wx = (int)sel.size();
+            std::vector<cd> Qw((size_t)ne * wx);
+            for (int i = 0; i < wx; ++i)
+                for (int r = 0; r < ne; ++r) Qw[(size_t)i * ne + r] = Z[(size_t)r * ne + sel[i]];
+            if (!host_orthonormalise(Qw, ne, wx)) return fail(c, OVL_ENOCONV, "Ritz vectors are dependent");
+            double2* X = w.W;  // wx orthonormal vectors spanning the converged T eigenspace
+            int r = rotate(c, w, w.V, ne, Qw, ne, wx, X);
+            if (r) return r;
+            double2* HAd = w.Hd;  // wx x wx, column-major
+            for (int i = 0; i < wx; ++i) {
+                applyA(X + (size_t)i * n, w.t0);
+                ovl::launch_multidot(X, n, wx, w.t0, HAd + (size_t)i * wx, 0, w.part, n, st);
+            }
+            std::vector<cd> HA((size_t)wx * wx);
+            OVL_CUDA_TRY(c, cudaMemcpyAsync(HA.data(), HAd, sizeof(double2) * wx * wx, cudaMemcpyDeviceToHost, st));
             OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
-            run.resid[j] = std::sqrt(rv.x);
-            worst = std::max(worst, run.resid[j]);
+            std::vector<cd> Br((size_t)wx * wx), lam, Zs;
+            for (int i = 0; i < wx; ++i)
+                for (int jj = 0; jj < wx; ++jj) Br[(size_t)i * wx + jj] = HA[i + (size_t)jj * wx];
+            if (ovl::host_eig(wx, Br, lam, Zs) != 0) return fail(c, OVL_ENOCONV, "Rayleigh-Ritz eigensolver failed");
+            // the want A pairs of smallest |lambda|
+            std::vector<int> oa(wx);
+            std::iota(oa.begin(), oa.end(), 0);
+            std::sort(oa.begin(), oa.end(), [&](int a, int b) { return std::abs(lam[a]) < std::abs(lam[b]); });
+            std::vector<cd> Zc((size_t)want * wx);
+            for (int i = 0; i < want; ++i)
+                for (int l = 0; l < wx; ++l) Zc[(size_t)i * wx + l] = Zs[(size_t)l * wx + oa[i]];
+            r = rotate(c, w, X, wx, Zc, wx, want, out);
+            if (r) return r;
+            run.theta.assign(want, 0.0);
+            run.resid.assign(want, 0.0);
+            double wr = 0.0;
+            for (int i = 0; i < want; ++i) {
+                run.theta[i] = lam[oa[i]];
+                applyA(out + (size_t)i * n, w.t0);
+                const double2 thd = make_double2(lam[oa[i]].real(), lam[oa[i]].imag());
+                k_resid<<<grid_n(n), 256, 0, st>>>(w.t0, out + (size_t)i * n, thd, w.ks, w.part, c->counter, n);
+                double2 rv;
+                OVL_CUDA_TRY(c, cudaMemcpyAsync(&rv, &w.ks->red[0], sizeof(double2), cudaMemcpyDeviceToHost, st));
+                OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
+                run.resid[i] = std::sqrt(rv.x);
+                wr = std::max(wr, run.resid[i]);
+            }
+            if (wr <= tol * std::sqrt(run.tnorm)) return OVL_OK;
+            if (ks.done) return fail(c, OVL_ENOCONV, "invariant Krylov space without accurate eigenpairs");
+            // not yet accurate for A: tighten the criterion on T and go on from the same basis
+            ttol = std::max(ttol * 0.1, 1e-14);
         }
-        // next filter: damp everything above the largest Ritz value of A^2 in the block
-        double amax = 0.0;
-        for (int j = 0; j < nb; ++j) amax = std::max(amax, std::norm(run.theta[j]));
-        acut = std::min(amax, bup / 4.0);
-        run.acut = acut;
-        if (worst <= tol * std::sqrt(sig2)) return OVL_OK;
+        // ---- thick restart: the want + keep smallest Ritz vectors and the last basis vector
+        const int kk2 = std::min(want + keep, ne - 1);
+        std::vector<cd> Q((size_t)ne * kk2);
+        for (int i = 0; i < kk2; ++i)
+            for (int r = 0; r < ne; ++r) Q[(size_t)i * ne + r] = Z[(size_t)r * ne + ord[i]];
+        if (!host_orthonormalise(Q, ne, kk2)) return fail(c, OVL_ENOCONV, "Ritz vectors are dependent");
+        int r = rotate(c, w, w.V, ne, Q, ne, kk2, w.W);
+        if (r) return r;
+        OVL_CUDA_TRY(c, cudaMemcpyAsync(w.V, w.W, sizeof(double2) * n * kk2, cudaMemcpyDeviceToDevice, st));
+        OVL_CUDA_TRY(c, cudaMemcpyAsync(w.V + (size_t)kk2 * n, w.V + (size_t)ne * n, sizeof(double2) * n,
+                                        cudaMemcpyDeviceToDevice, st));
+        // H <- [Q^dag H Q ; h e_ne^T Q]
+        std::vector<cd> HQ((size_t)ne * kk2, 0.0);
+        for (int i = 0; i < kk2; ++i)
+            for (int l = 0; l < ne; ++l) {
+                const cd q = Q[(size_t)i * ne + l];
+                if (q == cd(0.0)) continue;
+                for (int rr = 0; rr < ne; ++rr) HQ[(size_t)i * ne + rr] += Hsq[(size_t)rr * ne + l] * q;
+            }
+        std::fill(Hh.begin(), Hh.end(), cd(0.0));
+        for (int i = 0; i < kk2; ++i) {
+            for (int l = 0; l < kk2; ++l) {
+                cd sdot = 0.0;
+                for (int rr = 0; rr < ne; ++rr) sdot += std::conj(Q[(size_t)l * ne + rr]) * HQ[(size_t)i * ne + rr];
+                Hh[l + (size_t)i * ldH] = sdot;
+            }
+            Hh[kk2 + (size_t)i * ldH] = hlast * Q[(size_t)i * ne + (ne - 1)];
+        }
+        kk = kk2;
     }
     return fail(c, OVL_ENOCONV, "deflation eigensolver did not converge");
 }
 
 }  // namespace
 
-extern "C" int ovl_deflation_eigs(ovl_ctx* c, double mu, double kappa, int m, int nextra, double tol, int degree,
+extern "C" int ovl_deflation_eigs(ovl_ctx* c, double mu, double kappa, int m, int nextra, double tol, int nkrylov,
                                   int maxit, ovl_eiginfo* info) {
-    if (!c || m < 1 || nextra < 0 || m + nextra > 512 || degree < 1 || maxit < 1 || !(tol > 0))
+    if (!c || m < 1 || nextra < 0 || m + nextra > 512 || nkrylov < 0 || maxit < 1 || !(tol > 0))
         return fail(c, OVL_EINVAL, "bad argument");
     if (!c->have_gauge) return fail(c, OVL_ESTATE, "gauge field not set");
-    const int want = m + nextra;
-    const int nb = want + std::max(8, want / 2);
-    int r = ensure_solve(c, std::max(c->kcap, 2 * nb + 2));
-    if (r) return r;
-    if (c->inner_elems < (size_t)2 * nb * nb) return fail(c, OVL_ENOMEM, "workspace too small");
     const size_t n = c->n;
-    double2 *X = nullptr, *Y = nullptr, *T = nullptr, *XL = nullptr;
+    const int want = m + nextra;
+    if ((size_t)want > n) return fail(c, OVL_EINVAL, "more eigenpairs than the dimension");
+    // default basis: wide enough that the restart buffer spans well past the wanted cluster (the
+    // small eigenvalues of A^2 crowd at the bottom of its spectrum on larger lattices)
+    int nk = nkrylov > 0 ? nkrylov : std::min(512, std::max(3 * want + 40, 10 * want));
+    nk = (int)std::min<size_t>((size_t)std::max(nk, want + 8), n);
+    // device memory: basis, rotation target, two output blocks (at most 64 GiB, else a smaller basis)
+    auto bytes_for = [&](int k) { return sizeof(double2) * n * ((size_t)2 * k + 2 * want + 2); };
+    while (nk > want + 8 && bytes_for(nk) > ((size_t)64 << 30)) --nk;
+    const int keep = std::max(8, (nk - want) / 3);
+    int r = ensure_base(c);
+    if (r) return r;
+    const int mdb = ovl::multidot_blocks(n);
+    const size_t part_bytes = std::max<size_t>((size_t)mdb * (nk + 2) * sizeof(double2), (size_t)1 << 16);
+    ArnWork w = {};
+    double2 *XR = nullptr, *XL = nullptr;
+    void* ptrs[11] = {};
     auto cleanup = [&]() {
-        if (X) cudaFree(X);
-        if (Y) cudaFree(Y);
-        if (T) cudaFree(T);
-        if (XL) cudaFree(XL);
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
     };
-    if (cudaMalloc(&X, sizeof(double2) * n * nb) != cudaSuccess || cudaMalloc(&Y, sizeof(double2) * n * nb) != cudaSuccess ||
-        cudaMalloc(&T, sizeof(double2) * n * 3) != cudaSuccess || cudaMalloc(&XL, sizeof(double2) * n * nb) != cudaSuccess) {
-        cleanup();
-        return fail(c, OVL_ENOMEM, "eigensolver workspace");
-    }
+    const size_t sizes[11] = {sizeof(double2) * n * (nk + 1), sizeof(double2) * n * nk, sizeof(double2) * n,
+                              sizeof(double2) * (size_t)(nk + 1) * nk, sizeof(double2) * (nk + 2),
+                              sizeof(double2) * (nk + 2), sizeof(double2) * (size_t)nk * nk, part_bytes,
+                              sizeof(KState), sizeof(double2) * n * want, sizeof(double2) * n * want};
+    for (int i = 0; i < 11; ++i)
+        if (cudaMalloc(&ptrs[i], sizes[i]) != cudaSuccess) {
+            ptrs[i] = nullptr;
+            cleanup();
+            return fail(c, OVL_ENOMEM, "eigensolver workspace");
+        }
+    w.V = (double2*)ptrs[0], w.W = (double2*)ptrs[1], w.t0 = (double2*)ptrs[2], w.Hd = (double2*)ptrs[3];
+    w.h1 = (double2*)ptrs[4], w.h2 = (double2*)ptrs[5], w.Qd = (double2*)ptrs[6], w.part = (double*)ptrs[7];
+    w.ks = (KState*)ptrs[8];
+    XR = (double2*)ptrs[9], XL = (double2*)ptrs[10];
     EigRun right, left;
-    r = subspace_iteration(c, mu, kappa, 0, want, nb, tol, degree, maxit, X, Y, T, right);
-    if (!r) r = subspace_iteration(c, mu, kappa, 1, want, nb, tol, degree, maxit, XL, Y, T, left);
+    r = krylov_schur(c, mu, kappa, 0, want, nk, keep, tol, maxit, w, XR, right);
+    if (!r) r = krylov_schur(c, mu, kappa, 1, want, nk, keep, tol, maxit, w, XL, left);
+    auto fill_info = [&](int mm, const EigRun& e, double wr) {
+        if (!info) return;
+        info->m = mm;
+        info->iterations = right.cycles + left.cycles;
+        info->matvecs = right.matvecs + left.matvecs;
+        info->max_residual = wr;
+        info->lambda_cut = std::sqrt(e.tcut);
+    };
     if (r) {
+        // progress of the side that stopped: cycles, matvecs, the last residual check
+        const EigRun& e = left.cycles ? left : right;
+        double wr = 0.0;
+        for (double x : e.resid) wr = std::max(wr, x);
+        fill_info(0, e, wr);
         cleanup();
         return r;
     }
-    // select the m right pairs of smallest |Re lambda| among the converged ones, pair with left
+    // select the m right pairs of smallest |Re lambda| among the computed ones, pair with left
     std::vector<int> ord(want);
     std::iota(ord.begin(), ord.end(), 0);
     std::sort(ord.begin(), ord.end(),
               [&](int a, int b) { return std::fabs(right.theta[a].real()) < std::fabs(right.theta[b].real()); });
     std::vector<double> lam(2 * m);
-    double2* Rsel = Y;  // reuse: m selected right vectors
-    double2* Lsel = T;  // needs m vectors: reallocate if 3 < m
-    if (m > 3) {
-        cudaFree(T);
-        T = nullptr;
-        if (cudaMalloc(&T, sizeof(double2) * n * m) != cudaSuccess) {
-            cleanup();
-            return fail(c, OVL_ENOMEM, "eigensolver workspace");
-        }
-        Lsel = T;
-    }
+    double2* Rsel = w.V;  // the basis is free now: m selected right vectors, then m left ones
+    double2* Lsel = w.W;
     double worst_pair = 0.0;
     for (int q = 0; q < m; ++q) {
         const int j = ord[q];
@@ -285,25 +393,20 @@ extern "C" int ovl_deflation_eigs(ovl_ctx* c, double mu, double kappa, int m, in
         worst_pair = std::max(worst_pair, bd / std::max(std::abs(l), 1e-300));
         lam[2 * q] = l.real();
         lam[2 * q + 1] = l.imag();
-        cudaMemcpyAsync(Rsel + (size_t)q * n, X + (size_t)j * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(Rsel + (size_t)q * n, XR + (size_t)j * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(Lsel + (size_t)q * n, XL + (size_t)best * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice,
                         c->st);
     }
     if (worst_pair > 1e-6) {
+        fill_info(0, right, 0.0);
         cleanup();
         return fail(c, OVL_ENOCONV, "left and right eigenvalues do not pair up");
     }
     r = install_deflation(c, mu, kappa, m, lam.data(), Rsel, Lsel);
     cudaStreamSynchronize(c->st);
-    if (info) {
-        info->m = m;
-        info->iterations = right.iterations + left.iterations;
-        info->matvecs = right.matvecs + left.matvecs;
-        double wr = 0.0;
-        for (int q = 0; q < m; ++q) wr = std::max(wr, std::max(right.resid[ord[q]], 0.0));
-        info->max_residual = wr;
-        info->lambda_cut = std::sqrt(right.acut);
-    }
+    double wr = 0.0;
+    for (int q = 0; q < m; ++q) wr = std::max(wr, right.resid[ord[q]]);
+    fill_info(r ? 0 : m, right, wr);
     cleanup();
     return r;
 }

@@ -16,19 +16,27 @@ namespace ovl {
 using cd = std::complex<double>;
 
 static inline double cabs1(cd z) { return std::fabs(z.real()) + std::fabs(z.imag()); }
+// products without the IEEE special-value handling of std::complex's operator* (the inputs are finite)
+static inline cd cm(cd a, cd b) {
+    return cd(a.real() * b.real() - a.imag() * b.imag(), a.real() * b.imag() + a.imag() * b.real());
+}
+static inline cd cmc(cd a, cd b) {  // conj(a) b
+    return cd(a.real() * b.real() + a.imag() * b.imag(), a.real() * b.imag() - a.imag() * b.real());
+}
 
 // A: n x n row-major, overwritten.  w: eigenvalues.  X: right eigenvectors as
 // columns, row-major n x n.  Returns 0, or -1 if the QR iteration did not converge.
+// The accumulated unitary Z is kept column-major so that its column rotations are contiguous.
 int host_eig(int n, std::vector<cd>& A, std::vector<cd>& w, std::vector<cd>& X) {
     auto a = [&](int i, int j) -> cd& { return A[(size_t)i * n + j]; };
     std::vector<cd> Z((size_t)n * n, 0.0);
-    auto z = [&](int i, int j) -> cd& { return Z[(size_t)i * n + j]; };
+    auto z = [&](int i, int j) -> cd& { return Z[(size_t)j * n + i]; };
     for (int i = 0; i < n; ++i) z(i, i) = 1.0;
     w.assign(n, 0.0);
     X.assign((size_t)n * n, 0.0);
     if (n == 0) return 0;
     // 1. Hessenberg reduction
-    std::vector<cd> v(n);
+    std::vector<cd> v(n), sv(n);
     for (int k = 0; k < n - 2; ++k) {
         double alpha = 0.0;
         for (int i = k + 1; i < n; ++i) alpha += std::norm(a(i, k));
@@ -42,24 +50,38 @@ int host_eig(int n, std::vector<cd>& A, std::vector<cd>& w, std::vector<cd>& X) 
         double vn = 0.0;
         for (int i = k + 1; i < n; ++i) vn += std::norm(v[i]);
         if (vn == 0.0) continue;
-        // A <- (I - 2 v v^dag / vn) A (I - 2 v v^dag / vn)
-        for (int j = 0; j < n; ++j) {
-            cd s = 0.0;
-            for (int i = k + 1; i < n; ++i) s += std::conj(v[i]) * a(i, j);
-            s *= 2.0 / vn;
-            for (int i = k + 1; i < n; ++i) a(i, j) -= v[i] * s;
+        const double f = 2.0 / vn;
+        // A <- (I - f v v^dag) A: s_j = sum_i conj(v_i) a(i, j), accumulated row by row
+        for (int j = 0; j < n; ++j) sv[j] = 0.0;
+        for (int i = k + 1; i < n; ++i) {
+            const cd vi = v[i];
+            const cd* ai = &A[(size_t)i * n];
+            for (int j = 0; j < n; ++j) sv[j] += cmc(vi, ai[j]);
         }
-        for (int i = 0; i < n; ++i) {
-            cd s = 0.0;
-            for (int j = k + 1; j < n; ++j) s += a(i, j) * v[j];
-            s *= 2.0 / vn;
-            for (int j = k + 1; j < n; ++j) a(i, j) -= s * std::conj(v[j]);
+        for (int i = k + 1; i < n; ++i) {
+            const cd vi = f * v[i];
+            cd* ai = &A[(size_t)i * n];
+            for (int j = 0; j < n; ++j) ai[j] -= cm(vi, sv[j]);
         }
+        // A <- A (I - f v v^dag)
         for (int i = 0; i < n; ++i) {
-            cd s = 0.0;
-            for (int j = k + 1; j < n; ++j) s += z(i, j) * v[j];
-            s *= 2.0 / vn;
-            for (int j = k + 1; j < n; ++j) z(i, j) -= s * std::conj(v[j]);
+            cd* ai = &A[(size_t)i * n];
+            cd t = 0.0;
+            for (int j = k + 1; j < n; ++j) t += cm(ai[j], v[j]);
+            t *= f;
+            for (int j = k + 1; j < n; ++j) ai[j] -= cm(t, std::conj(v[j]));
+        }
+        // Z <- Z (I - f v v^dag), column by column
+        for (int i = 0; i < n; ++i) sv[i] = 0.0;
+        for (int j = k + 1; j < n; ++j) {
+            const cd vj = v[j];
+            const cd* zj = &Z[(size_t)j * n];
+            for (int i = 0; i < n; ++i) sv[i] += cm(zj[i], vj);
+        }
+        for (int j = k + 1; j < n; ++j) {
+            const cd cj = f * std::conj(v[j]);
+            cd* zj = &Z[(size_t)j * n];
+            for (int i = 0; i < n; ++i) zj[i] -= cm(sv[i], cj);
         }
         for (int i = k + 2; i < n; ++i) a(i, k) = 0.0;
     }
@@ -121,10 +143,13 @@ int host_eig(int n, std::vector<cd>& A, std::vector<cd>& w, std::vector<cd>& X) 
             gcr[k - lo] = c;
             gs[k - lo] = sn;
             // rows k, k+1: [c, s; -conj(s), c]
+            cd* ak = &A[(size_t)k * n];
+            cd* ak1 = &A[(size_t)(k + 1) * n];
+            const cd snc = std::conj(sn);
             for (int j = k; j < n; ++j) {
-                const cd t1 = a(k, j), t2 = a(k + 1, j);
-                a(k, j) = c * t1 + sn * t2;
-                a(k + 1, j) = -std::conj(sn) * t1 + c * t2;
+                const cd t1 = ak[j], t2 = ak1[j];
+                ak[j] = c * t1 + cm(sn, t2);
+                ak1[j] = c * t2 - cm(snc, t1);
             }
         }
         for (int k = lo; k < hi; ++k) {
@@ -132,15 +157,18 @@ int host_eig(int n, std::vector<cd>& A, std::vector<cd>& w, std::vector<cd>& X) 
             const cd sn = gs[k - lo];
             // columns k, k+1 from the right with the conjugate transpose
             const int rmax = std::min(hi, k + 2);
+            const cd snc = std::conj(sn);
             for (int i = 0; i <= rmax; ++i) {
                 const cd t1 = a(i, k), t2 = a(i, k + 1);
-                a(i, k) = c * t1 + std::conj(sn) * t2;
-                a(i, k + 1) = -sn * t1 + c * t2;
+                a(i, k) = c * t1 + cm(snc, t2);
+                a(i, k + 1) = c * t2 - cm(sn, t1);
             }
+            cd* zk = &Z[(size_t)k * n];
+            cd* zk1 = &Z[(size_t)(k + 1) * n];
             for (int i = 0; i < n; ++i) {
-                const cd t1 = z(i, k), t2 = z(i, k + 1);
-                z(i, k) = c * t1 + std::conj(sn) * t2;
-                z(i, k + 1) = -sn * t1 + c * t2;
+                const cd t1 = zk[i], t2 = zk1[i];
+                zk[i] = c * t1 + cm(snc, t2);
+                zk1[i] = c * t2 - cm(sn, t1);
             }
         }
         for (int k = lo; k <= hi; ++k) a(k, k) += mu;
@@ -154,19 +182,20 @@ int host_eig(int n, std::vector<cd>& A, std::vector<cd>& w, std::vector<cd>& X) 
         y[k] = 1.0;
         for (int i = k - 1; i >= 0; --i) {
             cd s = 0.0;
-            for (int j = i + 1; j <= k; ++j) s += a(i, j) * y[j];
+            const cd* ai = &A[(size_t)i * n];
+            for (int j = i + 1; j <= k; ++j) s += cm(ai[j], y[j]);
             cd d = a(i, i) - w[k];
             if (std::abs(d) < small) d = small;
             y[i] = -s / d;
         }
-        double nrm = 0.0;
         std::vector<cd> col(n, 0.0);
-        for (int i = 0; i < n; ++i) {
-            cd s = 0.0;
-            for (int j = 0; j <= k; ++j) s += z(i, j) * y[j];
-            col[i] = s;
-            nrm += std::norm(s);
+        for (int j = 0; j <= k; ++j) {
+            const cd yj = y[j];
+            const cd* zj = &Z[(size_t)j * n];
+            for (int i = 0; i < n; ++i) col[i] += cm(zj[i], yj);
         }
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) nrm += std::norm(col[i]);
         nrm = std::sqrt(nrm);
         for (int i = 0; i < n; ++i) X[(size_t)i * n + k] = col[i] / nrm;
     }

@@ -267,11 +267,14 @@ class Context:
             _ptr(R), _ptr(L), flags))
 
     def deflation_eigs(self, mu: float, kappa: float, m: int, nextra: int = 10, tol: float = 1e-10,
-                       degree: int = 80, maxit: int = 60):
-        """Compute and install the m critical eigenpairs on the GPU; returns info dict."""
+                       nkrylov: int = 0, maxit: int = 400):
+        """Compute and install the m critical eigenpairs on the GPU (thick-restart Arnoldi on A^2,
+        basis of nkrylov vectors, 0 = automatic, at most maxit restart cycles); returns info dict."""
         info = EigInfo()
-        self._check(self._lib.ovl_deflation_eigs(self._h, mu, kappa, m, nextra, tol, degree, maxit,
-                                                  ctypes.byref(info)))
+        r = self._lib.ovl_deflation_eigs(self._h, mu, kappa, m, nextra, tol, nkrylov, maxit, ctypes.byref(info))
+        if r == ENOCONV:
+            raise OvlError(r, f"{self._lib.ovl_last_error(self._h).decode()} {info.as_dict()}")
+        self._check(r)
         return info.as_dict()
 
     def get_deflation(self, device: bool = True):
