@@ -257,7 +257,8 @@ typedef struct {
 
 /* Deflation phase on the GPU (Sec. 3 and Sec. 5, where ARPACK plays this role): compute the
  * m + nextra eigenvalues of A = gamma5 D_w(mu) nearest 0 with right and left eigenvectors
- * (thick-restart Arnoldi on A^2 with a basis of nkrylov vectors, 0 = 10 (m + nextra) within
+ * (thick-restart Arnoldi on a Chebyshev polynomial of A^2 that amplifies its smallest
+ * eigenvalues, with a basis of nkrylov vectors, 0 = 10 (m + nextra) within
  * [3 (m + nextra) + 40, 512], at
  * most maxit restart cycles, then Rayleigh-Ritz with A and with A^dag; residual
  * |A r - lambda r| <= tol |A|), keep the m of smallest |Re lambda|, and install them as by

@@ -3,21 +3,24 @@
 // per gauge field and mu for all sources (Sec. 3, last paragraph; Sec. 5 uses
 // ARPACK on the CPU for this step).
 //
-// Method: thick-restart Arnoldi (Krylov-Schur form) on T = A^2.  The eigenvalues
-// of A nearest 0 are those of T of smallest modulus.  For gamma5 D_w(mu) at
-// moderate mu the spectrum of A lies close to the real axis, so T's lies in a
-// thin region along the positive real axis, and the wanted ones sit at its end
-// near 0, where Krylov methods converge.  (A Chebyshev filter on a real interval,
-// the first version of this solver, also amplifies the eigenvalues of T off the
-// real axis at the far end, Im(lambda^2) = 2 Re(lambda) Im(lambda), and stalled
-// on 16^3 x 8.)  Each cycle extends an orthonormal basis V to nkrylov vectors
-// (classical Gram-Schmidt twice, the library's Arnoldi kernels), computes the
-// Ritz pairs of the projected matrix H on the host (host_eig.cpp) and restarts
-// from the orthonormalised Ritz vectors of the want + keep smallest |theta| and
-// the last basis vector: with Q those Ritz vectors' coordinates,
-// T (V Q) = (V Q)(Q^dag H Q) + h v_next e^T Q keeps the Arnoldi relation with a
-// full last row.  Once the want smallest pairs of T have residuals
-// <= tol |T|, a Rayleigh-Ritz step with A itself on their span gives the
+// Method: thick-restart Arnoldi (Krylov-Schur form) on a Chebyshev polynomial
+// of T = A^2.  The eigenvalues of A nearest 0 are those of T of smallest
+// modulus.  For gamma5 D_w(mu) at moderate mu the spectrum of A lies close to
+// the real axis, so T's lies in a thin region along the positive real axis,
+// and the wanted ones crowd at its bottom end: on 16^3 x 8 the 40 smallest
+// eigenvalues of T lie within 15 % of each other against a spread of 5, which
+// makes Arnoldi on T itself converge slowly.  One Arnoldi cycle on T locates
+// (from above) the end acut of the wanted cluster; then P = T_d((c - T) / e),
+// the Chebyshev polynomial of degree d on [acut, |A|^2], maps the eigenvalues
+// below acut to the largest of P in modulus and spreads them out, and those
+// above acut into [-1, 1].  Each cycle extends an orthonormal basis V to
+// nkrylov vectors (classical Gram-Schmidt twice, the library's Arnoldi
+// kernels), computes the Ritz pairs of the projected matrix H on the host
+// (host_eig.cpp) and restarts from the orthonormalised Ritz vectors of the
+// want + keep largest |theta(P)| and the last basis vector: with Q those Ritz
+// vectors' coordinates, P (V Q) = (V Q)(Q^dag H Q) + h v_next e^T Q keeps the
+// Arnoldi relation with a full last row.  Once the wanted pairs have
+// converged, a Rayleigh-Ritz step with A itself on their span gives the
 // eigenpairs of A (right vectors from A, left ones from A^dag = gamma5
 // D_w(-mu)).  Pairs are matched by lambda_left = conj(lambda_right), the m of
 // smallest |Re lambda| kept and bi-orthonormalised (L <- L (L^dag R)^-H) when
@@ -69,6 +72,21 @@ __global__ void k_normalize(double2* y, const double2* h, size_t n) {
     }
 }
 
+// Chebyshev step of the filter: yn = s1 (c y - u) - s0 yp, with u = T y already in yn
+__global__ void k_cheb_step(const double2* __restrict__ y, const double2* __restrict__ yp, double2* yn, double c,
+                            double s1, double s0, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const double2 yy = y[e], u = yn[e];
+        double2 r = make_double2(s1 * (c * yy.x - u.x), s1 * (c * yy.y - u.y));
+        if (s0 != 0.0) {
+            const double2 pp = yp[e];
+            r.x -= s0 * pp.x;
+            r.y -= s0 * pp.y;
+        }
+        yn[e] = r;
+    }
+}
+
 // |t - theta x|^2 -> ks->red[0].x
 __global__ void __launch_bounds__(256) k_resid(const double2* __restrict__ t, const double2* __restrict__ x,
                                                double2 theta, KState* ks, double* partials, unsigned int* counter,
@@ -94,8 +112,8 @@ struct EigRun {
     std::vector<double> resid;  // |A x - theta x| of the unit vectors
     int cycles = 0;
     long long matvecs = 0;
-    double tnorm = 0;           // largest |theta(T)| seen (scale of T)
-    double tcut = 0;            // |theta(T)| of the want-th pair
+    double anorm = 0;           // estimate of |A| (power iteration on A^dag A)
+    double tcut = 0;            // |lambda|^2 of the want-th pair
 };
 
 // Columns of Q (ne x kk, column-major) made orthonormal: modified Gram-Schmidt, twice.
@@ -123,6 +141,7 @@ struct ArnWork {
     double2* V;      // (nk + 1) basis vectors
     double2* W;      // nk vectors: rotated basis, then the output eigenvectors
     double2* t0;     // one vector
+    double2* cb[3];  // Chebyshev recurrence
     double2* Hd;     // (nk + 1) x nk, column-major
     double2* h1;     // nk + 2
     double2* h2;     // nk + 2
@@ -151,6 +170,16 @@ int rotate(ovl_ctx* c, const ArnWork& w, const double2* V, int nv, const std::ve
 
 // One side (dagger = 0: A, 1: A^dag): the want eigenpairs of A of smallest |lambda| with
 // |A x - lambda x| <= tol |A|; unit eigenvectors in out (want x n), eigenvalues in run.theta.
+//
+// 1. |A|^2 from a power iteration on A^dag A (upper end of the spectrum of T = A^2).
+// 2. One Arnoldi cycle on T: its smallest Ritz values locate (from above) the end of the wanted
+//    cluster, acut = |theta| of the (want + keep)-th.
+// 3. Thick-restart Arnoldi on P = T_d((c - T) / e), the Chebyshev polynomial of degree d on
+//    [acut, |A|^2]: the eigenvalues of T below acut become the largest of P in modulus, spread
+//    out (the crowded bottom of T's spectrum is what slows Arnoldi on T itself); those above
+//    acut map into [-1, 1].  The want + keep Ritz vectors of largest |theta(P)| are kept.
+// 4. Rayleigh-Ritz with A on the converged ones; if a wanted |lambda|^2 lies above acut the
+//    filter interval is widened and step 3 continues.
 int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int nk, int keep, double tol,
                  int maxcycles, const ArnWork& w, double2* out, EigRun& run) {
     const size_t n = c->n;
@@ -161,9 +190,69 @@ int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int 
         ovl::launch_dslash(c->U64, 0, x, y, m_eff, kappa, 1, c->g, st, w.ks);
         ++run.matvecs;
     };
+    auto applyAdag = [&](const double2* x, double2* y) {
+        ovl::launch_dslash(c->U64, 0, x, y, -m_eff, kappa, 1, c->g, st, w.ks);
+        ++run.matvecs;
+    };
     auto reset_state = [&]() { return cudaMemsetAsync(w.ks, 0, sizeof(KState), st); };
-    // random unit start vector
+    // filter state: mode 0 = T, 1 = P
+    int mode = 0, deg = 1;
+    double cc = 0.0, ee = 1.0, acut = 0.0;
+    auto applyT = [&](const double2* x, double2* y) {
+        applyA(x, w.t0);
+        applyA(w.t0, y);
+    };
+    auto applyOp = [&](const double2* x, double2* y) -> int {
+        if (mode == 0) {
+            applyT(x, y);
+            return OVL_OK;
+        }
+        // y = T_deg((cc - T)/ee) x by the three-term recurrence in the scratch vectors cb[]
+        const double2* yp = x;
+        double2* yc = w.cb[0];
+        applyT(x, yc);
+        k_cheb_step<<<grid_n(n), 256, 0, st>>>(x, nullptr, yc, cc, 1.0 / ee, 0.0, n);
+        int free_i = 1;
+        for (int k = 2; k <= deg; ++k) {
+            double2* yn = w.cb[free_i];
+            applyT(yc, yn);
+            k_cheb_step<<<grid_n(n), 256, 0, st>>>(yc, yp, yn, cc, 2.0 / ee, 1.0, n);
+            // rotate: the buffer that held yp (if a scratch one) becomes free
+            int next_free = 0;
+            for (int q = 0; q < 3; ++q)
+                if (w.cb[q] != yc && w.cb[q] != yn) next_free = q;
+            yp = yc;
+            yc = yn;
+            free_i = next_free;
+        }
+        OVL_CUDA_TRY(c, cudaMemcpyAsync(y, yc, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+        return OVL_OK;
+    };
+    // ---- 1. |A|^2 by power iteration on A^dag A
     OVL_CUDA_TRY(c, reset_state());
+    k_rand_fill<<<grid_n(n), 256, 0, st>>>(w.t0, n, 0x5eedull + dagger);
+    double sig2 = 0.0;
+    {
+        double2* x = w.cb[0];
+        double2* ax = w.cb[1];
+        double2* aax = w.cb[2];
+        OVL_CUDA_TRY(c, cudaMemcpyAsync(x, w.t0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+        for (int it = 0; it < 30; ++it) {
+            ovl::launch_multidot(x, n, 1, x, w.h1, 0, w.part, n, st);
+            k_normalize<<<grid_n(n), 256, 0, st>>>(x, w.h1, n);
+            applyA(x, ax);
+            applyAdag(ax, aax);
+            ovl::launch_multidot(x, n, 1, aax, w.h1, 0, w.part, n, st);
+            double2 hv;
+            OVL_CUDA_TRY(c, cudaMemcpyAsync(&hv, w.h1, sizeof(double2), cudaMemcpyDeviceToHost, st));
+            OVL_CUDA_TRY(c, cudaStreamSynchronize(st));
+            sig2 = std::max(sig2, hv.x);
+            std::swap(x, aax);
+        }
+    }
+    const double bup = 1.15 * sig2;
+    run.anorm = std::sqrt(bup);
+    // random unit start vector
     k_rand_fill<<<grid_n(n), 256, 0, st>>>(w.V, n, 0x1234ull + 77 * dagger);
     ovl::launch_multidot(w.V, n, 1, w.V, w.h1, 0, w.part, n, st);
     k_normalize<<<grid_n(n), 256, 0, st>>>(w.V, w.h1, n);
@@ -171,15 +260,25 @@ int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int 
     std::vector<cd> Ar, th, Z;
     int kk = 0;
     double ttol = tol;
+    auto set_filter = [&](double a) {
+        acut = std::min(a, 0.5 * bup);
+        cc = 0.5 * (bup + acut);
+        ee = 0.5 * (bup - acut);
+        // about 8 e-folds of amplification across [0, acut]
+        const double rate = std::sqrt(2.0 * 2.0 * acut / (bup - acut));
+        deg = (int)std::min(400.0, std::max(16.0, std::ceil(8.0 / std::max(rate, 1e-12))));
+        mode = 1;
+    };
     for (int cyc = 0; cyc < maxcycles; ++cyc) {
         run.cycles = cyc + 1;
-        // ---- extend the basis from kk to nk vectors (T v_j = A (A v_j), CGS2 against V_0..V_j)
+        // ---- extend the basis from kk to nk vectors (CGS2 against V_0..V_j)
         OVL_CUDA_TRY(c, reset_state());
         for (int j = kk; j < nk; ++j) {
             const double2* vj = w.V + (size_t)j * n;
             double2* x = w.V + (size_t)(j + 1) * n;
-            applyA(vj, w.t0);
-            applyA(w.t0, x);
+            int r0 = 0;
+            if (mode == 0) applyT(vj, x);
+            else if ((r0 = applyOp(vj, x))) return r0;
             ovl::launch_multidot(w.V, n, j + 1, x, w.h1, 0, w.part, n, st, w.ks);
             ovl::launch_multiaxpy(w.V, n, j + 1, w.h1, x, w.part, c->counter, w.ks, 0, n, st);
             ovl::launch_multidot(w.V, n, j + 1, x, w.h2, 0, w.part, n, st, w.ks);
@@ -201,7 +300,7 @@ int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int 
         for (int j = kk; j < ne; ++j)
             for (int r2 = j + 2; r2 < ldH; ++r2) Hh[r2 + (size_t)j * ldH] = 0.0;
         OVL_CUDA_TRY(c, reset_state());
-        // ---- Ritz pairs of H (ne x ne), ordered by |theta|
+        // ---- Ritz pairs of H (ne x ne), wanted first: smallest |theta| of T, largest of P
         Ar.assign((size_t)ne * ne, 0.0);
         for (int i = 0; i < ne; ++i)
             for (int jj = 0; jj < ne; ++jj) Ar[(size_t)i * ne + jj] = Hh[i + (size_t)jj * ldH];
@@ -209,31 +308,50 @@ int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int 
         if (ovl::host_eig(ne, Ar, th, Z) != 0) return fail(c, OVL_ENOCONV, "Ritz eigensolver failed");
         std::vector<int> ord(ne);
         std::iota(ord.begin(), ord.end(), 0);
-        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(th[a]) < std::abs(th[b]); });
+        if (mode == 0)
+            std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(th[a]) < std::abs(th[b]); });
+        else
+            std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(th[a]) > std::abs(th[b]); });
         const cd hlast = ks.done ? cd(0.0) : Hh[ne + (size_t)(ne - 1) * ldH];
-        for (int i = 0; i < ne; ++i) run.tnorm = std::max(run.tnorm, std::abs(th[i]));
         if (ne < want) return fail(c, OVL_ENOCONV, "Krylov space smaller than the wanted eigenspace");
+        const int kk2 = std::min(want + keep, ne - 1);
+        if (mode == 0 && !ks.done) {
+            // ---- 2. the filter from the first cycle's smallest Ritz values, then restart from the
+            // sum of the kept Ritz vectors
+            set_filter(std::abs(th[ord[kk2]]));
+            std::vector<cd> sumv((size_t)ne, 0.0);
+            for (int i = 0; i < kk2; ++i)
+                for (int r = 0; r < ne; ++r) sumv[r] += Z[(size_t)r * ne + ord[i]];
+            if (!host_orthonormalise(sumv, ne, 1)) return fail(c, OVL_ENOCONV, "start vector");
+            int r = rotate(c, w, w.V, ne, sumv, ne, 1, w.W);
+            if (r) return r;
+            OVL_CUDA_TRY(c, cudaMemcpyAsync(w.V, w.W, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+            std::fill(Hh.begin(), Hh.end(), cd(0.0));
+            kk = 0;
+            continue;
+        }
+        // relative residual of each Ritz pair (P spans many orders of magnitude)
+        auto rres = [&](int i) {
+            const double sc = mode == 0 ? bup : std::max(std::abs(th[ord[i]]), 1e-300);
+            return std::abs(hlast) * std::abs(Z[(size_t)(ne - 1) * ne + ord[i]]) / sc;
+        };
         double worst = 0.0;
-        for (int i = 0; i < want; ++i)
-            worst = std::max(worst, std::abs(hlast) * std::abs(Z[(size_t)(ne - 1) * ne + ord[i]]));
-        run.tcut = std::abs(th[ord[want - 1]]);
-        if (worst <= ttol * run.tnorm || ks.done) {
-            // ---- Rayleigh-Ritz with A on the span of the converged Ritz vectors of T: the want
-            // smallest and those of the next keep that have converged too.  A T eigenvalue lambda^2
-            // is shared by A's lambda and -lambda (and nearly so by close pairs); a span that holds
-            // one of them without the other is not A-invariant, so partners beyond the want-th are
-            // taken along once they converge.
+        for (int i = 0; i < want; ++i) worst = std::max(worst, rres(i));
+        if (worst <= ttol || ks.done) {
+            // ---- 4. Rayleigh-Ritz with A on the span of the converged Ritz vectors: the want first
+            // and those of the next keep that have converged too.  An eigenvalue of T is shared by
+            // A's lambda and -lambda (and nearly so by close pairs); a span that holds one of them
+            // without the other is not A-invariant, so partners beyond the want-th are taken
+            // along once they converge.
             std::vector<int> sel;
             for (int i = 0; i < std::min(want + keep, ne); ++i)
-                if (i < want || ks.done ||
-                    std::abs(hlast) * std::abs(Z[(size_t)(ne - 1) * ne + ord[i]]) <= ttol * run.tnorm)
-                    sel.push_back(ord[i]);
+                if (i < want || ks.done || rres(i) <= ttol) sel.push_back(ord[i]);
             const int wx = (int)sel.size();
             std::vector<cd> Qw((size_t)ne * wx);
             for (int i = 0; i < wx; ++i)
                 for (int r = 0; r < ne; ++r) Qw[(size_t)i * ne + r] = Z[(size_t)r * ne + sel[i]];
             if (!host_orthonormalise(Qw, ne, wx)) return fail(c, OVL_ENOCONV, "Ritz vectors are dependent");
-            double2* X = w.W;  // wx orthonormal vectors spanning the converged T eigenspace
+            double2* X = w.W;  // wx orthonormal vectors spanning the converged invariant subspace
             int r = rotate(c, w, w.V, ne, Qw, ne, wx, X);
             if (r) return r;
             double2* HAd = w.Hd;  // wx x wx, column-major
@@ -271,13 +389,27 @@ int krylov_schur(ovl_ctx* c, double mu, double kappa, int dagger, int want, int 
                 run.resid[i] = std::sqrt(rv.x);
                 wr = std::max(wr, run.resid[i]);
             }
-            if (wr <= tol * std::sqrt(run.tnorm)) return OVL_OK;
+            run.tcut = std::norm(lam[oa[want - 1]]);
+            if (mode == 1 && !ks.done && run.tcut > acut) {
+                // a wanted eigenvalue lies outside the amplified region: widen the filter and
+                // start over from the current eigenvectors' sum
+                set_filter(2.0 * run.tcut);
+                std::vector<cd> ones((size_t)want, 1.0);
+                r = rotate(c, w, out, want, ones, want, 1, w.V);
+                if (r) return r;
+                ovl::launch_multidot(w.V, n, 1, w.V, w.h1, 0, w.part, n, st);
+                k_normalize<<<grid_n(n), 256, 0, st>>>(w.V, w.h1, n);
+                std::fill(Hh.begin(), Hh.end(), cd(0.0));
+                kk = 0;
+                ttol = tol;
+                continue;
+            }
+            if (wr <= tol * run.anorm) return OVL_OK;
             if (ks.done) return fail(c, OVL_ENOCONV, "invariant Krylov space without accurate eigenpairs");
-            // not yet accurate for A: tighten the criterion on T and go on from the same basis
+            // not yet accurate for A: tighten the criterion and go on from the same basis
             ttol = std::max(ttol * 0.1, 1e-14);
         }
-        // ---- thick restart: the want + keep smallest Ritz vectors and the last basis vector
-        const int kk2 = std::min(want + keep, ne - 1);
+        // ---- thick restart: the want + keep wanted-end Ritz vectors and the last basis vector
         std::vector<cd> Q((size_t)ne * kk2);
         for (int i = 0; i < kk2; ++i)
             for (int r = 0; r < ne; ++r) Q[(size_t)i * ne + r] = Z[(size_t)r * ne + ord[i]];
@@ -324,7 +456,7 @@ extern "C" int ovl_deflation_eigs(ovl_ctx* c, double mu, double kappa, int m, in
     int nk = nkrylov > 0 ? nkrylov : std::min(512, std::max(3 * want + 40, 10 * want));
     nk = (int)std::min<size_t>((size_t)std::max(nk, want + 8), n);
     // device memory: basis, rotation target, two output blocks (at most 64 GiB, else a smaller basis)
-    auto bytes_for = [&](int k) { return sizeof(double2) * n * ((size_t)2 * k + 2 * want + 2); };
+    auto bytes_for = [&](int k) { return sizeof(double2) * n * ((size_t)2 * k + 2 * want + 5); };
     while (nk > want + 8 && bytes_for(nk) > ((size_t)64 << 30)) --nk;
     const int keep = std::max(8, (nk - want) / 3);
     int r = ensure_base(c);
@@ -333,16 +465,17 @@ extern "C" int ovl_deflation_eigs(ovl_ctx* c, double mu, double kappa, int m, in
     const size_t part_bytes = std::max<size_t>((size_t)mdb * (nk + 2) * sizeof(double2), (size_t)1 << 16);
     ArnWork w = {};
     double2 *XR = nullptr, *XL = nullptr;
-    void* ptrs[11] = {};
+    void* ptrs[14] = {};
     auto cleanup = [&]() {
         for (void* p : ptrs)
             if (p) cudaFree(p);
     };
-    const size_t sizes[11] = {sizeof(double2) * n * (nk + 1), sizeof(double2) * n * nk, sizeof(double2) * n,
+    const size_t sizes[14] = {sizeof(double2) * n * (nk + 1), sizeof(double2) * n * nk, sizeof(double2) * n,
                               sizeof(double2) * (size_t)(nk + 1) * nk, sizeof(double2) * (nk + 2),
                               sizeof(double2) * (nk + 2), sizeof(double2) * (size_t)nk * nk, part_bytes,
-                              sizeof(KState), sizeof(double2) * n * want, sizeof(double2) * n * want};
-    for (int i = 0; i < 11; ++i)
+                              sizeof(KState), sizeof(double2) * n * want, sizeof(double2) * n * want,
+                              sizeof(double2) * n, sizeof(double2) * n, sizeof(double2) * n};
+    for (int i = 0; i < 14; ++i)
         if (cudaMalloc(&ptrs[i], sizes[i]) != cudaSuccess) {
             ptrs[i] = nullptr;
             cleanup();
@@ -352,6 +485,7 @@ extern "C" int ovl_deflation_eigs(ovl_ctx* c, double mu, double kappa, int m, in
     w.h1 = (double2*)ptrs[4], w.h2 = (double2*)ptrs[5], w.Qd = (double2*)ptrs[6], w.part = (double*)ptrs[7];
     w.ks = (KState*)ptrs[8];
     XR = (double2*)ptrs[9], XL = (double2*)ptrs[10];
+    for (int q = 0; q < 3; ++q) w.cb[q] = (double2*)ptrs[11 + q];
     EigRun right, left;
     r = krylov_schur(c, mu, kappa, 0, want, nk, keep, tol, maxit, w, XR, right);
     if (!r) r = krylov_schur(c, mu, kappa, 1, want, nk, keep, tol, maxit, w, XL, left);
