@@ -1,0 +1,110 @@
+"""The larger workloads at full size, through the C ABI: the 8^4 lattice at three chemical
+potentials (Arnoldi and two-sided Lanczos with 20 deflated eigenpairs from the library's
+eigensolver), 16^3 x 8 in mixed precision with 30 deflated eigenpairs, and 12 point sources on
+each of four lattices of uneven sizes with 20 deflated eigenpairs each in one batch.
+
+The dense oracle cannot reach these sizes, so the checks are those that hold at any size: the
+eigenpair relations A r = lambda r and A^dag l = conj(lambda) l at sampled sites against the
+oracle's single-site operator (Sec. 1, Eq. 1.2), two independent methods (Arnoldi, Sec. 2, and
+two-sided Lanczos, Sec. 4) agreeing, mixed precision against FP64 at a larger Krylov size, and
+sgn(A)^2 b = b (Eq. 1.4)."""
+import numpy as np
+import pytest
+
+from gpu_common import KAPPA, rel, torch_c128
+from oracle import wilson as W
+from paper_0810_4228_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ovl():
+    from paper_0810_4228_gb300 import ovl as O
+    O.load()
+    return O
+
+
+def _check_pairs_sampled(U, dims, mu, lam, R, L, qs, sites, atol):
+    """A r_q = lambda_q r_q and A^dag l_q = conj(lambda_q) l_q at the sampled sites, with A and
+    A^dag = gamma5 D_w(-mu) from the oracle's single-site evaluator."""
+    for q in qs:
+        for s in sites:
+            ar = W.wilson_site(U, dims, mu, KAPPA, R[q], s)
+            np.testing.assert_allclose(ar, lam[q] * R[q][12 * s:12 * s + 12], atol=atol)
+            al = W.wilson_site(U, dims, -mu, KAPPA, L[q], s)
+            np.testing.assert_allclose(al, np.conj(lam[q]) * L[q][12 * s:12 * s + 12], atol=atol)
+
+
+@pytest.mark.parametrize("mu", [0.1, 0.3, 0.5])
+def test_8x4_deflated_arnoldi_and_lanczos2(ovl, mu):
+    dims = (8, 8, 8, 8)
+    U = synth.gauge_field(dims, 1.0, 1001)
+    b = torch_c128(synth.gaussian_source(dims, 2001))
+    ctx = ovl.Context(dims)
+    ctx.set_gauge(torch_c128(U))
+    info = ctx.deflation_eigs(mu, KAPPA, 20)
+    assert info["m"] == 20 and info["max_residual"] < 1e-10
+    lam, R, L = ctx.get_deflation(device=False)
+    # the kept pairs are the 20 of smallest |Re lambda| among the computed ones
+    assert np.all(np.abs(lam.real) <= info["lambda_cut"] + 1e-12)
+    _check_pairs_sampled(U, dims, mu, lam, R, L, (0, 19), (0, 1234, 4095), 1e-12)
+    np.testing.assert_allclose(L.conj() @ R.T, np.eye(20), atol=1e-9)
+    y2 = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, b)[0].clone()
+    ya = ctx.sign_krylov(ovl.ARNOLDI, 1000, mu, KAPPA, b)[0].clone()
+    ym = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
+    assert rel(y2.cpu().numpy(), ya.cpu().numpy()) < 1e-9
+    assert rel(ym.cpu().numpy(), y2.cpu().numpy()) < 1e-8
+    # sgn(A)^2 b = b
+    z = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, y2)[0]
+    assert rel(z.cpu().numpy(), b.cpu().numpy()) < 1e-8
+    ctx.close()
+
+
+def test_16x3x8_mixed_30_deflated(ovl):
+    """16^3 x 8, mu = 0.3, 30 deflated eigenpairs: mixed precision within 1e-8 of the FP64
+    result at Krylov sizes 600 and 800, FP64 at k = 800 within 1e-10 of k = 1200."""
+    dims, mu = (16, 16, 16, 8), 0.3
+    U = synth.gauge_field(dims, 1.0, 1002)
+    b = torch_c128(synth.gaussian_source(dims, 2002))
+    ctx = ovl.Context(dims)
+    ctx.set_gauge(torch_c128(U))
+    info = ctx.deflation_eigs(mu, KAPPA, 30)
+    assert info["m"] == 30 and info["max_residual"] < 1e-10
+    lam, R, L = ctx.get_deflation(device=False)
+    _check_pairs_sampled(U, dims, mu, lam, R, L, (0, 29), (0, 20000, 32767), 1e-12)
+    ref = ctx.sign_krylov(ovl.LANCZOS2, 1200, mu, KAPPA, b)[0].clone()
+    y64 = ctx.sign_krylov(ovl.LANCZOS2, 800, mu, KAPPA, b)[0].clone()
+    assert rel(y64.cpu().numpy(), ref.cpu().numpy()) < 1e-10
+    for k in (600, 800):
+        ym = ctx.sign_krylov(ovl.LANCZOS2, k, mu, KAPPA, b, flags=ovl.MIXED)[0]
+        assert rel(ym.cpu().numpy(), ref.cpu().numpy()) < 1e-8, k
+    z = ctx.sign_krylov(ovl.LANCZOS2, 1200, mu, KAPPA, ref)[0]
+    assert rel(z.cpu().numpy(), b.cpu().numpy()) < 1e-9
+    ctx.close()
+
+
+def test_uneven_lattices_batch_20_deflated(ovl):
+    """12 point sources on each of 6^4, 8^4, 12^4 and 16^3 x 8 (mu = 0.2, 20 deflated eigenpairs
+    each) in one mixed-precision batch at k = 700, against single FP64 solves at k = 1000."""
+    mu = 0.2
+    dims_list = [(6, 6, 6, 6), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 8)]
+    ctxs, srcs = [], []
+    for j, d in enumerate(dims_list):
+        c = ovl.Context(d)
+        c.set_gauge(torch_c128(synth.gauge_field(d, 1.0, 3800 + j)))
+        info = c.deflation_eigs(mu, KAPPA, 20)
+        assert info["m"] == 20 and info["max_residual"] < 1e-10, (d, info)
+        ctxs.append(c)
+        srcs.append(synth.point_sources(d, site=0))
+    bt = ovl.Batch(ctxs, [12] * 4)
+    outs, infos, st = bt.solve(700, mu, KAPPA, [torch_c128(s) for s in srcs], flags=ovl.MIXED | ovl.OVERLAP)
+    assert st == 0 and len(infos) == 48
+    for j, c in enumerate(ctxs):
+        for r in (0, 5, 11):
+            y1 = c.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, torch_c128(srcs[j][r]), flags=ovl.OVERLAP)[0]
+            e = rel(outs[j][r].cpu().numpy(), y1.cpu().numpy())
+            assert e < 1e-8, (dims_list[j], r, e)
+    bt.close()
+    for c in ctxs:
+        c.close()
