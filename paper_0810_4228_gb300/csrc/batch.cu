@@ -192,6 +192,16 @@ __device__ bool seq_reduce(A (&v)[NQ], double2* part, unsigned int* cnt, int loc
     return true;
 }
 
+// Programmatic dependent launch: the batched kernels of one solve follow each other on one
+// stream and are launched with programmatic stream serialisation, so a kernel's blocks may be
+// scheduled while the previous kernel drains.  Each kernel waits here (full completion and memory
+// visibility of the previous grid) before it reads anything the previous kernel wrote, and lets
+// the next kernel be scheduled once all of its own blocks have started.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <class R>
 __device__ __forceinline__ void* vslot(const BSeq& q, int j, bool wvec) {
     if (!wvec && q.V) return q.V + (size_t)j * q.n;
@@ -203,8 +213,9 @@ template <int LF, class R, int SH>
 __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
                                                int klast, HopCoef<R> hv, HopCoef<R> hw) {
     using VT = typename BVec<R>::T;
-    const BSeq& q = S[bseq[blockIdx.x]];
+    const BSeq& q = S[bseq[blockIdx.x]];  // set-up data, not written by the solve
     KState* ks = q.ks;
+    pdl_wait_and_release();
     if (ks->done || ks->status) return;
     constexpr int BT = SHAPE_SITES[SH];
     const int local = blockIdx.x - q.blk0[SH];
@@ -249,8 +260,9 @@ __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restri
 template <class R, int SH>
 __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_lstep(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i) {
     using VT = typename BVec<R>::T;
-    const BSeq& q = S[bseq[blockIdx.x]];
+    const BSeq& q = S[bseq[blockIdx.x]];  // set-up data, not written by the solve
     KState* ks = q.ks;
+    pdl_wait_and_release();
     if (ks->done || ks->status) return;
     __shared__ cx<R> cf[4];
     if (threadIdx.x == 0) {
@@ -332,10 +344,11 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
                                                     HopCoef<R> hc) {
     using VT = typename VecT<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
-    cx<R>(*dirpart)[TT][12] = reinterpret_cast<cx<R>(*)[TT][12]>(smraw);  // [8][TT][12]
+    cx<R>(*dirpart)[TT][6] = reinterpret_cast<cx<R>(*)[TT][6]>(smraw);  // [8][TT][2 spins x 3 colours]
     __shared__ cx<R> cf[4];
-    const BSeq& q = S[tseq[blockIdx.x]];
+    const BSeq& q = S[tseq[blockIdx.x]];  // set-up data, not written by the solve
     const KState* ks = q.ks;
+    pdl_wait_and_release();
     if (ks->status || i + 1 >= ks->kused) return;
     if (threadIdx.x == 0) {
         const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(q.beta[i]));
@@ -349,20 +362,17 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
     const VT* ri = (const VT*)q.r[i % 3];
     const void* U = LF == LINK_DF ? q.Udf : (const void*)q.U64;
     {
+        // warp wid: hop wid of the tile's 32 sites, kept as its half spinor
         const int i0 = tile * TT + lane;
-        Spinor<R> acc[1];
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc[0].s[s][c] = mk(R(0), R(0));
         if (i0 < q.g.V) {
             const Coord c = site_coord(q.g, i0);
             const VT* const xs[1] = {ri};
             const HopCoef<R> hcs[1] = {hc};
-            hop_uniform<LF, R, 1>(wid, q.g, c, i0, U, xs, acc, hcs);
-        }
+            Half<R> hp[1];
+            hop_half_uniform<LF, R, 1>(wid, q.g, c, i0, U, xs, hp, hcs);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) dirpart[wid][lane][c] = acc[0].s[c / 3][c % 3];
+            for (int c6 = 0; c6 < 6; ++c6) dirpart[wid][lane][c6] = hp[0].h[c6 / 3][c6 % 3];
+        }
     }
     __syncthreads();
     // epilogue: 256 threads (site, part), components part and part + 8 (< 12)
@@ -378,8 +388,9 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
         if (c >= 12) break;
         const cx<R> self = ld_comp_cg<R>(ri, q.g.V, ii, c);
         cx<R> z = self;
+        const int sp = c / 3, a = c % 3;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) z = z + dirpart[w][site][c];
+        for (int w = 0; w < 8; ++w) z = z + hop_spin<R>(w, sp, dirpart[w][site][a], dirpart[w][site][3 + a]);
         if (c >= 6) z = -z;  // gamma5: spins 2, 3
         z = cf[0] * z - cf[1] * self;
         if (i > 0) z = z - cf[2] * ld_comp_cg<R>(rm, q.g.V, ii, c);
@@ -585,25 +596,43 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     return OVL_OK;
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait_and_release).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // One pass-1 step of every sequence with site-block shape SH.
 template <int SH>
 void pass1_step(ovl_batch* b, int i, int k, double mu, double kappa, bool mixed, cudaStream_t st) {
     const int nb = b->nblocks[SH], T = ovl::SHAPE_SITES[SH];
+    const ovl::BSeq* S = b->dseq;
+    const int* tab = b->dbseq[SH];
     if (mixed) {
-        ovl::k_b_pair<ovl::LINK_F32_12, float, SH><<<nb, T, 0, st>>>(
-            b->dseq, b->dbseq[SH], i, k - 1, ovl::make_coef<float>(mu, kappa), ovl::make_coef<float>(-mu, kappa));
-        if (i + 1 < k) ovl::k_b_lstep<float, SH><<<nb, T, 0, st>>>(b->dseq, b->dbseq[SH], i);
+        launch_pdl(ovl::k_b_pair<ovl::LINK_F32_12, float, SH>, nb, T, 0, st, S, tab, i, k - 1,
+                   ovl::make_coef<float>(mu, kappa), ovl::make_coef<float>(-mu, kappa));
+        if (i + 1 < k) launch_pdl(ovl::k_b_lstep<float, SH>, nb, T, 0, st, S, tab, i);
     } else {
-        ovl::k_b_pair<ovl::LINK_F64, double, SH><<<nb, T, 0, st>>>(
-            b->dseq, b->dbseq[SH], i, k - 1, ovl::make_coef<double>(mu, kappa), ovl::make_coef<double>(-mu, kappa));
-        if (i + 1 < k) ovl::k_b_lstep<double, SH><<<nb, T, 0, st>>>(b->dseq, b->dbseq[SH], i);
+        launch_pdl(ovl::k_b_pair<ovl::LINK_F64, double, SH>, nb, T, 0, st, S, tab, i, k - 1,
+                   ovl::make_coef<double>(mu, kappa), ovl::make_coef<double>(-mu, kappa));
+        if (i + 1 < k) launch_pdl(ovl::k_b_lstep<double, SH>, nb, T, 0, st, S, tab, i);
     }
 }
 
 // One regeneration step of every sequence, blocks-per-SM bound MINB.
 template <int MINB>
 void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStream_t st) {
-    const size_t smr = (size_t)8 * ovl::TT * 12 * 16;
+    const size_t smr = (size_t)8 * ovl::TT * 6 * 16;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -612,12 +641,14 @@ void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStre
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
         attr = true;
     }
+    const ovl::BSeq* S = b->dseq;
+    const int* tab = b->dtseq;
     if (dfm)
-        ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB><<<b->ntiles, 8 * ovl::TT, smr, st>>>(
-            b->dseq, b->dtseq, i, ovl::make_coef<ovl::df>(mu, kappa));
+        launch_pdl(ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB>, b->ntiles, 8 * ovl::TT, smr, st, S, tab, i,
+                   ovl::make_coef<ovl::df>(mu, kappa));
     else
-        ovl::k_b_regen<double, ovl::LINK_F64, MINB><<<b->ntiles, 8 * ovl::TT, smr, st>>>(
-            b->dseq, b->dtseq, i, ovl::make_coef<double>(mu, kappa));
+        launch_pdl(ovl::k_b_regen<double, ovl::LINK_F64, MINB>, b->ntiles, 8 * ovl::TT, smr, st, S, tab, i,
+                   ovl::make_coef<double>(mu, kappa));
 }
 
 // Everything between the packed sources and the unpacked results, on stream st.

@@ -120,13 +120,15 @@ __device__ __forceinline__ cx<R> unit_mul(cx<R> x, bool imag, bool neg) {
 }
 
 // Hop h = 0..7 (direction nu = h & 3, forward for h < 4) with nu and the sign as warp-uniform
-// runtime values: the spin projection and reconstruction of (1 +- gamma_nu) are written as selects
-// and sign flips, so every warp of a direction-split block runs the same instructions (one copy of
-// the hop in the instruction cache instead of eight).  Same arithmetic as hop_fwd / hop_bwd.
+// runtime values: the spin projection of (1 +- gamma_nu) is written as selects and sign flips, so
+// every warp of a direction-split block runs the same instructions (one copy of the hop in the
+// instruction cache instead of eight).  Same arithmetic as hop_fwd / hop_bwd up to the half
+// spinor: out = coefficient x U (or U^dag) x (projected half spinor) of the neighbour; the full
+// four-spin contribution is hop_spin(h, sp, out.h[0], out.h[1]).
 template <int LF, class R, int NIN>
-__device__ __forceinline__ void hop_uniform(int h, const Geom& g, const Coord& c, int i, const void* U,
-                                            const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
-                                            const HopCoef<R> (&hc)[NIN]) {
+__device__ __forceinline__ void hop_half_uniform(int h, const Geom& g, const Coord& c, int i, const void* U,
+                                                 const typename VecT<R>::T* const (&x)[NIN], Half<R> (&out)[NIN],
+                                                 const HopCoef<R> (&hc)[NIN]) {
     const int nu = h & 3;
     const bool fwd = h < 4;
     int y[4];
@@ -146,12 +148,10 @@ __device__ __forceinline__ void hop_uniform(int h, const Geom& g, const Coord& c
     Link<R> L;
     load_link_any<LF>(U, g.V, nu, fwd ? i : nb, L);
     // (1 + S gamma_nu), S = +1 forward, -1 backward, chiral basis: upper spins
-    // h0 = p0 + u0 p[2 or 3], h1 = p1 + u1 p[3 or 2]; lower spins rebuilt from (h0, h1)
+    // h0 = p0 + u0 p[2 or 3], h1 = p1 + u1 p[3 or 2]
     const bool hi2 = nu >= 2, im = (nu & 1) == 0;
     const bool n0 = (nu == 3) ? !fwd : fwd;
     const bool n1 = (nu == 0) ? fwd : !fwd;
-    const bool nA = !fwd;
-    const bool nB = (nu == 0 || nu == 3) ? !fwd : fwd;
 #pragma unroll
     for (int n = 0; n < NIN; ++n) {
         Spinor<R> p;
@@ -167,13 +167,26 @@ __device__ __forceinline__ void hop_uniform(int h, const Geom& g, const Coord& c
         const R cf = (fwd ? (nu == 3 ? hc[n].f[3] : hc[n].f[0]) : (nu == 3 ? hc[n].b[3] : hc[n].b[0])) * ph;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const cx<R> h0 = cf * uh.h[0][a], h1 = cf * uh.h[1][a];
-            acc[n].s[0][a] = acc[n].s[0][a] + h0;
-            acc[n].s[1][a] = acc[n].s[1][a] + h1;
-            acc[n].s[2][a] = acc[n].s[2][a] + unit_mul(hi2 ? h0 : h1, im, nA);
-            acc[n].s[3][a] = acc[n].s[3][a] + unit_mul(hi2 ? h1 : h0, im, nB);
+            out[n].h[0][a] = cf * uh.h[0][a];
+            out[n].h[1][a] = cf * uh.h[1][a];
         }
     }
+}
+
+// Spin sp of hop h's contribution rebuilt from its half spinor (h0, h1): the upper spins are h0,
+// h1, the lower ones +-h or +-i h of one of them (the (1 +- gamma_nu) structure in the chiral
+// basis).  With h and sp compile-time constants this is a select of a component and a sign.
+template <class R>
+__device__ __forceinline__ cx<R> hop_spin(int h, int sp, const cx<R>& h0, const cx<R>& h1) {
+    const int nu = h & 3;
+    const bool fwd = h < 4;
+    const bool hi2 = nu >= 2, im = (nu & 1) == 0;
+    const bool nA = !fwd;
+    const bool nB = (nu == 0 || nu == 3) ? !fwd : fwd;
+    if (sp == 0) return h0;
+    if (sp == 1) return h1;
+    if (sp == 2) return unit_mul(hi2 ? h0 : h1, im, nA);
+    return unit_mul(hi2 ? h1 : h0, im, nB);
 }
 
 template <int LF, class R, int NIN>
