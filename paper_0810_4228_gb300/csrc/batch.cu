@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
         cx<R> z = self;
         const int sp = c / 3, a = c % 3;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) z = z + hop_spin<R>(w, sp, dirpart[w][site][a], dirpart[w][site][3 + a]);
+        for (int w = 0; w < 8; ++w) z = add_lazy(z, hop_spin<R>(w, sp, dirpart[w][site][a], dirpart[w][site][3 + a]));
         if (c >= 6) z = -z;  // gamma5: spins 2, 3
         z = cf[0] * z - cf[1] * self;
         if (i > 0) z = z - cf[2] * ld_comp_cg<R>(rm, q.g.V, ii, c);

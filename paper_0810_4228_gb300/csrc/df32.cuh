@@ -54,6 +54,17 @@ OVL_HD df operator+(df a, df b) {
     e = DF_ADD(e, DF_ADD(a.lo, b.lo));
     return df_fast2sum(s, e);
 }
+// Sum without the final renormalisation: hi + lo holds the sum to the rounding of the lo part,
+// but lo may exceed ulp(hi) / 2 by a few ulps.  Every consumer (products, which take the cross
+// terms with lo in FP32; further sums; the renormalising multiply or store) handles such pairs at
+// the same accuracy; used for intermediate sums whose result feeds another operation.
+OVL_HD df df_add_lazy(df a, df b) {
+    const float s = DF_ADD(a.hi, b.hi);
+    const float bb = DF_SUB(s, a.hi);
+    float e = DF_ADD(DF_SUB(a.hi, DF_SUB(s, bb)), DF_SUB(b.hi, bb));
+    e = DF_ADD(e, DF_ADD(a.lo, b.lo));
+    return df(s, e);
+}
 OVL_HD df operator-(df a) { return df(-a.hi, -a.lo); }
 OVL_HD df operator-(df a, df b) { return a + (-b); }
 OVL_HD df operator*(df a, df b) {
@@ -142,6 +153,8 @@ OVL_HD void mul_link_dag<df>(const Link<df>& U, const Half<df>& h, Half<df>& o) 
             o.h[s][a] = mk(dfacc_value(re), dfacc_value(im));
         }
 }
+
+OVL_HD cx<df> add_lazy(const cx<df>& a, const cx<df>& b) { return mk(df_add_lazy(a.r, b.r), df_add_lazy(a.i, b.i)); }
 
 struct __align__(16) dfc {
     float rh, rl, ih, il;

@@ -113,6 +113,12 @@ __device__ __forceinline__ void one_hop(int h, const Geom& g, const Coord& c, in
 }
 
 // x times a unit: i x if imag, negated if neg (exact: no multiplication)
+// a + b; for double-float an intermediate sum without renormalisation (df_add_lazy)
+template <class R>
+__device__ __forceinline__ cx<R> add_lazy(const cx<R>& a, const cx<R>& b) {
+    return a + b;
+}
+
 template <class R>
 __device__ __forceinline__ cx<R> unit_mul(cx<R> x, bool imag, bool neg) {
     const cx<R> y = imag ? mk(-x.i, x.r) : x;
@@ -159,8 +165,8 @@ __device__ __forceinline__ void hop_half_uniform(int h, const Geom& g, const Coo
         Half<R> hh, uh;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            hh.h[0][a] = p.s[0][a] + unit_mul(hi2 ? p.s[2][a] : p.s[3][a], im, n0);
-            hh.h[1][a] = p.s[1][a] + unit_mul(hi2 ? p.s[3][a] : p.s[2][a], im, n1);
+            hh.h[0][a] = add_lazy(p.s[0][a], unit_mul(hi2 ? p.s[2][a] : p.s[3][a], im, n0));
+            hh.h[1][a] = add_lazy(p.s[1][a], unit_mul(hi2 ? p.s[3][a] : p.s[2][a], im, n1));
         }
         if (fwd) mul_link(L, hh, uh);
         else mul_link_dag(L, hh, uh);
