@@ -331,6 +331,217 @@ __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_lstep(const BSeq* __restr
     }
 }
 
+// ---- persistent batched pass 1 (all sites of the batch resident at once) ----------------------
+// One cooperative launch runs the whole FP32 pass 1 of every sequence: one thread per site, blocks
+// of BP1_T sites, each block within one sequence.  Per step: phase A, t = sv A v~_i and
+// s = sw A^dag w~_i at the own site (kept in registers), block partials of w~^dag t and |t|^2;
+// the sequence's blocks meet at a bounded barrier (a monotonic counter per sequence); every block
+// sums the sequence's partials in the same fixed order, so all of them hold the same alpha_i;
+// phase C, the recurrence of Eq. 4.2 at the own site (v^, w^ stored: the neighbours' next
+// stencil reads them), partials of w^^dag v^, |v^|^2, |w^|^2; second barrier; every block forms
+// beta_i, gamma_i, the scales and the breakdown decisions, identically.  Sequences finish
+// independently.  Vector loads go through L2 (.cg): the ring slots are rewritten during the launch.
+constexpr int BP1_T = 128;
+constexpr long long BP1_SPIN = 20000000;  // polls before a barrier wait gives up (sets ks->timeout)
+
+struct BP1Args {
+    const BSeq* S;
+    const int* bseq;      // block -> sequence (blocks of BP1_T sites: the pass-1 shape 1 tables)
+    unsigned int* bar;    // one barrier counter per sequence, zero at launch
+    int k;
+    HopCoef<float> hv, hw;
+};
+
+// Block sum of NQ compensated pairs into part[local * 4 + q] (warp trees, then the warps in order).
+template <int NQ>
+__device__ __forceinline__ void bp1_block_partial(AccF (&v)[NQ], double2* part, int local) {
+    __shared__ double2 red[NQ][BP1_T / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        AccF x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = accf_add(x, acc_shfl(x, o));
+        if (lane == 0) red[q][wid] = acc_store(x);
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        const int q = threadIdx.x;
+        AccF sacc = acc_load(red[q][0], AccF());
+        for (int w = 1; w < BP1_T / 32; ++w) sacc = accf_add(sacc, acc_load(red[q][w], AccF()));
+        part[(size_t)local * 4 + q] = acc_store(sacc);
+    }
+}
+
+// The sequence's sums of NQ values over its nblk block partials, in a fixed order (lanes over the
+// blocks, then the warp tree), one warp per value; out (shared) is valid in all threads on return.
+template <int NQ>
+__device__ __forceinline__ void bp1_seq_sum(const double2* part, int nblk, double* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int qv = wid; qv < NQ; qv += BP1_T / 32) {
+        AccF acc = acc_load(make_double2(0.0, 0.0), AccF());
+        for (int b = lane; b < nblk; b += 32) acc = accf_add(acc, acc_load(__ldcg(&part[(size_t)b * 4 + qv]), AccF()));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = accf_add(acc, acc_shfl(acc, o));
+        if (lane == 0) {
+            const double2 r = acc_store(acc);
+            out[qv] = r.x + r.y;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ cx<float> f32c(cx<double> z) { return mk((float)z.r, (float)z.i); }
+
+template <int LF>
+__global__ void __launch_bounds__(BP1_T, 3) k_bp1(BP1Args a) {
+    const int sidx = a.bseq[blockIdx.x];
+    const BSeq& q = a.S[sidx];
+    KState* ks = q.ks;
+    if (ks->done || ks->status) return;  // the whole sequence leaves (written before this launch)
+    __shared__ cx<float> cs[2];          // sv, sw of the current step
+    __shared__ cx<float> cc[4];          // alpha sv, conj(alpha) sw, gamma_{i-1} svp, conj(beta_{i-1}) swp
+    __shared__ double osum[4];
+    __shared__ int sdone;
+    const int local = blockIdx.x - q.blk0[1], nblk = q.nblk[1];
+    const int site = local * BP1_T + threadIdx.x;
+    const bool ok = site < q.g.V;
+    const int V = q.g.V;
+    unsigned int* bar = a.bar + sidx;
+    int* err = &ks->timeout;
+    double2* partA = q.part;
+    double2* partC = q.part + (size_t)nblk * 4;
+    // recurrence scalars in FP64, meaningful in thread 0 (identical in every block of the sequence)
+    cx<double> sv = d2c(ks->sv), sw = d2c(ks->sw), svp = d2c(ks->svp), swp = d2c(ks->swp);
+    cx<double> beta_prev = mk(0.0, 0.0), gamma_prev = mk(0.0, 0.0);
+    double anorm = ks->anorm;
+    int kused = 0, bd = -1;
+    if (threadIdx.x == 0) {
+        cs[0] = f32c(sv);
+        cs[1] = f32c(sw);
+    }
+    __syncthreads();
+    unsigned int nb = 0;
+    for (int i = 0; i < a.k; ++i) {
+        const float4* vi = (const float4*)q.v[i % 3];
+        const float4* wi = (const float4*)q.w[i % 3];
+        // ---- phase A
+        AccF pa[3];
+        Spinor<float> t, s;
+        if (ok) {
+            const float4* const xs[2] = {vi, wi};
+            const HopCoef<float> hcs[2] = {a.hv, a.hw};
+            Spinor<float> acc[2], self[2];
+            apply_site<LF, float, 2, true>(q.g, site, q.U, xs, acc, hcs);
+            load_spinor_cg(vi, V, site, self[0]);
+            load_spinor_cg(wi, V, site, self[1]);
+            finish_site(acc[0], self[0], true);
+            finish_site(acc[1], self[1], true);
+            t = acc[0];
+            s = acc[1];
+            const cx<float> fsv = cs[0], fsw = cs[1];
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    t.s[sp][c] = fsv * t.s[sp][c];
+                    s.s[sp][c] = fsw * s.s[sp][c];
+                    acc_cdot(pa, self[1].s[sp][c], t.s[sp][c]);
+                    acc_norm2(pa[2], t.s[sp][c]);
+                }
+        }
+        bp1_block_partial<3>(pa, partA, local);
+        grid_barrier_mono(bar, (unsigned)nblk * (++nb), err, 1, BP1_SPIN);
+        if (*(volatile int*)err) return;
+        bp1_seq_sum<3>(partA, nblk, osum);
+        if (threadIdx.x == 0) {
+            const cx<double> alpha = cdot(sw, mk(osum[0], osum[1]));  // conj(sw) w~^dag t
+            anorm = fmax(anorm, sqrt(osum[2]));
+            kused = i + 1;
+            if (local == 0) q.alpha[i] = c2d(alpha);
+            cc[0] = f32c(alpha * sv);
+            cc[1] = f32c(conj(alpha) * sw);
+            cc[2] = f32c(i > 0 ? gamma_prev * svp : mk(0.0, 0.0));
+            cc[3] = f32c(i > 0 ? conj(beta_prev) * swp : mk(0.0, 0.0));
+        }
+        if (i == a.k - 1) break;
+        __syncthreads();
+        // ---- phase C: v^ = t - alpha v_i - gamma_{i-1} v_{i-1}, w^ likewise (Eq. 4.2)
+        AccF pc[4];
+        if (ok) {
+            const cx<float> ca = cc[0], da = cc[1], cg = cc[2], db = cc[3];
+            Spinor<float> vv, ww, vm, wm;
+            load_spinor_cg(vi, V, site, vv);
+            load_spinor_cg(wi, V, site, ww);
+            if (i > 0) {
+                load_spinor_cg((const float4*)q.v[(i + 2) % 3], V, site, vm);
+                load_spinor_cg((const float4*)q.w[(i + 2) % 3], V, site, wm);
+            }
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    cx<float> x = t.s[sp][c] - ca * vv.s[sp][c];
+                    cx<float> y = s.s[sp][c] - da * ww.s[sp][c];
+                    if (i > 0) {
+                        x = x - cg * vm.s[sp][c];
+                        y = y - db * wm.s[sp][c];
+                    }
+                    t.s[sp][c] = x;
+                    s.s[sp][c] = y;
+                    acc_cdot(pc, y, x);
+                    acc_norm2(pc[2], x);
+                    acc_norm2(pc[3], y);
+                }
+            store_spinor((float4*)q.v[(i + 1) % 3], V, site, t);
+            store_spinor((float4*)q.w[(i + 1) % 3], V, site, s);
+        }
+        bp1_block_partial<4>(pc, partC, local);
+        grid_barrier_mono(bar, (unsigned)nblk * (++nb), err, 1, BP1_SPIN);
+        if (*(volatile int*)err) return;
+        bp1_seq_sum<4>(partC, nblk, osum);
+        if (threadIdx.x == 0) {
+            const double nv = sqrt(osum[2]), nw = sqrt(osum[3]);
+            const cx<double> delta = mk(osum[0], osum[1]);
+            int dn = 0;
+            if (nv <= 1e-13 * fmax(anorm, 1e-300)) {
+                dn = 1;  // lucky breakdown
+            } else if (sqrt(norm2(delta)) <= 1e-14 * nv * nw) {
+                dn = 1;  // serious breakdown
+                bd = i + 1;
+            } else {
+                const cx<double> gm = mk(osum[0] / nv, osum[1] / nv);
+                beta_prev = mk(nv, 0.0);
+                gamma_prev = gm;
+                svp = sv;
+                swp = sw;
+                sv = mk(1.0 / nv, 0.0);
+                sw = cdiv(mk(1.0, 0.0), conj(gm));
+                if (local == 0) {
+                    q.beta[i] = make_double2(nv, 0.0);
+                    q.gamma[i] = c2d(gm);
+                    q.vscale[i + 1] = c2d(sv);
+                }
+                cs[0] = f32c(sv);
+                cs[1] = f32c(sw);
+            }
+            sdone = dn;
+        }
+        __syncthreads();
+        if (sdone) break;
+    }
+    if (local == 0 && threadIdx.x == 0) {
+        ks->kused = kused;
+        ks->done = 1;
+        ks->anorm = anorm;
+        if (bd >= 0) ks->bdstep = bd;
+        ks->sv = c2d(sv);
+        ks->sw = c2d(sw);
+        ks->svp = c2d(svp);
+        ks->swp = c2d(swp);
+    }
+}
+
 // Regeneration (Sec. 5): r_{i+1} = ((A - alpha_i) r_i - gamma_{i-1} r_{i-1}) / beta_i, y += c_{i+1} r_{i+1},
 // in FP64 (R = double) or double-float (R = df; ring and y converted beforehand).  One block per
 // 32-site tile of a sequence: warp h applies hop h (direction-uniform code) to the tile's sites, the
@@ -418,6 +629,8 @@ struct ovl_batch {
     ovl::BSeq* dseq = nullptr;
     int* dbseq[ovl::NSHAPE] = {nullptr, nullptr, nullptr};
     int* dtseq = nullptr;
+    unsigned int* pbar = nullptr;  // per-sequence barrier counters of the persistent pass 1
+    int bp1_fit = -1;              // persistent pass 1 fits the GPU (-1: not yet determined)
     int nblocks[ovl::NSHAPE] = {0, 0, 0};
     int ntiles = 0;
     // autotuned launch shapes: pass-1 site-block shape, blocks per SM of the regeneration kernel
@@ -481,7 +694,9 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     for (int s = 0; s < ns; ++s) {
         const ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const size_t n = c->n;
-        const int nblk = (c->g.V + ovl::SHAPE_SITES[0] - 1) / ovl::SHAPE_SITES[0];  // the most blocks
+        // partials: the most blocks of a pass-1 shape, or two sets for the persistent pass 1
+        const int nblk = std::max((c->g.V + ovl::SHAPE_SITES[0] - 1) / ovl::SHAPE_SITES[0],
+                                  2 * ((c->g.V + ovl::BP1_T - 1) / ovl::BP1_T));
         for (int h = 0; h < ovl::NSHAPE; ++h) nblocks[h] += (c->g.V + ovl::SHAPE_SITES[h] - 1) / ovl::SHAPE_SITES[h];
         ntiles += (c->g.V + ovl::TT - 1) / ovl::TT;
         size_t z = 0;
@@ -498,7 +713,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
              al((size_t)ns * inner_stride * sizeof(double2)) + al((size_t)ns * qpart_stride * sizeof(double)) +
              al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks[0] * sizeof(int)) +
              al(nblocks[1] * sizeof(int)) + al(nblocks[2] * sizeof(int)) +
-             al(ntiles * sizeof(int)) +
+             al(ntiles * sizeof(int)) + al(ns * sizeof(unsigned int)) +
              al((size_t)(1 << 20) * sizeof(double)) + al(64 * sizeof(unsigned int));
     if (cudaMalloc(&b->mem, total) != cudaSuccess) {
         b->mem = nullptr;
@@ -521,6 +736,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     b->dseq = (ovl::BSeq*)take(ns * sizeof(ovl::BSeq));
     for (int h = 0; h < ovl::NSHAPE; ++h) b->dbseq[h] = (int*)take(nblocks[h] * sizeof(int));
     b->dtseq = (int*)take(ntiles * sizeof(int));
+    b->pbar = (unsigned int*)take(ns * sizeof(unsigned int));
     b->part = (double*)take((size_t)(1 << 20) * sizeof(double));
     b->counter = (unsigned int*)take(64 * sizeof(unsigned int));
     b->hseq.assign(ns, ovl::BSeq());
@@ -566,7 +782,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         q.cvec = b->cvec + s * kk;
         q.vscale = b->vscale + s * kk;
         for (int h = 0; h < ovl::NSHAPE; ++h) q.nblk[h] = (c->g.V + ovl::SHAPE_SITES[h] - 1) / ovl::SHAPE_SITES[h];
-        q.part = (double2*)take((size_t)q.nblk[0] * 4 * sizeof(double2));
+        q.part = (double2*)take((size_t)std::max(q.nblk[0], 2 * q.nblk[1]) * 4 * sizeof(double2));
         b->pq[s] = (double2*)take(128 * sizeof(double2));
         q.cnt = b->qcnt + s;  // the inner quadrature's counters follow at qcnt + nseq
         for (int h = 0; h < ovl::NSHAPE; ++h) {
@@ -610,6 +826,40 @@ void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaSt
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// The whole FP32 pass 1 as one cooperative launch when all of the batch's sites fit the GPU at once.
+bool bp1_fits(ovl_batch* b) {
+    if (b->bp1_fit < 0) {
+        int per_sm = 0, nsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ovl::k_bp1<ovl::LINK_F32_12>, ovl::BP1_T, 0);
+        b->bp1_fit = (per_sm > 0 && b->nblocks[1] <= per_sm * nsm) ? 1 : 0;
+    }
+    return b->bp1_fit == 1;
+}
+
+int launch_bp1(ovl_batch* b, int k, double mu, double kappa, cudaStream_t st) {
+    if (cudaMemsetAsync(b->pbar, 0, b->nseq * sizeof(unsigned int), st) != cudaSuccess) return OVL_ECUDA;
+    ovl::BP1Args a;
+    a.S = b->dseq;
+    a.bseq = b->dbseq[1];
+    a.bar = b->pbar;
+    a.k = k;
+    a.hv = ovl::make_coef<float>(mu, kappa);
+    a.hw = ovl::make_coef<float>(-mu, kappa);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->nblocks[1]);
+    cfg.blockDim = dim3(ovl::BP1_T);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ovl::k_bp1<ovl::LINK_F32_12>, a) == cudaSuccess ? OVL_OK : OVL_ECUDA;
 }
 
 // One pass-1 step of every sequence with site-block shape SH.
@@ -678,8 +928,11 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
             cudaMemcpyAsync(q.w[0], b->bL[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
         }
     }
-    // pass 1 (all sequences per launch)
+    // pass 1 (all sequences per launch): one persistent launch for mixed batches that fit the GPU
     if (prof) cudaEventRecord(b->ev[0], st);
+    if (mixed && !(flags & OVL_STEPWISE) && bp1_fits(b)) {
+        if (launch_bp1(b, k, mu, kappa, st)) return bfail(b, OVL_ECUDA, "persistent pass-1 launch");
+    } else
     for (int i = 0; i < k; ++i) {
         switch (b->shape) {
             case 0: pass1_step<0>(b, i, k, mu, kappa, mixed, st); break;
@@ -881,7 +1134,7 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
         for (cudaEvent_t& e : b->ev)
             if (!e && cudaEventCreate(&e) != cudaSuccess) return bfail(b, OVL_ECUDA, "profile events");
     }
-    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH | OVL_TWO_PASS | OVL_PASS2_F64);
+    const int gflags = flags & (OVL_MIXED | OVL_NO_GRAPH | OVL_TWO_PASS | OVL_PASS2_F64 | OVL_STEPWISE);
     if (flags & OVL_NO_GRAPH) {
         r = enqueue_batch(b, k, mu, kappa, flags, st);
         if (r) return r;

@@ -195,7 +195,9 @@ __device__ __forceinline__ cx<R> hop_spin(int h, int sp, const cx<R>& h0, const 
     return unit_mul(hi2 ? h1 : h0, im, nB);
 }
 
-template <int LF, class R, int NIN>
+// The hopping term of site i for NIN inputs (CG: L2-coherent vector loads, for vectors written by
+// other blocks of the same kernel).
+template <int LF, class R, int NIN, bool CG = false>
 __device__ __forceinline__ void apply_site(const Geom& g, int i, const void* U,
                                            const typename VecT<R>::T* const (&x)[NIN], Spinor<R> (&acc)[NIN],
                                            const HopCoef<R> (&hc)[NIN]) {
@@ -206,10 +208,10 @@ __device__ __forceinline__ void apply_site(const Geom& g, int i, const void* U,
         for (int s = 0; s < 4; ++s)
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc[n].s[s][a] = mk(R(0), R(0));
-    hops_dir<0, LF, R, NIN>(g, c, i, U, x, acc, hc);
-    hops_dir<1, LF, R, NIN>(g, c, i, U, x, acc, hc);
-    hops_dir<2, LF, R, NIN>(g, c, i, U, x, acc, hc);
-    hops_dir<3, LF, R, NIN>(g, c, i, U, x, acc, hc);
+    hops_dir<0, LF, R, NIN, CG>(g, c, i, U, x, acc, hc);
+    hops_dir<1, LF, R, NIN, CG>(g, c, i, U, x, acc, hc);
+    hops_dir<2, LF, R, NIN, CG>(g, c, i, U, x, acc, hc);
+    hops_dir<3, LF, R, NIN, CG>(g, c, i, U, x, acc, hc);
 }
 
 // add the diagonal term and apply gamma5 = diag(1, 1, -1, -1)

@@ -264,3 +264,22 @@ def test_batch_rejects_unknown_shape(ovl, small):
         bt.set_tuning(128, 5)
     assert bt.tuning() is None
     bt.close()
+
+
+def test_batch_persistent_pass1_equals_stepwise(ovl, mid):
+    """The persistent pass 1 (one cooperative launch) and the stepwise kernels with the same block
+    shape (128 sites) do the same arithmetic in the same order: equal results."""
+    c4 = config4()
+    ca, cb = _ctx(ovl, c4["dims"], c4["U"]), _ctx(ovl, mid["dims"], mid["U"])
+    ba, bb = _sources(c4["dims"], 4200, 2), _sources(mid["dims"], 4201, 3)
+    srcs = [torch_c128(ba), torch_c128(bb)]
+    bt = ovl.Batch([ca, cb], [2, 3])
+    bt.set_tuning(128, 3)
+    yp = [o.cpu().numpy() for o in bt.solve(400, c4["mu"], KAPPA, srcs, flags=ovl.MIXED)[0]]
+    ys = [o.cpu().numpy() for o in bt.solve(400, c4["mu"], KAPPA, srcs, flags=ovl.MIXED | ovl.STEPWISE)[0]]
+    for a, b in zip(yp, ys):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    sgn4 = c4["X"] @ (S.csign(c4["lam"])[:, None] * c4["Xi"])
+    for r in range(2):
+        assert rel(yp[0][r], sgn4 @ ba[r]) < 1e-8
+    bt.close()
