@@ -426,6 +426,17 @@ def run_ours(args, world, rank, local):
         else:
             t = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix),
                             [0], args.warmup, args.steps, flush)
+        if args.profile_one:
+            # one more solve between cudaProfilerStart/Stop: `ncu --profile-from-start off` captures
+            # exactly the launches of one solve (no effect without a profiler)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
+            if args.single:
+                ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, srcs[0], out1, flags=fl_mix)
+            else:
+                bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
         print(json.dumps({"solves_only": True, "single": args.single, "k": k_mix, "ms_per_step": statistics.mean(t)}))
         return
 
@@ -584,6 +595,8 @@ def main():
     ap.add_argument("--single", action="store_true", help="with --solves-only: single-source solves instead of batches")
     ap.add_argument("--dw-only", action="store_true", help="only the stencil bandwidth measurement (--steps repetitions)")
     ap.add_argument("--dw-dims", default="", help="lattice of the stencil bandwidth measurement, e.g. 32,32,32,32")
+    ap.add_argument("--profile-one", action="store_true",
+                    help="with --solves-only: one extra solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--solves-only", action="store_true",
                     help="only the timed solves (for profiler captures): needs --k, skips calibration, "
                          "profile, FP64/Arnoldi/e2e legs, the bandwidth lattice and the CPU baseline")
