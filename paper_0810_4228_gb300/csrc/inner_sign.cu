@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "ovl_kernels.h"
+#include "df32.cuh"
 
 namespace ovl {
 
@@ -49,8 +50,9 @@ struct QStride {
 
 size_t inner_work_elems(int kmax, int method) {
     if (method == 0) {
-        // per thread and row: 3 complex (b/d, u/d, w/d), plus T and S sums
-        return (size_t)quad_threads(QUAD_LEVELS - 1) * (size_t)kmax * 3 + 2 * (size_t)kmax + 64;
+        // per thread and row: 3 complex (b/d, u/d, w/d), plus T and S sums, plus the double-float
+        // copies of alpha, beta, gamma
+        return (size_t)quad_threads(QUAD_LEVELS - 1) * (size_t)kmax * 3 + 5 * (size_t)kmax + 64;
     }
     // Newton: S, X (kmax^2 each) + pivots, slots, scalars, barrier, partials
     return 2 * (size_t)kmax * kmax + 4 * (size_t)kmax + 8192;
@@ -59,7 +61,7 @@ size_t inner_work_elems(int kmax, int method) {
 // ---------------------------------------------------------- quadrature --
 // log of a Gershgorin bound on |lambda_max(G)| -> ks->red[7].x
 __global__ void k_quad_prep(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,
-                            QStride qs) {
+                            double2* work, size_t coef_off, QStride qs) {
     __shared__ double red[32];
     {
         const size_t j = blockIdx.x;
@@ -67,8 +69,16 @@ __global__ void k_quad_prep(const double2* alpha, const double2* beta, const dou
         beta += j * qs.coef;
         gamma += j * qs.coef;
         ks += j;
+        work += j * qs.work;
     }
     const int n = ks->kused;
+    // double-float copies of the tridiagonal coefficients for the solves (dfc in the FP64 slots)
+    dfc* cd = reinterpret_cast<dfc*>(work + coef_off);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        cd[i] = c2dfc(d2df(alpha[i]));
+        cd[n + i] = c2dfc(d2df(beta[i]));
+        cd[2 * n + i] = c2dfc(d2df(gamma[i]));
+    }
     double m = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double r = hypot(alpha[i].x, alpha[i].y);
@@ -91,16 +101,36 @@ __global__ void k_quad_prep(const double2* alpha, const double2* beta, const dou
     }
 }
 
-// One thread per (node, sign): solve (G + s i e^u) x = e_1, store e^u x in the
-// scratch column of the thread (row-major over rows, thread fastest).
-__global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* __restrict__ beta,
-                             const double2* __restrict__ gamma, KState* ks, double2* __restrict__ work, int level,
-                             int nthreads, QStride qs) {
+// Double-float complex helpers of the solves: conj, 1/z with a power-of-two scaling (the FP32
+// exponent range of the hi parts: |z| reaches e^40 |G| at the quadrature's ends), |re| + |im|.
+__device__ __forceinline__ cx<df> dconj(const cx<df>& z) { return mk(z.r, -z.i); }
+__device__ __forceinline__ df df_scale(df a, float s) { return df(a.hi * s, a.lo * s); }  // exact (power of 2)
+__device__ __forceinline__ df df_rcp(df a) {
+    const df r0(__frcp_rn(a.hi), 0.f);
+    const df e = df(1) - a * r0;  // one Newton step: r = r0 + r0 (1 - a r0)
+    return r0 + r0 * e;
+}
+__device__ __forceinline__ cx<df> crcp(const cx<df>& z) {
+    const float mx = fmaxf(fabsf(z.r.hi), fabsf(z.i.hi));
+    int e;
+    frexpf(mx, &e);
+    const float sc = ldexpf(1.f, -e);
+    const cx<df> zs = mk(df_scale(z.r, sc), df_scale(z.i, sc));
+    const df inv = df_rcp(zs.r * zs.r + zs.i * zs.i);
+    return mk(df_scale(zs.r * inv, sc), df_scale(-(zs.i * inv), sc));
+}
+__device__ __forceinline__ float cabs1f(const cx<df>& z) { return fabsf(z.r.hi) + fabsf(z.i.hi); }
+
+// One thread per (node, sign): solve (G + s i e^u) x = e_1 by Gaussian elimination with partial
+// pivoting (interchanging rows i and i+1 when |beta_i| > |d_i|), store e^u x in the scratch column
+// of the thread (row-major over rows, thread fastest).  Double-float arithmetic (df32.cuh) on the
+// FP32 pipe: a node's elimination is one dependent chain of complex operations per row, and
+// GB300's FP64 unit would run each of them 64x slower; 48 significant bits keep the quadrature's
+// 1e-14 accuracy.
+__global__ void k_quad_solve(KState* ks, double2* __restrict__ work, size_t coef_off, int level, int nthreads,
+                             QStride qs) {
     {
         const size_t j = blockIdx.y;
-        alpha += j * qs.coef;
-        beta += j * qs.coef;
-        gamma += j * qs.coef;
         ks += j;
         work += j * qs.work;
     }
@@ -108,9 +138,12 @@ __global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* _
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nthreads) return;
     const int n = ks->kused;
+    const dfc* ca = reinterpret_cast<const dfc*>(work + coef_off);
+    const dfc* cb = ca + n;
+    const dfc* cg = ca + 2 * n;
     const double lo = ks->red[7].x - QUAD_HALFWIDTH;
     const int node = t >> 1;
-    const double sgn = (t & 1) ? -1.0 : 1.0;
+    const float sgn = (t & 1) ? -1.f : 1.f;
     double u;
     if (level == 0) {
         u = lo + node * QUAD_H0;
@@ -118,59 +151,55 @@ __global__ void k_quad_solve(const double2* __restrict__ alpha, const double2* _
         const double hl = QUAD_H0 / (double)(1 << level);
         u = lo + (2 * node + 1) * hl;
     }
-    const double tau = exp(u);
-    const cx<double> sig = mk(0.0, sgn * tau);
+    const df tau(exp(u));
+    const cx<df> sig = mk(df(0), df(tau.hi * sgn, tau.lo * sgn));
     // arrays: bd = b/d, ud = u/d, wd = w/d of the final (upper triangular) rows
-    double2* bd = work;
-    double2* ud = work + (size_t)n * nthreads;
-    double2* wd = work + 2 * (size_t)n * nthreads;
+    dfc* bd = reinterpret_cast<dfc*>(work);
+    dfc* ud = bd + (size_t)n * nthreads;
+    dfc* wd = bd + 2 * (size_t)n * nthreads;
+    const dfc zero = {0.f, 0.f, 0.f, 0.f};
 #define IDX(i) ((size_t)(i) * nthreads + t)
     // current row i: (d, u) at (i, i+1), rhs rb
-    cx<double> d = d2c(alpha[0]) + sig;
-    cx<double> uu = n > 1 ? d2c(gamma[0]) : mk(0.0, 0.0);
-    cx<double> rb = mk(1.0, 0.0);
+    cx<df> d = dfc2c(ca[0]) + sig;
+    cx<df> uu = n > 1 ? dfc2c(cg[0]) : mk(df(0), df(0));
+    cx<df> rb = mk(df(1), df(0));
     for (int i = 0; i + 1 < n; ++i) {
-        const cx<double> l = d2c(beta[i]);                    // row i+1, column i
-        const cx<double> dn = d2c(alpha[i + 1]) + sig;        // row i+1, column i+1
-        const cx<double> un = (i + 2 < n) ? d2c(gamma[i + 1]) : mk(0.0, 0.0);
-        const double nd2 = norm2(d), nl2 = norm2(l);
-        if (nd2 >= nl2) {
-            // no interchange: final row i = (d, uu, 0); one reciprocal 1/d = conj(d)/|d|^2
-            const double inv = 1.0 / nd2;
-            const cx<double> id = mk(d.r * inv, -d.i * inv);
-            const cx<double> m = l * id;
-            bd[IDX(i)] = c2d(rb * id);
-            ud[IDX(i)] = c2d(uu * id);
-            wd[IDX(i)] = make_double2(0.0, 0.0);
+        const cx<df> l = dfc2c(cb[i]);                  // row i+1, column i
+        const cx<df> dn = dfc2c(ca[i + 1]) + sig;       // row i+1, column i+1
+        const cx<df> un = (i + 2 < n) ? dfc2c(cg[i + 1]) : mk(df(0), df(0));
+        if (cabs1f(d) >= cabs1f(l)) {
+            // no interchange: final row i = (d, uu, 0)
+            const cx<df> id = crcp(d);
+            const cx<df> m = l * id;
+            bd[IDX(i)] = c2dfc(rb * id);
+            ud[IDX(i)] = c2dfc(uu * id);
+            wd[IDX(i)] = zero;
             d = dn - m * uu;
             uu = un;
-            rb = mk(0.0, 0.0) - m * rb;   // rhs of row i+1 is 0 for e_1 beyond row 0
+            rb = -(m * rb);  // rhs of row i+1 is 0 for e_1 beyond row 0
         } else {
             // interchange rows i and i+1: final row i = (l, dn, un), rhs 0
-            const double inv = 1.0 / nl2;
-            const cx<double> il = mk(l.r * inv, -l.i * inv);
-            const cx<double> m = d * il;
-            bd[IDX(i)] = make_double2(0.0, 0.0);
-            ud[IDX(i)] = c2d(dn * il);
-            wd[IDX(i)] = c2d(un * il);
-            const cx<double> nd = uu - m * dn;
-            const cx<double> nu = mk(0.0, 0.0) - m * un;
+            const cx<df> il = crcp(l);
+            const cx<df> m = d * il;
+            bd[IDX(i)] = zero;
+            ud[IDX(i)] = c2dfc(dn * il);
+            wd[IDX(i)] = c2dfc(un * il);
+            const cx<df> nd = uu - m * dn;
+            uu = -(m * un);
             d = nd;
-            uu = nu;
             // new rhs of row i+1: rb (old row i) - m * 0
         }
     }
-    if (norm2(d) == 0.0) {
+    if (d.r.hi == 0.f && d.i.hi == 0.f) {
         atomicExch(&ks->status, 5);  // singular shifted matrix
         return;
     }
     // back substitution, x overwrites bd
-    const cx<double> w8 = mk(tau, 0.0);
-    cx<double> x1 = cdiv(rb, d), x2 = mk(0.0, 0.0);
-    bd[IDX(n - 1)] = c2d(w8 * x1);
+    cx<df> x1 = rb * crcp(d), x2 = mk(df(0), df(0));
+    bd[IDX(n - 1)] = c2dfc(mk(tau * x1.r, tau * x1.i));
     for (int i = n - 2; i >= 0; --i) {
-        cx<double> x = d2c(bd[IDX(i)]) - d2c(ud[IDX(i)]) * x1 - d2c(wd[IDX(i)]) * x2;
-        bd[IDX(i)] = c2d(w8 * x);
+        const cx<df> x = dfc2c(bd[IDX(i)]) - dfc2c(ud[IDX(i)]) * x1 - dfc2c(wd[IDX(i)]) * x2;
+        bd[IDX(i)] = c2dfc(mk(tau * x.r, tau * x.i));
         x2 = x1;
         x1 = x;
     }
@@ -198,20 +227,25 @@ __global__ void k_quad_sum(const double2* __restrict__ work, double2* __restrict
     // one warp per row i
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = blockIdx.x * nw + wid; i < n; i += gridDim.x * nw) {
-        double sr = 0.0, si = 0.0, er = 0.0, ei = 0.0;  // all nodes; even nodes (step 2h)
+        // double-float sums of the solves' double-float outputs (all nodes; even nodes, step 2h)
+        df dsr(0), dsi(0), der(0), dei(0);
+        const dfc* wk = reinterpret_cast<const dfc*>(work);
         for (int t = lane; t < nthreads; t += 32) {
-            double2 v = work[(size_t)i * nthreads + t];
-            sr += v.x;
-            si += v.y;
+            const cx<df> v = dfc2c(wk[(size_t)i * nthreads + t]);
+            dsr = df_add_lazy(dsr, v.r);
+            dsi = df_add_lazy(dsi, v.i);
             if (((t >> 1) & 1) == 0) {
-                er += v.x;
-                ei += v.y;
+                der = df_add_lazy(der, v.r);
+                dei = df_add_lazy(dei, v.i);
             }
         }
-        sr = warp_sum(sr);
-        si = warp_sum(si);
-        er = warp_sum(er);
-        ei = warp_sum(ei);
+        for (int o = 16; o > 0; o >>= 1) {
+            dsr = dsr + df(__shfl_xor_sync(0xffffffffu, dsr.hi, o), __shfl_xor_sync(0xffffffffu, dsr.lo, o));
+            dsi = dsi + df(__shfl_xor_sync(0xffffffffu, dsi.hi, o), __shfl_xor_sync(0xffffffffu, dsi.lo, o));
+            der = der + df(__shfl_xor_sync(0xffffffffu, der.hi, o), __shfl_xor_sync(0xffffffffu, der.lo, o));
+            dei = dei + df(__shfl_xor_sync(0xffffffffu, dei.hi, o), __shfl_xor_sync(0xffffffffu, dei.lo, o));
+        }
+        const double sr = dsr.to_double(), si = dsi.to_double(), er = der.to_double(), ei = dei.to_double();
         if (lane == 0) {
             // level 0 compares with the trapezoid sum of step 2h over its even nodes
             double2 old = level == 0 ? make_double2(2.0 * wgt * er, 2.0 * wgt * ei) : T[i];
@@ -244,10 +278,11 @@ static void quad_launch(const double2* alpha, const double2* beta, const double2
                         cudaStream_t st) {
     const int tmax = quad_threads(QUAD_LEVELS - 1);
     double2* T = work + (size_t)tmax * kmax * 3;
-    k_quad_prep<<<nseq, 256, 0, st>>>(alpha, beta, gamma, ks, qs);
+    const size_t coef_off = (size_t)tmax * kmax * 3 + 2 * (size_t)kmax + 64;
+    k_quad_prep<<<nseq, 256, 0, st>>>(alpha, beta, gamma, ks, work, coef_off, qs);
     for (int level = 0; level < QUAD_LEVELS; ++level) {
         const int nt = quad_threads(level);
-        k_quad_solve<<<dim3((nt + 31) / 32, nseq), 32, 0, st>>>(alpha, beta, gamma, ks, work, level, nt, qs);
+        k_quad_solve<<<dim3((nt + 31) / 32, nseq), 32, 0, st>>>(ks, work, coef_off, level, nt, qs);
         int blocks = (kmax + 7) / 8;
         if (blocks > 256) blocks = 256;
         k_quad_sum<<<dim3(blocks, nseq), 256, 0, st>>>(work, T, c, ks, level, nt, partials, counter, qs);
