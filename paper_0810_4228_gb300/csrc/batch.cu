@@ -648,8 +648,15 @@ struct ovl_batch {
     double* qpart = nullptr;
     size_t qpart_stride = 0;
     unsigned int* qcnt = nullptr;
-    double* part = nullptr;      // scratch of the per-sequence prologue kernels
+    double* part = nullptr;      // scratch of the per-sequence prologue kernels (pro_off[s] doubles in)
+    std::vector<size_t> pro_off;
+    std::vector<int> pro_m;      // deflation sizes the prologue scratch was laid out for
     unsigned int* counter = nullptr;
+    // the sequences' prologues run on side streams (graph branches), joined before pass 1
+    static constexpr int NSIDE = 4;
+    cudaStream_t side[NSIDE] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[NSIDE] = {nullptr, nullptr, nullptr, nullptr};
     double2* stage = nullptr;    // host transfers
     // per-phase profile (OVL_PROFILE): pass 1, inner sign, pass 2 / combination
     double prof_ms[3] = {0.0, 0.0, 0.0};
@@ -709,12 +716,22 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         seq_bytes[s] = z;
         total += z;
     }
+    // prologue scratch per sequence: the two-stage projections' partials (m vectors x blocks,
+    // complex) or the deflation split's grid sum (4 values x at most 512 blocks)
+    std::vector<size_t> pro_off(ns + 1, 0);
+    std::vector<int> pro_m(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+        const ovl_ctx* c = b->ctx[b->seq_ctx[s]];
+        pro_m[s] = c->m;
+        const size_t need = std::max<size_t>((size_t)2 * std::max(c->m, 1) * ovl::multidot_blocks(c->n), 2048);
+        pro_off[s + 1] = pro_off[s] + ((need + 31) & ~(size_t)31);
+    }
     total += al(ns * sizeof(ovl::KState)) + 5 * al(ns * kk * sizeof(double2)) +
              al((size_t)ns * inner_stride * sizeof(double2)) + al((size_t)ns * qpart_stride * sizeof(double)) +
              al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks[0] * sizeof(int)) +
              al(nblocks[1] * sizeof(int)) + al(nblocks[2] * sizeof(int)) +
              al(ntiles * sizeof(int)) + al(ns * sizeof(unsigned int)) +
-             al((size_t)(1 << 20) * sizeof(double)) + al(64 * sizeof(unsigned int));
+             al(pro_off[ns] * sizeof(double)) + al(64 * sizeof(unsigned int));
     if (cudaMalloc(&b->mem, total) != cudaSuccess) {
         b->mem = nullptr;
         return bfail(b, OVL_ENOMEM, "batch workspace");
@@ -737,7 +754,9 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     for (int h = 0; h < ovl::NSHAPE; ++h) b->dbseq[h] = (int*)take(nblocks[h] * sizeof(int));
     b->dtseq = (int*)take(ntiles * sizeof(int));
     b->pbar = (unsigned int*)take(ns * sizeof(unsigned int));
-    b->part = (double*)take((size_t)(1 << 20) * sizeof(double));
+    b->part = (double*)take(pro_off[ns] * sizeof(double));
+    b->pro_off = pro_off;
+    b->pro_m = pro_m;
     b->counter = (unsigned int*)take(64 * sizeof(unsigned int));
     b->hseq.assign(ns, ovl::BSeq());
     b->b64.assign(ns, nullptr), b->bR.assign(ns, nullptr), b->bL.assign(ns, nullptr), b->pq.assign(ns, nullptr);
@@ -908,25 +927,45 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
     const bool twopass = b->mode != 0;
     const int ns = b->nseq;
     const bool prof = (flags & OVL_PROFILE) != 0;
+    // prologue of every sequence (deflation split, start vectors): independent, so they run on
+    // side streams forked from st and joined before pass 1 (parallel branches of the graph)
+    const int nside = std::min(ns, ovl_batch::NSIDE);
+    if (!b->ev_fork) {
+        if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+            return bfail(b, OVL_ECUDA, "prologue events");
+        for (int j = 0; j < ovl_batch::NSIDE; ++j)
+            if (cudaStreamCreateWithFlags(&b->side[j], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ev_join[j], cudaEventDisableTiming) != cudaSuccess)
+                return bfail(b, OVL_ECUDA, "prologue streams");
+    }
+    cudaEventRecord(b->ev_fork, st);
+    for (int j = 0; j < nside; ++j) cudaStreamWaitEvent(b->side[j], b->ev_fork, 0);
     for (int s = 0; s < ns; ++s) {
+        cudaStream_t ss = b->side[s % nside];
         ovl_ctx* c = b->ctx[b->seq_ctx[s]];
         const ovl::BSeq& q = b->hseq[s];
         const size_t n = q.n;
-        ovl::launch_state_init(q.ks, st);
+        double* part = b->part + b->pro_off[s];
+        unsigned int* cnt = b->qcnt + 2 * ns + s;  // zero between uses (the last block resets it)
+        ovl::launch_state_init(q.ks, ss);
         const int m = c->m;
         if (m > 0) {
-            ovl::launch_multidot(c->L, n, m, b->b64[s], b->pq[s], 0, b->part, n, st);
-            ovl::launch_multidot(c->R, n, m, b->b64[s], b->pq[s] + m, 0, b->part, n, st);
+            ovl::launch_multidot(c->L, n, m, b->b64[s], b->pq[s], 0, part, n, ss);
+            ovl::launch_multidot(c->R, n, m, b->b64[s], b->pq[s] + m, 0, part, n, ss);
         }
         ovl::launch_deflate_split(b->b64[s], c->R, c->L, c->lam, m, b->pq[s], b->bR[s], b->bL[s], q.y, q.ks,
-                                  q.vscale, b->part, b->counter, n, st);
+                                  q.vscale, part, cnt, n, ss);
         if (mixed) {
-            ovl::launch_native_f64_to_f32(b->bR[s], q.v[0], q.g, 1, st);
-            ovl::launch_native_f64_to_f32(b->bL[s], q.w[0], q.g, 1, st);
+            ovl::launch_native_f64_to_f32(b->bR[s], q.v[0], q.g, 1, ss);
+            ovl::launch_native_f64_to_f32(b->bL[s], q.w[0], q.g, 1, ss);
         } else {
-            cudaMemcpyAsync(q.V ? (void*)q.V : q.v[0], b->bR[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(q.w[0], b->bL[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(q.V ? (void*)q.V : q.v[0], b->bR[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, ss);
+            cudaMemcpyAsync(q.w[0], b->bL[s], n * sizeof(double2), cudaMemcpyDeviceToDevice, ss);
         }
+    }
+    for (int j = 0; j < nside; ++j) {
+        cudaEventRecord(b->ev_join[j], b->side[j]);
+        cudaStreamWaitEvent(st, b->ev_join[j], 0);
     }
     // pass 1 (all sequences per launch): one persistent launch for mixed batches that fit the GPU
     if (prof) cudaEventRecord(b->ev[0], st);
@@ -1084,6 +1123,11 @@ int ovl_batch_destroy(ovl_batch* b) {
     if (b->cap_st) cudaStreamDestroy(b->cap_st);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
+    for (int j = 0; j < ovl_batch::NSIDE; ++j) {
+        if (b->side[j]) cudaStreamDestroy(b->side[j]);
+        if (b->ev_join[j]) cudaEventDestroy(b->ev_join[j]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     delete b;
     return OVL_OK;
 }
@@ -1098,6 +1142,13 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
     for (int q = 0; q < b->nseq; ++q) ntot += b->ctx[b->seq_ctx[q]]->n;
     const bool fits = ((size_t)k + 2) * ntot * sizeof(double2) <= ((size_t)32 << 30);
     const int mode = (flags & OVL_MIXED) ? 1 : ((flags & OVL_TWO_PASS) || !fits) ? 2 : 0;
+    // a deflation set larger than the prologue scratch was laid out for: lay the workspace out again
+    if (b->mem)
+        for (int q = 0; q < b->nseq; ++q)
+            if (b->ctx[b->seq_ctx[q]]->m > b->pro_m[q]) {
+                bfree(b);
+                break;
+            }
     int r = balloc(b, mode, k);
     if (r) return r;
     for (ovl_ctx* c : b->ctx) {
