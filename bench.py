@@ -308,10 +308,16 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
-def batch_launches(nseq, k, m):
-    """Kernels one batched solve launches (pack, prologue, pass 1, inner sign, pass 2, unpack)."""
-    per_seq = 1 + 1 + (4 if m > 0 else 0) + 1 + 2 + 2 + 1 + 1  # pack, init, multidots, split, convert, Newton, start, unpack
-    return nseq * per_seq + (2 * k - 1) + 1 + 2 * 6 + (k - 1)
+def batch_launches(nseq, k, m, persistent_pass1=True):
+    """Kernels one mixed batched solve launches: per sequence pack, state init, projections (two
+    two-stage kernels), split, two FP32 conversions, the Newton fallback (two, they return at once
+    when the quadrature settled), start vector, two and one double-float conversions, unpack; then
+    pass 1 (one persistent launch, or pair + recurrence per step), the inner sign (prep, six levels
+    of solve + sum) and k - 1 regeneration steps.  755 for 12 sequences, k = 550, m = 20 (the ncu
+    launch list of one solve counts the same)."""
+    per_seq = 1 + 1 + (4 if m > 0 else 0) + 1 + 2 + 2 + 1 + 2 + 1 + 1
+    pass1 = 1 if persistent_pass1 else 2 * k - 1
+    return nseq * per_seq + pass1 + 1 + 2 * 6 + (k - 1)
 
 
 def calibrate_batch(torch, bt, srcs, refs, flags, grid):
