@@ -181,16 +181,20 @@ def make_inputs(torch, n_src, rank):
     return U, srcs
 
 
-def calibrate_k(ovl, ctx, torch, b, flags_list):
-    """Smallest k on K_GRID whose solve agrees with the FP64 k=1000 solve to 1e-8."""
+def calibrate_k(ovl, ctx, torch, b, flags_list, grid=None):
+    """Smallest k on K_GRID whose solve agrees with the FP64 k=1000 solve to 1e-8; entries of
+    flags_list are (name, flags) for two-sided Lanczos or (name, flags, method)."""
     ref, _ = ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, b)
     ref = ref.clone()
     nrm = torch.linalg.vector_norm(ref).item()
     out = {}
-    for name, fl in flags_list:
-        chosen, err = K_GRID[-1], None
-        for k in K_GRID:
-            y, info = ctx.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, b, flags=fl)
+    for entry in flags_list:
+        name, fl = entry[0], entry[1]
+        method = entry[2] if len(entry) > 2 else ovl.LANCZOS2
+        kg = grid or K_GRID
+        chosen, err = kg[-1], None
+        for k in kg:
+            y, info = ctx.sign_krylov(method, k, MU, KAPPA, b, flags=fl)
             e = torch.linalg.vector_norm(y - ref).item() / nrm
             print(f"[bench] calibrate {name} k={k} err={e:.3e}", file=sys.stderr, flush=True)
             if e <= 1e-8:
@@ -411,14 +415,17 @@ def run_ours(args, world, rank, local):
     fl_64 = ovl.OVERLAP
     # ---- accuracy calibration (untimed): every source against the FP64 k = 1000 solve
     if args.k:
-        k_mix = k_64 = k_s = k_s64 = args.k
-        err_mix = err_64 = err_s = err_s64 = None
+        k_mix = k_64 = k_s = k_s64 = k_arn = args.k
+        err_mix = err_64 = err_s = err_s64 = err_arn = None
     else:
         refs = torch.stack([ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, srcs[r])[0].clone() for r in range(NRHS)])
         k_mix, err_mix = calibrate_batch(torch, bt, srcs, refs, ovl.MIXED, K_GRID)
         k_64, err_64 = calibrate_batch(torch, bt, srcs, refs, 0, K_GRID)
         cal = calibrate_k(ovl, ctx, torch, srcs[0], [("mixed", ovl.MIXED), ("fp64", 0)])
         (k_s, err_s), (k_s64, err_s64) = cal["mixed"], cal["fp64"]
+        # Arnoldi on its own k grid (step 25: it needs a smaller subspace, Sec. 5)
+        cal_a = calibrate_k(ovl, ctx, torch, srcs[0], [("arnoldi", 0, ovl.ARNOLDI)], grid=list(range(250, 801, 25)))
+        k_arn, err_arn = cal_a["arnoldi"]
     print(f"[bench] batch k mixed={k_mix} ({err_mix}), fp64={k_64} ({err_64}); single k mixed={k_s}, fp64={k_s64}",
           file=sys.stderr, flush=True)
 
@@ -485,7 +492,7 @@ def run_ours(args, world, rank, local):
                       bsingle, 2, nctx, flush)
     t_s64 = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s64, MU, KAPPA, b, out1, flags=fl_64),
                         bsingle, 2, nctx, flush)
-    t_arn = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, min(k_s64, 600), MU, KAPPA, b, out1,
+    t_arn = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_arn, MU, KAPPA, b, out1,
                                                               flags=ovl.OVERLAP), bsingle, 1, 2, flush)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
@@ -576,7 +583,8 @@ def run_ours(args, world, rank, local):
             "fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_s64), "ms": statistics.mean(t_s64),
                                    "k": k_s64, "rel_err_vs_k1000_fp64": err_s64},
             "arnoldi_fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_arn), "ms": statistics.mean(t_arn),
-                                           "k": min(k_s64, 600)},
+                                           "k": k_arn, "rel_err_vs_k1000_fp64": err_arn,
+                                           "k_ratio_2sl_over_arnoldi": (k_s64 / k_arn) if k_arn else None},
             "profile_ms_per_batch": {kk: round(v, 4) for kk, v in prof.items()},
             "multi_lattice_batch": multi,
             "dw": dw,
