@@ -575,7 +575,8 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "mu": MU, "kappa": KAPPA, "eps": EPS,
                        "rhs_per_step": NRHS,
-                       "autotuned_shapes": {"pass1_sites_per_block": tuned[0], "regen_blocks_per_sm": tuned[1]}
+                       "autotuned_shapes": {"pass1_sites_per_block": tuned[0], "regen_blocks_per_sm": tuned[1],
+                                            "regen_sequences_per_block": tuned[2]}
                        if tuned else None,
                        "method": "batched two-sided Lanczos, two-pass mixed (FP32 pass 1, FP64 pass 2)",
                        "k": k_mix, "m_deflated": args.m, "deflation_setup": eig,

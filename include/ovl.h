@@ -199,13 +199,18 @@ int ovl_batch_solve(ovl_batch* batch, int k, double mu, double kappa, const void
  * combination; *nsolves the number of such solves.  reset != 0 clears the totals. */
 int ovl_batch_profile(ovl_batch* batch, double* ms3, int* nsolves, int reset);
 /* Launch shapes of the batched kernels.  The first solve in each precision times the candidates
- * (pass-1 site blocks of 64, 128 or 256 sites; regeneration kernel at 2, 3 or 4 blocks per SM) with
- * short eager solves of the batch itself and keeps the fastest (OVL_NO_TUNE skips this).  Writes the
- * chosen shapes; returns OVL_ESTATE before the first tuning. */
-int ovl_batch_tuning(const ovl_batch* batch, int* pass1_block_sites, int* regen_blocks_per_sm);
-/* Pins the launch shapes (pass1_block_sites 64, 128 or 256; regen_blocks_per_sm 2, 3 or 4) and
- * turns the autotuner off for this batch.  OVL_EINVAL for any other value (nothing changed). */
-int ovl_batch_set_tuning(ovl_batch* batch, int pass1_block_sites, int regen_blocks_per_sm);
+ * (pass-1 site blocks of 64, 128 or 256 sites; the regeneration kernel at 3 to 6 blocks per SM
+ * with one sequence per block, or at 2 to 4 blocks per SM with two sequences of one lattice per
+ * block) with short eager solves of the batch itself and keeps the fastest (OVL_NO_TUNE skips
+ * this).  Writes the chosen shapes (NULL pointers are skipped); returns OVL_ESTATE before the
+ * first tuning. */
+int ovl_batch_tuning(const ovl_batch* batch, int* pass1_block_sites, int* regen_blocks_per_sm,
+                     int* regen_seqs_per_block);
+/* Pins the launch shapes (pass1_block_sites 64, 128 or 256; regen_blocks_per_sm 2 to 6;
+ * regen_seqs_per_block 1 or 2) and turns the autotuner off for this batch.  OVL_EINVAL for any
+ * other value (nothing changed). */
+int ovl_batch_set_tuning(ovl_batch* batch, int pass1_block_sites, int regen_blocks_per_sm,
+                         int regen_seqs_per_block);
 /* create + solve + destroy (no graph reuse); errors are reported on ctxs[0]. */
 int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int k, double mu, double kappa,
                             const void* const* b, void* const* out, int flags, ovl_info* info);

@@ -550,6 +550,90 @@ template <class R> __device__ __forceinline__ cx<R> cvt_coef(cx<double> z);
 template <> __device__ __forceinline__ cx<double> cvt_coef<double>(cx<double> z) { return z; }
 template <> __device__ __forceinline__ cx<df> cvt_coef<df>(cx<double> z) { return mk(df(z.r), df(z.i)); }
 
+// Hop h of the double-float regeneration at site i, written straight to out[0..6) (the half
+// spinor, spins 0 and 1, colours 0..2, times the hop coefficient): the neighbour's spinor is
+// projected colour by colour and the link applied row by row (U) or column by column (U^dag), so
+// that only the projected half spinor, one link row and two accumulators are live at a time (few
+// registers: more blocks per SM).  The operations and their order are those of hop_half_uniform
+// with mul_link / mul_link_dag, so the results are the same.
+__device__ __forceinline__ void hop_half_rows_df(int h, const Geom& g, const Coord& c, int i, const dfc* __restrict__ U,
+                                                 const dfc* __restrict__ x, const HopCoef<df>& hc,
+                                                 cx<df>* __restrict__ out) {
+    const int nu = h & 3;
+    const bool fwd = h < 4;
+    int y[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        int v = c.x[d];
+        if (d == nu) {
+            v += fwd ? 1 : -1;
+            if (v == g.L[d]) v = 0;
+            if (v < 0) v = g.L[d] - 1;
+        }
+        y[d] = v;
+    }
+    const int nb = internal_index(g, y);
+    const bool edge = fwd ? (c.x[3] == g.L[3] - 1) : (c.x[3] == 0);
+    const df ph = (nu == 3 && edge) ? df(g.bc_t) : df(1);
+    const bool hi2 = nu >= 2, im = (nu & 1) == 0;
+    const bool n0 = (nu == 3) ? !fwd : fwd;
+    const bool n1 = (nu == 0) ? fwd : !fwd;
+    const float4* xv = reinterpret_cast<const float4*>(x);
+    const size_t V = (size_t)g.V;
+    auto ldx = [&](int q) {
+        const float4 v = __ldg(xv + (size_t)q * V + nb);
+        return mk(df(v.x, v.y), df(v.z, v.w));
+    };
+    Half<df> hh;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const cx<df> p0 = ldx(a), p1 = ldx(3 + a), p2 = ldx(6 + a), p3 = ldx(9 + a);
+        hh.h[0][a] = add_lazy(p0, unit_mul(hi2 ? p2 : p3, im, n0));
+        hh.h[1][a] = add_lazy(p1, unit_mul(hi2 ? p3 : p2, im, n1));
+    }
+    const df cf = (fwd ? (nu == 3 ? hc.f[3] : hc.f[0]) : (nu == 3 ? hc.b[3] : hc.b[0])) * ph;
+    const float4* uv = reinterpret_cast<const float4*>(U) + (size_t)nu * 9 * V + (fwd ? i : nb);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<df> u[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = __ldg(uv + (size_t)(fwd ? 3 * a + k : 3 * k + a) * V);
+            u[k] = mk(df(v.x, v.y), df(v.z, v.w));
+        }
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            dfacc re, imv;
+            if (fwd) {  // U h: re = sum ur hr - ui hi, im = sum ur hi + ui hr
+                dfacc_first(re, u[0].r, hh.h[sp][0].r, false);
+                dfacc_add(re, u[0].i, hh.h[sp][0].i, true);
+                dfacc_first(imv, u[0].r, hh.h[sp][0].i, false);
+                dfacc_add(imv, u[0].i, hh.h[sp][0].r, false);
+#pragma unroll
+                for (int k = 1; k < 3; ++k) {
+                    dfacc_add(re, u[k].r, hh.h[sp][k].r, false);
+                    dfacc_add(re, u[k].i, hh.h[sp][k].i, true);
+                    dfacc_add(imv, u[k].r, hh.h[sp][k].i, false);
+                    dfacc_add(imv, u[k].i, hh.h[sp][k].r, false);
+                }
+            } else {  // U^dag h: re = sum ur hr + ui hi, im = sum ur hi - ui hr
+                dfacc_first(re, u[0].r, hh.h[sp][0].r, false);
+                dfacc_add(re, u[0].i, hh.h[sp][0].i, false);
+                dfacc_first(imv, u[0].r, hh.h[sp][0].i, false);
+                dfacc_add(imv, u[0].i, hh.h[sp][0].r, true);
+#pragma unroll
+                for (int k = 1; k < 3; ++k) {
+                    dfacc_add(re, u[k].r, hh.h[sp][k].r, false);
+                    dfacc_add(re, u[k].i, hh.h[sp][k].i, false);
+                    dfacc_add(imv, u[k].r, hh.h[sp][k].i, false);
+                    dfacc_add(imv, u[k].i, hh.h[sp][k].r, true);
+                }
+            }
+            out[3 * sp + a] = cf * mk(dfacc_value(re), dfacc_value(imv));
+        }
+    }
+}
+
 template <class R, int LF, int MINB>
 __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict__ S, const int* __restrict__ tseq, int i,
                                                     HopCoef<R> hc) {
@@ -577,12 +661,16 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
         const int i0 = tile * TT + lane;
         if (i0 < q.g.V) {
             const Coord c = site_coord(q.g, i0);
-            const VT* const xs[1] = {ri};
-            const HopCoef<R> hcs[1] = {hc};
-            Half<R> hp[1];
-            hop_half_uniform<LF, R, 1>(wid, q.g, c, i0, U, xs, hp, hcs);
+            if constexpr (LF == LINK_DF) {
+                hop_half_rows_df(wid, q.g, c, i0, (const dfc*)U, (const dfc*)ri, hc, dirpart[wid][lane]);
+            } else {
+                const VT* const xs[1] = {ri};
+                const HopCoef<R> hcs[1] = {hc};
+                Half<R> hp[1];
+                hop_half_uniform<LF, R, 1>(wid, q.g, c, i0, U, xs, hp, hcs);
 #pragma unroll
-            for (int c6 = 0; c6 < 6; ++c6) dirpart[wid][lane][c6] = hp[0].h[c6 / 3][c6 % 3];
+                for (int c6 = 0; c6 < 6; ++c6) dirpart[wid][lane][c6] = hp[0].h[c6 / 3][c6 % 3];
+            }
         }
     }
     __syncthreads();
@@ -610,6 +698,88 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
     }
 }
 
+// The regeneration step for two sequences of the same lattice per block (work entry: the two
+// sequences, the tile, whether the second one exists): each hop warp loads the link and computes
+// the neighbour index once and runs the two sequences' double-float products as independent chains
+// (twice the work in flight per warp); the epilogue spreads the 2 x 32 sites x 12 components over
+// the 256 threads, three each.  Same arithmetic per sequence as k_b_regen.
+template <class R, int LF, int MINB>
+__global__ void __launch_bounds__(8 * TT, MINB) k_b_regen2(const BSeq* __restrict__ S, const int4* __restrict__ work,
+                                                     int i, HopCoef<R> hc) {
+    using VT = typename VecT<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R>(*dirpart)[8][TT][6] = reinterpret_cast<cx<R>(*)[8][TT][6]>(smraw);  // [2][8][TT][6]
+    __shared__ cx<R> cf[2][4];
+    const int4 wk = work[blockIdx.x];  // set-up data, not written by the solve
+    const BSeq& qa = S[wk.x];
+    const BSeq& qb = S[wk.y];
+    const bool two = wk.w != 0;
+    pdl_wait_and_release();
+    const bool la = !(qa.ks->status || i + 1 >= qa.ks->kused);
+    const bool lb = two && !(qb.ks->status || i + 1 >= qb.ks->kused);
+    if (!la && !lb) return;
+    if (threadIdx.x < 2 && (threadIdx.x == 0 || two)) {
+        const BSeq& q = threadIdx.x ? qb : qa;
+        const cx<double> ib = cdiv(mk(1.0, 0.0), d2c(q.beta[i]));
+        cf[threadIdx.x][0] = cvt_coef<R>(ib);
+        cf[threadIdx.x][1] = cvt_coef<R>(ib * d2c(q.alpha[i]));
+        cf[threadIdx.x][2] = cvt_coef<R>(i > 0 ? ib * d2c(q.gamma[i - 1]) : mk(0.0, 0.0));
+        cf[threadIdx.x][3] = cvt_coef<R>(d2c(q.cvec[i + 1]));
+    }
+    const int tile = wk.z;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const Geom& g = qa.g;
+    const VT* ra = (const VT*)qa.r[i % 3];
+    const VT* rb = two ? (const VT*)qb.r[i % 3] : ra;
+    const void* U = LF == LINK_DF ? qa.Udf : (const void*)qa.U64;
+    {
+        const int i0 = tile * TT + lane;
+        if (i0 < g.V) {
+            const Coord c = site_coord(g, i0);
+            if constexpr (LF == LINK_DF) {
+                hop_half_rows_df(wid, g, c, i0, (const dfc*)U, (const dfc*)ra, hc, dirpart[0][wid][lane]);
+                hop_half_rows_df(wid, g, c, i0, (const dfc*)U, (const dfc*)rb, hc, dirpart[1][wid][lane]);
+            } else {
+                const VT* const xs[2] = {ra, rb};
+                const HopCoef<R> hcs[2] = {hc, hc};
+                Half<R> hp[2];
+                hop_half_uniform<LF, R, 2>(wid, g, c, i0, U, xs, hp, hcs);
+#pragma unroll
+                for (int c6 = 0; c6 < 6; ++c6) {
+                    dirpart[0][wid][lane][c6] = hp[0].h[c6 / 3][c6 % 3];
+                    dirpart[1][wid][lane][c6] = hp[1].h[c6 / 3][c6 % 3];
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr) {
+        const int task = threadIdx.x + rr * 8 * TT;
+        const int sq = task / (TT * 12), rem = task % (TT * 12);
+        const int site = rem / 12, c = rem % 12;
+        if (sq ? !lb : !la) continue;
+        const BSeq& q = sq ? qb : qa;
+        const int ii = tile * TT + site;
+        if (ii >= g.V) continue;
+        const VT* ri = sq ? rb : ra;
+        const VT* rm = (const VT*)q.r[(i + 2) % 3];
+        VT* rn = (VT*)q.r[(i + 1) % 3];
+        VT* y = (VT*)q.y;
+        const cx<R> self = ld_comp_cg<R>(ri, g.V, ii, c);
+        cx<R> z = self;
+        const int sp = c / 3, a = c % 3;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            z = add_lazy(z, hop_spin<R>(w, sp, dirpart[sq][w][site][a], dirpart[sq][w][site][3 + a]));
+        if (c >= 6) z = -z;  // gamma5: spins 2, 3
+        z = cf[sq][0] * z - cf[sq][1] * self;
+        if (i > 0) z = z - cf[sq][2] * ld_comp_cg<R>(rm, g.V, ii, c);
+        st_comp<R>(rn, g.V, ii, c, z);
+        st_comp<R>(y, g.V, ii, c, ld_comp_cg<R>(y, g.V, ii, c) + cf[sq][3] * z);
+    }
+}
+
 }  // namespace
 }  // namespace ovl
 
@@ -629,6 +799,8 @@ struct ovl_batch {
     ovl::BSeq* dseq = nullptr;
     int* dbseq[ovl::NSHAPE] = {nullptr, nullptr, nullptr};
     int* dtseq = nullptr;
+    int4* dpair = nullptr;         // regeneration work of two sequences per block: (a, b, tile, two)
+    int npair_blocks = 0;
     unsigned int* pbar = nullptr;  // per-sequence barrier counters of the persistent pass 1
     int bp1_fit = -1;              // persistent pass 1 fits the GPU (-1: not yet determined)
     int nblocks[ovl::NSHAPE] = {0, 0, 0};
@@ -636,6 +808,7 @@ struct ovl_batch {
     // autotuned launch shapes: pass-1 site-block shape, blocks per SM of the regeneration kernel
     int shape = 1;
     int regen_minb = 3;
+    int regen_pair = 0;         // 1: two sequences of one lattice per regeneration block
     bool tuned = false;
     bool pinned = false;        // shapes set by ovl_batch_set_tuning: never retuned
     int tuned_mode = -1;
@@ -718,6 +891,20 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     }
     // prologue scratch per sequence: the two-stage projections' partials (m vectors x blocks,
     // complex) or the deflation split's grid sum (4 values x at most 512 blocks)
+    // two sequences of one lattice per regeneration block (the sources of a context are consecutive)
+    std::vector<int4> ptable;
+    {
+        int s0 = 0;
+        for (size_t j = 0; j < b->ctx.size(); ++j) {
+            const int nt = (b->ctx[j]->g.V + ovl::TT - 1) / ovl::TT;
+            for (int r = 0; r < b->nrhs[j]; r += 2) {
+                const int sa = s0 + r, two = r + 1 < b->nrhs[j];
+                const int sb = two ? sa + 1 : sa;
+                for (int t = 0; t < nt; ++t) ptable.push_back(make_int4(sa, sb, t, two));
+            }
+            s0 += b->nrhs[j];
+        }
+    }
     std::vector<size_t> pro_off(ns + 1, 0);
     std::vector<int> pro_m(ns, 0);
     for (int s = 0; s < ns; ++s) {
@@ -730,7 +917,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
              al((size_t)ns * inner_stride * sizeof(double2)) + al((size_t)ns * qpart_stride * sizeof(double)) +
              al(ns * 64 * sizeof(unsigned int)) + al(ns * sizeof(ovl::BSeq)) + al(nblocks[0] * sizeof(int)) +
              al(nblocks[1] * sizeof(int)) + al(nblocks[2] * sizeof(int)) +
-             al(ntiles * sizeof(int)) + al(ns * sizeof(unsigned int)) +
+             al(ntiles * sizeof(int)) + al(ns * sizeof(unsigned int)) + al(ptable.size() * sizeof(int4)) +
              al(pro_off[ns] * sizeof(double)) + al(64 * sizeof(unsigned int));
     if (cudaMalloc(&b->mem, total) != cudaSuccess) {
         b->mem = nullptr;
@@ -754,6 +941,8 @@ int balloc(ovl_batch* b, int mode, int kmax) {
     for (int h = 0; h < ovl::NSHAPE; ++h) b->dbseq[h] = (int*)take(nblocks[h] * sizeof(int));
     b->dtseq = (int*)take(ntiles * sizeof(int));
     b->pbar = (unsigned int*)take(ns * sizeof(unsigned int));
+    b->dpair = (int4*)take(ptable.size() * sizeof(int4));
+    b->npair_blocks = (int)ptable.size();
     b->part = (double*)take(pro_off[ns] * sizeof(double));
     b->pro_off = pro_off;
     b->pro_m = pro_m;
@@ -821,6 +1010,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         cudaMemcpy(b->dbseq[1], table[1].data(), table[1].size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dbseq[2], table[2].data(), table[2].size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dtseq, ttable.data(), ttable.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->dpair, ptable.data(), ptable.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->qcnt, 0, ns * 64 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(b->counter, 0, 64 * sizeof(unsigned int)) != cudaSuccess) {
         bfree(b);
@@ -898,7 +1088,7 @@ void pass1_step(ovl_batch* b, int i, int k, double mu, double kappa, bool mixed,
     }
 }
 
-// One regeneration step of every sequence, blocks-per-SM bound MINB.
+// One regeneration step of every sequence, blocks-per-SM bound MINB (one or two sequences per block).
 template <int MINB>
 void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStream_t st) {
     const size_t smr = (size_t)8 * ovl::TT * 6 * 16;
@@ -908,9 +1098,22 @@ void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStre
                              (int)smr);
         cudaFuncSetAttribute(ovl::k_b_regen<double, ovl::LINK_F64, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        cudaFuncSetAttribute(ovl::k_b_regen2<ovl::df, ovl::LINK_DF, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smr));
+        cudaFuncSetAttribute(ovl::k_b_regen2<double, ovl::LINK_F64, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smr));
         attr = true;
     }
     const ovl::BSeq* S = b->dseq;
+    if (b->regen_pair) {
+        if (dfm)
+            launch_pdl(ovl::k_b_regen2<ovl::df, ovl::LINK_DF, MINB>, b->npair_blocks, 8 * ovl::TT, 2 * smr, st, S,
+                       (const int4*)b->dpair, i, ovl::make_coef<ovl::df>(mu, kappa));
+        else
+            launch_pdl(ovl::k_b_regen2<double, ovl::LINK_F64, MINB>, b->npair_blocks, 8 * ovl::TT, 2 * smr, st, S,
+                       (const int4*)b->dpair, i, ovl::make_coef<double>(mu, kappa));
+        return;
+    }
     const int* tab = b->dtseq;
     if (dfm)
         launch_pdl(ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB>, b->ntiles, 8 * ovl::TT, smr, st, S, tab, i,
@@ -1010,6 +1213,8 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
             switch (b->regen_minb) {
                 case 2: regen_step<2>(b, i, mu, kappa, dfm, st); break;
                 case 4: regen_step<4>(b, i, mu, kappa, dfm, st); break;
+                case 5: regen_step<5>(b, i, mu, kappa, dfm, st); break;
+                case 6: regen_step<6>(b, i, mu, kappa, dfm, st); break;
                 default: regen_step<3>(b, i, mu, kappa, dfm, st); break;
             }
         }
@@ -1035,13 +1240,19 @@ int autotune(ovl_batch* b, double mu, double kappa, int flags, cudaStream_t st) 
     const int saved_shape = b->shape, saved_minb = b->regen_minb;
     for (cudaEvent_t& e : b->ev)
         if (!e && cudaEventCreate(&e) != cudaSuccess) return bfail(b, OVL_ECUDA, "tuning events");
-    const int minbs[ovl::NSHAPE] = {2, 3, 4};
+    // candidates: pass-1 site-block shape, regeneration blocks per SM, sequences per regeneration block
+    struct Cand {
+        int shape, minb, pair;
+    };
+    const Cand cands[] = {{0, 3, 0}, {1, 4, 0}, {2, 5, 0}, {1, 6, 0}, {1, 2, 1}, {1, 3, 1}, {1, 4, 1}};
+    const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
     float best1 = 1e30f, best2 = 1e30f;
-    int bs = saved_shape, bm = saved_minb;
+    int bs = saved_shape, bm = saved_minb, bp = b->regen_pair;
     for (int rep = 0; rep < 2; ++rep)  // the first round warms caches and instruction memory
-        for (int c = 0; c < ovl::NSHAPE; ++c) {
-            b->shape = c;
-            b->regen_minb = minbs[c];
+        for (int c = 0; c < ncand; ++c) {
+            b->shape = cands[c].shape;
+            b->regen_minb = cands[c].minb;
+            b->regen_pair = cands[c].pair;
             const int r = enqueue_batch(b, TUNE_K, mu, kappa, (flags | OVL_PROFILE) & ~OVL_NO_GRAPH, st);
             if (r) return r;
             if (cudaStreamSynchronize(st) != cudaSuccess) return bfail(b, OVL_ECUDA, "tuning solve");
@@ -1049,12 +1260,13 @@ int autotune(ovl_batch* b, double mu, double kappa, int flags, cudaStream_t st) 
             cudaEventElapsedTime(&t1, b->ev[0], b->ev[1]);
             cudaEventElapsedTime(&t2, b->ev[2], b->ev[3]);
             if (rep == 1) {
-                if (t1 < best1) best1 = t1, bs = c;
-                if (t2 < best2) best2 = t2, bm = minbs[c];
+                if (t1 < best1) best1 = t1, bs = cands[c].shape;
+                if (t2 < best2) best2 = t2, bm = cands[c].minb, bp = cands[c].pair;
             }
         }
     b->shape = bs;
     b->regen_minb = bm;
+    b->regen_pair = bp;
     b->tuned = true;
     b->tuned_mode = b->mode;
     if (b->exec) cudaGraphExecDestroy(b->exec);  // a captured graph holds the old shapes
@@ -1066,22 +1278,25 @@ int autotune(ovl_batch* b, double mu, double kappa, int flags, cudaStream_t st) 
 
 extern "C" {
 
-int ovl_batch_tuning(const ovl_batch* b, int* pass1_block_sites, int* regen_blocks_per_sm) {
+int ovl_batch_tuning(const ovl_batch* b, int* pass1_block_sites, int* regen_blocks_per_sm, int* regen_seqs_per_block) {
     if (!b) return OVL_EINVAL;
     if (pass1_block_sites) *pass1_block_sites = ovl::SHAPE_SITES[b->shape];
     if (regen_blocks_per_sm) *regen_blocks_per_sm = b->regen_minb;
+    if (regen_seqs_per_block) *regen_seqs_per_block = b->regen_pair ? 2 : 1;
     return b->tuned ? OVL_OK : OVL_ESTATE;
 }
 
-int ovl_batch_set_tuning(ovl_batch* b, int pass1_block_sites, int regen_blocks_per_sm) {
+int ovl_batch_set_tuning(ovl_batch* b, int pass1_block_sites, int regen_blocks_per_sm, int regen_seqs_per_block) {
     if (!b) return OVL_EINVAL;
     int sh = -1;
     for (int c = 0; c < ovl::NSHAPE; ++c)
         if (ovl::SHAPE_SITES[c] == pass1_block_sites) sh = c;
-    if (sh < 0 || regen_blocks_per_sm < 2 || regen_blocks_per_sm > 4)
+    if (sh < 0 || regen_blocks_per_sm < 2 || regen_blocks_per_sm > 6 || regen_seqs_per_block < 1 ||
+        regen_seqs_per_block > 2)
         return bfail(b, OVL_EINVAL, "unsupported launch shape");
     b->shape = sh;
     b->regen_minb = regen_blocks_per_sm;
+    b->regen_pair = regen_seqs_per_block == 2;
     b->tuned = b->pinned = true;
     if (b->exec) cudaGraphExecDestroy(b->exec);  // a captured graph holds the old shapes
     b->exec = nullptr;

@@ -105,8 +105,8 @@ def load(path: str = LIB_PATH):
         "ovl_batch_last_error": (ctypes.c_char_p, [P]),
         "ovl_batch_solve": (I, [P, I, D, D, ctypes.POINTER(P), ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
         "ovl_batch_profile": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
-        "ovl_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
-        "ovl_batch_set_tuning": (I, [P, I, I]),
+        "ovl_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ovl_batch_set_tuning": (I, [P, I, I, I]),
         "ovl_sign_krylov_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, D, D, ctypes.POINTER(P),
                                         ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
     }
@@ -383,14 +383,16 @@ class Batch:
         return {"pass1": ms[0], "inner_sign": ms[1], "pass2_or_combine": ms[2]}, n.value
 
     def tuning(self):
-        """(pass-1 sites per block, regeneration blocks per SM) chosen by the autotuner, or None."""
-        a, b = ctypes.c_int(), ctypes.c_int()
-        r = self._lib.ovl_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(b))
-        return (a.value, b.value) if r == 0 else None
+        """(pass-1 sites per block, regeneration blocks per SM, sequences per regeneration block) chosen
+        by the autotuner, or None."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        r = self._lib.ovl_batch_tuning(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return (a.value, b.value, c.value) if r == 0 else None
 
-    def set_tuning(self, pass1_block_sites: int, regen_blocks_per_sm: int):
-        """Pin the launch shapes (64/128/256 sites per pass-1 block, 2/3/4 regeneration blocks per SM);
-        the autotuner is then skipped."""
-        r = self._lib.ovl_batch_set_tuning(self._h, int(pass1_block_sites), int(regen_blocks_per_sm))
+    def set_tuning(self, pass1_block_sites: int, regen_blocks_per_sm: int, regen_seqs_per_block: int = 1):
+        """Pin the launch shapes (64/128/256 sites per pass-1 block, 2..6 regeneration blocks per SM,
+        1/2 sequences per regeneration block); the autotuner is then skipped."""
+        r = self._lib.ovl_batch_set_tuning(self._h, int(pass1_block_sites), int(regen_blocks_per_sm),
+                                           int(regen_seqs_per_block))
         if r:
             raise OvlError(r, self._lib.ovl_batch_last_error(self._h).decode())

@@ -215,8 +215,8 @@ def test_batch_autotuner_picks_shapes(ovl, small):
     bt = ovl.Batch([c], [2])
     assert bt.tuning() is None
     y1 = bt.solve(25, small["mu"], KAPPA, [b])[0][0].cpu().numpy()
-    sites, minb = bt.tuning()
-    assert sites in (64, 128, 256) and minb in (2, 3, 4)
+    sites, minb, seqs = bt.tuning()
+    assert sites in (64, 128, 256) and minb in (2, 3, 4, 5, 6) and seqs in (1, 2)
     bt2 = ovl.Batch([c], [2])
     y2 = bt2.solve(25, small["mu"], KAPPA, [b], flags=ovl.NO_TUNE)[0][0].cpu().numpy()
     assert bt2.tuning() is None
@@ -227,16 +227,17 @@ def test_batch_autotuner_picks_shapes(ovl, small):
     bt2.close()
 
 
-@pytest.mark.parametrize("sites,minb", [(64, 2), (128, 3), (256, 4), (64, 4), (256, 2)])
-def test_batch_every_pinned_shape(ovl, small, mid, sites, minb):
+@pytest.mark.parametrize("sites,minb,seqs", [(64, 2, 1), (128, 3, 1), (256, 4, 1), (64, 5, 1), (256, 6, 1),
+                                             (128, 2, 2), (128, 3, 2), (64, 4, 2)])
+def test_batch_every_pinned_shape(ovl, small, mid, sites, minb, seqs):
     """Each pinned launch shape: FP64 two-pass at k = 25 against the oracle's two-sided Lanczos on
     a lattice smaller than one block, and mixed precision on two lattices against the dense sign."""
     dims, U = small["dims"], small["U"]
     c = _ctx(ovl, dims, U)
     b = _sources(dims, 4100, 3)
     bt = ovl.Batch([c], [3])
-    bt.set_tuning(sites, minb)
-    assert bt.tuning() == (sites, minb)
+    bt.set_tuning(sites, minb, seqs)
+    assert bt.tuning() == (sites, minb, seqs)
     y = bt.solve(25, small["mu"], KAPPA, [torch_c128(b)], flags=ovl.TWO_PASS)[0][0].cpu().numpy()
     for r in range(3):
         assert rel(y[r], _oracle_2sl(small, b[r], 25)) < 1e-11, r
@@ -244,14 +245,29 @@ def test_batch_every_pinned_shape(ovl, small, mid, sites, minb):
     c4 = config4()
     ca, cb = _ctx(ovl, c4["dims"], c4["U"]), _ctx(ovl, mid["dims"], mid["U"])
     ba, bb = _sources(c4["dims"], 4101, 2), _sources(mid["dims"], 4102, 2)
-    bt = ovl.Batch([ca, cb], [2, 2])
-    bt.set_tuning(sites, minb)
+    bt = ovl.Batch([ca, cb], [2, 3])
+    bt.set_tuning(sites, minb, seqs)
+    bb = _sources(mid["dims"], 4102, 3)
     outs, _, st = bt.solve(500, c4["mu"], KAPPA, [torch_c128(ba), torch_c128(bb)], flags=ovl.MIXED)
-    assert st == 0 and bt.tuning() == (sites, minb)
+    assert st == 0 and bt.tuning() == (sites, minb, seqs)
     sgn4 = c4["X"] @ (S.csign(c4["lam"])[:, None] * c4["Xi"])
     for r in range(2):
         assert rel(outs[0][r].cpu().numpy(), sgn4 @ ba[r]) < 1e-8
+    for r in range(3):  # an odd count: the last sequence has no partner in the two-sequence blocks
         assert rel(outs[1][r].cpu().numpy(), mid["sgn"] @ bb[r]) < 1e-8
+    bt.close()
+
+
+def test_batch_two_sequence_regeneration_equals_one(ovl, mid):
+    """Two sequences per regeneration block do each sequence's arithmetic as one per block."""
+    c = _ctx(ovl, mid["dims"], mid["U"])
+    b = torch_c128(_sources(mid["dims"], 4300, 5))
+    bt = ovl.Batch([c], [5])
+    bt.set_tuning(128, 2, 1)
+    y1 = bt.solve(300, mid["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    bt.set_tuning(128, 2, 2)
+    y2 = bt.solve(300, mid["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    assert np.array_equal(y1, y2)
     bt.close()
 
 
@@ -261,7 +277,9 @@ def test_batch_rejects_unknown_shape(ovl, small):
     with pytest.raises(ovl.OvlError):
         bt.set_tuning(96, 3)
     with pytest.raises(ovl.OvlError):
-        bt.set_tuning(128, 5)
+        bt.set_tuning(128, 7)
+    with pytest.raises(ovl.OvlError):
+        bt.set_tuning(128, 3, 3)
     assert bt.tuning() is None
     bt.close()
 
