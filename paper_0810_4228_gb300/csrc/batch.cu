@@ -393,6 +393,12 @@ __device__ __forceinline__ void bp1_seq_sum(const double2* part, int nblk, doubl
 
 __device__ __forceinline__ cx<float> f32c(cx<double> z) { return mk((float)z.r, (float)z.i); }
 
+struct BP1Scalars {
+    cx<double> sv, sw, svp, swp, beta_prev, gamma_prev;
+    double anorm;
+    int kused, bd;
+};
+
 template <int LF>
 __global__ void __launch_bounds__(BP1_T, 3) k_bp1(BP1Args a) {
     const int sidx = a.bseq[blockIdx.x];
@@ -412,13 +418,15 @@ __global__ void __launch_bounds__(BP1_T, 3) k_bp1(BP1Args a) {
     double2* partA = q.part;
     double2* partC = q.part + (size_t)nblk * 4;
     // recurrence scalars in FP64, meaningful in thread 0 (identical in every block of the sequence)
-    cx<double> sv = d2c(ks->sv), sw = d2c(ks->sw), svp = d2c(ks->svp), swp = d2c(ks->swp);
-    cx<double> beta_prev = mk(0.0, 0.0), gamma_prev = mk(0.0, 0.0);
-    double anorm = ks->anorm;
-    int kused = 0, bd = -1;
+    // recurrence scalars in FP64, used by thread 0 only (shared: no registers in the other threads)
+    __shared__ BP1Scalars sc;
     if (threadIdx.x == 0) {
-        cs[0] = f32c(sv);
-        cs[1] = f32c(sw);
+        sc.sv = d2c(ks->sv), sc.sw = d2c(ks->sw), sc.svp = d2c(ks->svp), sc.swp = d2c(ks->swp);
+        sc.beta_prev = mk(0.0, 0.0), sc.gamma_prev = mk(0.0, 0.0);
+        sc.anorm = ks->anorm;
+        sc.kused = 0, sc.bd = -1;
+        cs[0] = f32c(sc.sv);
+        cs[1] = f32c(sc.sw);
     }
     __syncthreads();
     unsigned int nb = 0;
@@ -455,14 +463,14 @@ __global__ void __launch_bounds__(BP1_T, 3) k_bp1(BP1Args a) {
         if (*(volatile int*)err) return;
         bp1_seq_sum<3>(partA, nblk, osum);
         if (threadIdx.x == 0) {
-            const cx<double> alpha = cdot(sw, mk(osum[0], osum[1]));  // conj(sw) w~^dag t
-            anorm = fmax(anorm, sqrt(osum[2]));
-            kused = i + 1;
+            const cx<double> alpha = cdot(sc.sw, mk(osum[0], osum[1]));  // conj(sw) w~^dag t
+            sc.anorm = fmax(sc.anorm, sqrt(osum[2]));
+            sc.kused = i + 1;
             if (local == 0) q.alpha[i] = c2d(alpha);
-            cc[0] = f32c(alpha * sv);
-            cc[1] = f32c(conj(alpha) * sw);
-            cc[2] = f32c(i > 0 ? gamma_prev * svp : mk(0.0, 0.0));
-            cc[3] = f32c(i > 0 ? conj(beta_prev) * swp : mk(0.0, 0.0));
+            cc[0] = f32c(alpha * sc.sv);
+            cc[1] = f32c(conj(alpha) * sc.sw);
+            cc[2] = f32c(i > 0 ? sc.gamma_prev * sc.svp : mk(0.0, 0.0));
+            cc[3] = f32c(i > 0 ? conj(sc.beta_prev) * sc.swp : mk(0.0, 0.0));
         }
         if (i == a.k - 1) break;
         __syncthreads();
@@ -504,26 +512,26 @@ __global__ void __launch_bounds__(BP1_T, 3) k_bp1(BP1Args a) {
             const double nv = sqrt(osum[2]), nw = sqrt(osum[3]);
             const cx<double> delta = mk(osum[0], osum[1]);
             int dn = 0;
-            if (nv <= 1e-13 * fmax(anorm, 1e-300)) {
+            if (nv <= 1e-13 * fmax(sc.anorm, 1e-300)) {
                 dn = 1;  // lucky breakdown
             } else if (sqrt(norm2(delta)) <= 1e-14 * nv * nw) {
                 dn = 1;  // serious breakdown
-                bd = i + 1;
+                sc.bd = i + 1;
             } else {
                 const cx<double> gm = mk(osum[0] / nv, osum[1] / nv);
-                beta_prev = mk(nv, 0.0);
-                gamma_prev = gm;
-                svp = sv;
-                swp = sw;
-                sv = mk(1.0 / nv, 0.0);
-                sw = cdiv(mk(1.0, 0.0), conj(gm));
+                sc.beta_prev = mk(nv, 0.0);
+                sc.gamma_prev = gm;
+                sc.svp = sc.sv;
+                sc.swp = sc.sw;
+                sc.sv = mk(1.0 / nv, 0.0);
+                sc.sw = cdiv(mk(1.0, 0.0), conj(gm));
                 if (local == 0) {
                     q.beta[i] = make_double2(nv, 0.0);
                     q.gamma[i] = c2d(gm);
-                    q.vscale[i + 1] = c2d(sv);
+                    q.vscale[i + 1] = c2d(sc.sv);
                 }
-                cs[0] = f32c(sv);
-                cs[1] = f32c(sw);
+                cs[0] = f32c(sc.sv);
+                cs[1] = f32c(sc.sw);
             }
             sdone = dn;
         }
@@ -531,14 +539,14 @@ __global__ void __launch_bounds__(BP1_T, 3) k_bp1(BP1Args a) {
         if (sdone) break;
     }
     if (local == 0 && threadIdx.x == 0) {
-        ks->kused = kused;
+        ks->kused = sc.kused;
         ks->done = 1;
-        ks->anorm = anorm;
-        if (bd >= 0) ks->bdstep = bd;
-        ks->sv = c2d(sv);
-        ks->sw = c2d(sw);
-        ks->svp = c2d(svp);
-        ks->swp = c2d(swp);
+        ks->anorm = sc.anorm;
+        if (sc.bd >= 0) ks->bdstep = sc.bd;
+        ks->sv = c2d(sc.sv);
+        ks->sw = c2d(sc.sw);
+        ks->svp = c2d(sc.svp);
+        ks->swp = c2d(sc.swp);
     }
 }
 
