@@ -51,8 +51,8 @@ WORKLOAD = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3, 
             "two-sided Lanczos, 20 eigenvalues of smallest |Re lambda| deflated")
 MULTI_DIMS = [(6, 6, 6, 6), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 8)]
 MULTI_MU, MULTI_K, MULTI_M = 0.2, 700, 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_b_regen launch (12 x 8^4 sequences), mean of 3
-REGEN_DRAM_BYTES_PER_LAUNCH = 32445696
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_b_regen launch (12 x 8^4 sequences), steady-state mean
+REGEN_DRAM_BYTES_PER_LAUNCH = 30998400
 
 
 def peaks():
