@@ -80,9 +80,10 @@ PASS1_BYTES_SITE = 768
 # step per site, counted from the arithmetic of df32.cuh in the kernel: per hop the projection
 # (12 unnormalised double-float sums x 8), the link product (6 complex outputs x 134: one exact
 # product of 4 operations and 11 compensated terms of 12, two renormalisations of 3), the
-# coefficient (13 double-float products x 7); per output component the hop sum (16 x 8), four
-# complex double-float products (50 each) and three complex sums (22 each)
-REGEN_DF_OPS_SITE = 8 * (12 * 8 + 6 * 134 + 13 * 7) + 12 * (16 * 8 + 4 * 50 + 3 * 22)
+# coefficient (13 double-float products x 7); per output component the hop sum (16 x 8), the real
+# 1/beta_i times a complex number (2 x 7), three complex double-float products (50 each) and three
+# complex sums (22 each)
+REGEN_DF_OPS_SITE = 8 * (12 * 8 + 6 * 134 + 13 * 7) + 12 * (16 * 8 + 2 * 7 + 3 * 50 + 3 * 22)
 # FP32 issue rate: 152 SMs x 128 lanes x 2.07 GHz (one operation per lane and clock)
 FP32_OPS_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 # FP64 pass-2 step: links (576) + v_i (192) + v_{i-1} (192) + v_{i+1} write (192) + y read/write (384)

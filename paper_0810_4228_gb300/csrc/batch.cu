@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
 #pragma unroll
         for (int w = 0; w < 8; ++w) z = add_lazy(z, hop_spin<R>(w, sp, dirpart[w][site][a], dirpart[w][site][3 + a]));
         if (c >= 6) z = -z;  // gamma5: spins 2, 3
-        z = cf[0] * z - cf[1] * self;
+        z = mk(cf[0].r * z.r, cf[0].r * z.i) - cf[1] * self;  // 1 / beta_i is real
         if (i > 0) z = z - cf[2] * ld_comp_cg<R>(rm, q.g.V, ii, c);
         st_comp<R>(rn, q.g.V, ii, c, z);
         st_comp<R>(y, q.g.V, ii, c, ld_comp_cg<R>(y, q.g.V, ii, c) + cf[3] * z);
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen2(const BSeq* __restric
         for (int w = 0; w < 8; ++w)
             z = add_lazy(z, hop_spin<R>(w, sp, dirpart[sq][w][site][a], dirpart[sq][w][site][3 + a]));
         if (c >= 6) z = -z;  // gamma5: spins 2, 3
-        z = cf[sq][0] * z - cf[sq][1] * self;
+        z = mk(cf[sq][0].r * z.r, cf[sq][0].r * z.i) - cf[sq][1] * self;  // 1 / beta_i is real
         if (i > 0) z = z - cf[sq][2] * ld_comp_cg<R>(rm, g.V, ii, c);
         st_comp<R>(rn, g.V, ii, c, z);
         st_comp<R>(y, g.V, ii, c, ld_comp_cg<R>(y, g.V, ii, c) + cf[sq][3] * z);
