@@ -425,8 +425,8 @@ def run_ours(args, world, rank, local):
     fl_64 = ovl.OVERLAP
     # ---- accuracy calibration (untimed): every source against the FP64 k = 1000 solve
     if args.k:
-        k_mix = k_64 = k_s = k_s64 = k_arn = args.k
-        err_mix = err_64 = err_s = err_s64 = err_arn = None
+        k_mix = k_64 = k_s = k_s64 = k_arn = k_adf = args.k
+        err_mix = err_64 = err_s = err_s64 = err_arn = err_adf = None
     else:
         refs = torch.stack([ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, srcs[r])[0].clone() for r in range(NRHS)])
         k_mix, err_mix = calibrate_batch(torch, bt, srcs, refs, ovl.MIXED, K_GRID)
@@ -434,17 +434,21 @@ def run_ours(args, world, rank, local):
         cal = calibrate_k(ovl, ctx, torch, srcs[0], [("mixed", ovl.MIXED), ("fp64", 0)])
         (k_s, err_s), (k_s64, err_s64) = cal["mixed"], cal["fp64"]
         # Arnoldi on its own k grid (step 25: it needs a smaller subspace, Sec. 5)
-        cal_a = calibrate_k(ovl, ctx, torch, srcs[0], [("arnoldi", 0, ovl.ARNOLDI)], grid=list(range(250, 801, 25)))
-        k_arn, err_arn = cal_a["arnoldi"]
+        cal_a = calibrate_k(ovl, ctx, torch, srcs[0], [("arnoldi", 0, ovl.ARNOLDI),
+                                                       ("arnoldi_df", ovl.MIXED, ovl.ARNOLDI)],
+                            grid=list(range(250, 801, 25)))
+        (k_arn, err_arn), (k_adf, err_adf) = cal_a["arnoldi"], cal_a["arnoldi_df"]
     print(f"[bench] batch k mixed={k_mix} ({err_mix}), fp64={k_64} ({err_64}); single k mixed={k_s}, fp64={k_s64}",
           file=sys.stderr, flush=True)
 
     if args.solves_only:
         if not args.k:
             raise SystemExit("--solves-only needs --k")
-        if args.single:
+        one_method = ovl.ARNOLDI if args.arnoldi else ovl.LANCZOS2
+        one_flags = (ovl.OVERLAP | ovl.MIXED) if args.arnoldi else fl_mix
+        if args.single or args.arnoldi:
             out1 = torch.empty_like(srcs[0])
-            t = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, b, out1, flags=fl_mix),
+            t = time_solves(torch, ctx, lambda b: ctx.sign_krylov(one_method, k_s, MU, KAPPA, b, out1, flags=one_flags),
                             [srcs[r] for r in range(NRHS)], args.warmup, args.steps, flush)
         else:
             t = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix),
@@ -454,13 +458,14 @@ def run_ours(args, world, rank, local):
             # exactly the launches of one solve (no effect without a profiler)
             torch.cuda.synchronize()
             torch.cuda.cudart().cudaProfilerStart()
-            if args.single:
-                ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, srcs[0], out1, flags=fl_mix)
+            if args.single or args.arnoldi:
+                ctx.sign_krylov(one_method, k_s, MU, KAPPA, srcs[0], out1, flags=one_flags)
             else:
                 bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix)
             torch.cuda.synchronize()
             torch.cuda.cudart().cudaProfilerStop()
-        print(json.dumps({"solves_only": True, "single": args.single, "k": k_mix, "ms_per_step": statistics.mean(t)}))
+        print(json.dumps({"solves_only": True, "single": args.single, "arnoldi_doublefloat": args.arnoldi, "k": k_mix,
+                          "ms_per_step": statistics.mean(t)}))
         return
 
     outb = torch.empty_like(srcs)
@@ -504,6 +509,21 @@ def run_ours(args, world, rank, local):
                         bsingle, 2, nctx, flush)
     t_arn = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_arn, MU, KAPPA, b, out1,
                                                               flags=ovl.OVERLAP), bsingle, 1, 2, flush)
+    t_adf = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_adf, MU, KAPPA, b, out1,
+                                                              flags=ovl.OVERLAP | ovl.MIXED), bsingle, 2, nctx, flush)
+    # the double-float Gram-Schmidt sweeps against HBM: 4 passes over v_0..v_j at step j, 16 B per
+    # complex element (CUDA events around each sweep kernel, eager launches)
+    ctx.profile(reset=True)
+    ctx.sign_krylov(ovl.ARNOLDI, k_adf, MU, KAPPA, srcs[0], out1, flags=ovl.OVERLAP | ovl.MIXED | ovl.PROFILE)
+    torch.cuda.synchronize()
+    aprof = ctx.profile(reset=True)
+    sweep_ms = sum(aprof.get(kk, {}).get("ms", 0.0) for kk in ("multidot", "multiaxpy"))
+    sweep_bytes = 2 * k_adf * (k_adf + 1) * ctx.n * 16
+    adf_sweeps = {"bytes_per_solve": sweep_bytes, "ms": round(sweep_ms, 3),
+                  "GB_s": round(sweep_bytes / (sweep_ms * 1e6), 1) if sweep_ms else None,
+                  "frac_hbm": round(sweep_bytes / (sweep_ms * 1e6) / hbm_peak, 3) if sweep_ms else None,
+                  "inner_sign_ms": round(aprof.get("inner_sign", {}).get("ms", 0.0), 3),
+                  "stencil_ms": round(aprof.get("dslash", {}).get("ms", 0.0), 3)}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     hsrc = srcs.cpu().pin_memory()
@@ -599,6 +619,10 @@ def run_ours(args, world, rank, local):
             "arnoldi_fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_arn), "ms": statistics.mean(t_arn),
                                            "k": k_arn, "rel_err_vs_k1000_fp64": err_arn,
                                            "k_ratio_2sl_over_arnoldi": (k_s64 / k_arn) if k_arn else None},
+            "arnoldi_doublefloat_single_source": {"solves_per_s": 1e3 / statistics.mean(t_adf),
+                                                  "ms": statistics.mean(t_adf), "k": k_adf,
+                                                  "rel_err_vs_k1000_fp64": err_adf,
+                                                  "gram_schmidt_sweeps": adf_sweeps},
             "profile_ms_per_batch": {kk: round(v, 4) for kk, v in prof.items()},
             "multi_lattice_batch": multi,
             "dw": dw,
@@ -623,6 +647,8 @@ def main():
     ap.add_argument("--single", action="store_true", help="with --solves-only: single-source solves instead of batches")
     ap.add_argument("--dw-only", action="store_true", help="only the stencil bandwidth measurement (--steps repetitions)")
     ap.add_argument("--dw-dims", default="", help="lattice of the stencil bandwidth measurement, e.g. 32,32,32,32")
+    ap.add_argument("--arnoldi", action="store_true",
+                    help="with --solves-only: single-source double-float Arnoldi solves (D_ov b) instead")
     ap.add_argument("--profile-one", action="store_true",
                     help="with --solves-only: one extra solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--solves-only", action="store_true",

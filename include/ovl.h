@@ -70,12 +70,19 @@ typedef struct ovl_ctx ovl_ctx;
 #define OVL_F32_FULL     0x0020  /* apply_Dw: FP32 stencil with 18-real links              */
 #define OVL_OVERLAP      0x0100  /* sign_krylov: out = D_ov b = b + gamma5 sgn(A) b,
                                     otherwise out = sgn(A) b                               */
-#define OVL_MIXED        0x0200  /* sign_krylov: FP32 basis + 12-real links in pass 1, FP64
-                                    coefficients, FP64 regeneration pass (two-pass, Sec. 5) */
+#define OVL_MIXED        0x0200  /* sign_krylov LANCZOS2: FP32 basis + 12-real links in pass 1, FP64
+                                    coefficients, FP64 regeneration pass (two-pass, Sec. 5).
+                                    ARNOLDI: the stored basis as double-float pairs (about 48
+                                    significant bits, 16 bytes per complex element as in FP64) and
+                                    both Gram-Schmidt sweeps in double-float arithmetic on the FP32
+                                    pipe; FP64 stencil, H and inner sign.  Results agree with the
+                                    FP64 Arnoldi run to about 1e-12                          */
 #define OVL_TWO_PASS     0x0400  /* sign_krylov LANCZOS2: do not store the basis, regenerate it
                                     from alpha, beta, gamma in a second pass (Sec. 5)       */
-#define OVL_INNER_NEWTON 0x1000  /* inner sgn(G_k): Roberts/Newton (Sec. 2) instead of the
-                                    resolvent quadrature (2sL only)                        */
+#define OVL_INNER_NEWTON 0x1000  /* inner sgn(G_k) / sgn(H_k): Roberts/Newton (Sec. 2) instead of
+                                    the resolvent quadrature (tridiagonal solves for 2sL,
+                                    Givens-rotation Hessenberg solves for Arnoldi); without the
+                                    flag Newton still runs if the quadrature does not converge */
 #define OVL_REPROJ       0x8000  /* sign_krylov MIXED with deflation: project the deflated directions
                                     out of every FP32 pass-1 vector (v^ -= R L^dag v^, w^ -= L R^dag w^).
                                     Off by default: with FP32 copies of R, L the projected operator
@@ -284,7 +291,9 @@ int ovl_get_deflation(ovl_ctx* ctx, int* m_out, double* lambda, void* R, void* L
 /* out = sgn(A) b (or D_ov(mu) b with OVL_OVERLAP), A = gamma5 D_w(mu), by the method
  * (OVL_ARNOLDI / OVL_LANCZOS2) with Krylov size k >= 1 and the installed deflation.
  * b, out: canonical complex128 (device, or host with OVL_HOST), may not overlap.
- * info may be NULL.  Returns OVL_EBREAKDOWN on a serious 2sL breakdown (out holds the
+ * info may be NULL.  OVL_EINVAL for OVL_TWO_PASS with OVL_ARNOLDI (the Arnoldi basis is always
+ * stored: k + 1 vectors of 16 bytes per complex element, FP64 or double-float with OVL_MIXED).
+ * Returns OVL_EBREAKDOWN on a serious 2sL breakdown (out holds the
  * approximation from the steps before it), OVL_ESINGULAR if the projected matrix has an
  * eigenvalue on the imaginary axis, OVL_ENOCONV if the inner sign did not converge. */
 int ovl_sign_krylov(ovl_ctx* ctx, int method, int k, double mu, double kappa,

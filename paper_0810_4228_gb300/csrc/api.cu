@@ -111,7 +111,8 @@ int ensure_solve(ovl_ctx* c, int k) {
     const int kc = std::max(k, c->kcap);
     const size_t vb = c->n * sizeof(double2);
     const size_t kb = (size_t)(kc + 1) * sizeof(double2);
-    const size_t ie = std::max(ovl::inner_work_elems(kc, 0), ovl::inner_work_elems(kc, 1));
+    const size_t ie = std::max({ovl::inner_work_elems(kc, 0), ovl::inner_work_elems(kc, 1),
+                                ovl::inner_work_elems(kc, 2)});
     if ((r = dalloc(c, &c->V64, vb * (kc + 1))) || (r = dalloc(c, &c->alpha, kb)) || (r = dalloc(c, &c->beta, kb)) ||
         (r = dalloc(c, &c->gamma, kb)) || (r = dalloc(c, &c->vscale, kb)) || (r = dalloc(c, &c->cvec, kb)) ||
         (r = dalloc(c, &c->H, kb * (kc + 1))) || (r = dalloc(c, &c->h1, kb)) || (r = dalloc(c, &c->h2, kb)) ||
@@ -266,6 +267,21 @@ void prof_collect(ovl_ctx* c) {
 }
 
 // Queue the whole solve (everything between packing b and unpacking y).
+// c = |b_perp| sgn(H_k) e_1 for Arnoldi: the resolvent quadrature with Givens-rotation solves of
+// the shifted Hessenberg systems, and Roberts/Newton only if it did not converge (or on request)
+int arnoldi_inner_sign(ovl_ctx* c, int ldH, int flags) {
+    cudaStream_t st = c->st;
+    if (!(flags & OVL_INNER_NEWTON)) {
+        const int q = ovl::launch_inner_quadrature_hess(c->H, ldH, c->ks, c->cvec, c->inner, c->inner_elems,
+                                                        c->kcap, c->partials, c->counter, st);
+        if (q == 0)
+            return ovl::launch_inner_newton(nullptr, nullptr, nullptr, c->H, ldH, 0, c->ks, c->cvec, c->inner,
+                                            c->inner_elems, c->kcap, c->num_sms, st, 1);
+    }
+    return ovl::launch_inner_newton(nullptr, nullptr, nullptr, c->H, ldH, 0, c->ks, c->cvec, c->inner,
+                                    c->inner_elems, c->kcap, c->num_sms, st);
+}
+
 int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int flags) {
     cudaStream_t st = c->st;
     const size_t n = c->n;
@@ -391,6 +407,40 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
         } else {
             prof(c, KC_COMBINE, [&] { ovl::launch_combine(c->V64, n, c->vscale, c->cvec, ks, c->kcap, c->y64, n, st); });
         }
+    } else if (flags & OVL_MIXED) {  // Arnoldi, double-float basis (csrc/arnoldi_df.cu)
+        prof(c, KC_DEFLATE, [&] {
+            ovl::launch_deflate_split(c->b64, c->R, c->L, c->lam, m, c->pq, c->bR, nullptr, c->y64, ks, nullptr,
+                                      part, cnt, n, st);
+        });
+        // V64 holds kcap + 1 double-float vectors (same 16 bytes per complex element); the
+        // two-sided Lanczos coefficient arrays (kcap + 1 entries each, unused by Arnoldi) hold the
+        // double-float copies of h1, h2 and of the combination coefficients
+        float4* Vd = reinterpret_cast<float4*>(c->V64);
+        float4* h1d = reinterpret_cast<float4*>(c->alpha);
+        float4* h2d = reinterpret_cast<float4*>(c->beta);
+        float4* cdf = reinterpret_cast<float4*>(c->gamma);
+        double2* x64 = c->s64;  // FP64 value of v_j, the stencil's input
+        prof(c, KC_ANORM, [&] { ovl::launch_adf_start(c->bR, Vd, x64, ks, n, st); });
+        const int ldH = c->kcap + 1;
+        for (int j = 0; j < k; ++j) {
+            float4* t = Vd + (size_t)(j + 1) * n;
+            prof(c, KC_ADSLASH, [&] {
+                ovl::launch_dslash(c->U64, 0, x64, c->t64, mu, kappa, 1, g, st, ks);
+                ovl::launch_adf_todf(c->t64, t, ks, n, st);
+            }, 2);
+            prof(c, KC_ADOT, [&] { ovl::launch_adf_dot(Vd, n, j + 1, t, c->h1, h1d, part, n, c->num_sms, ks, st); }, 2);
+            prof(c, KC_AAXPY, [&] { ovl::launch_adf_update(Vd, n, j + 1, h1d, t, n, ks, part, cnt, st); });
+            prof(c, KC_ADOT, [&] { ovl::launch_adf_dot(Vd, n, j + 1, t, c->h2, h2d, part, n, c->num_sms, ks, st); }, 2);
+            prof(c, KC_AAXPY, [&] {
+                ovl::launch_adf_update_fin(Vd, n, j + 1, h2d, t, c->H, ldH, c->h1, c->h2, j, k - 1, part, cnt, ks,
+                                           n, st);
+            });
+            prof(c, KC_ANORM, [&] { ovl::launch_adf_normalize(t, x64, ks, n, st); });
+        }
+        int r = 0;
+        prof(c, KC_INNER, [&] { r = arnoldi_inner_sign(c, ldH, flags); }, (flags & OVL_INNER_NEWTON) ? 2 : 15);
+        if (r) return fail(c, OVL_ECUDA, "inner sign launch failed");
+        prof(c, KC_COMBINE, [&] { ovl::launch_adf_combine(Vd, n, c->cvec, cdf, ks, c->kcap, c->y64, n, st); }, 2);
     } else {  // Arnoldi
         prof(c, KC_DEFLATE, [&] {
             ovl::launch_deflate_split(c->b64, c->R, c->L, c->lam, m, c->pq, c->bR, nullptr, c->y64, ks, nullptr,
@@ -412,10 +462,7 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
             prof(c, KC_ANORM, [&] { ovl::launch_arnoldi_normalize(t, ks, n, st); });
         }
         int r = 0;
-        prof(c, KC_INNER, [&] {
-            r = ovl::launch_inner_newton(nullptr, nullptr, nullptr, c->H, ldH, 0, ks, c->cvec, c->inner,
-                                         c->inner_elems, c->kcap, c->num_sms, st);
-        }, 2);
+        prof(c, KC_INNER, [&] { r = arnoldi_inner_sign(c, ldH, flags); }, (flags & OVL_INNER_NEWTON) ? 2 : 15);
         if (r) return fail(c, OVL_ECUDA, "inner sign launch failed");
         prof(c, KC_COMBINE, [&] { ovl::launch_combine(c->V64, n, nullptr, c->cvec, ks, c->kcap, c->y64, n, st); });
     }
@@ -651,8 +698,8 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
     if (b == out) return fail(c, OVL_EINVAL, "b and out must not overlap");
     if (c->m > 0 && (mu != c->dmu || kappa != c->dkappa))
         return fail(c, OVL_EINVAL, "mu/kappa differ from those of the installed deflation");
-    if (method == OVL_ARNOLDI && (flags & (OVL_MIXED | OVL_TWO_PASS)))
-        return fail(c, OVL_EINVAL, "mixed/two-pass is defined for two-sided Lanczos only");
+    if (method == OVL_ARNOLDI && (flags & OVL_TWO_PASS))
+        return fail(c, OVL_EINVAL, "two-pass is defined for two-sided Lanczos only");
     int r = ensure_solve(c, k);
     if (r) return r;
     const size_t cb = c->n * sizeof(double2);

@@ -1,0 +1,333 @@
+// Arnoldi (Sec. 2, Eq. 2.2-2.6; with LR deflation Sec. 3, Eq. 3.4) with the basis V_k stored as
+// double-float pairs and the classical Gram-Schmidt (applied twice) evaluated in double-float
+// arithmetic on the FP32 pipe.
+//
+// Step j of the Arnoldi relation A V_j = V_{j+1} H_j:  t = A v_j (FP64 stencil on the FP64 copy of
+// v_j), h1 = V^dag t, t -= V h1, h2 = V^dag t, t -= V h2, H[0..j, j] = h1 + h2,
+// H[j+1, j] = |t|, v_{j+1} = t / |t|.  The two passes over the stored basis per Gram-Schmidt sweep
+// are the whole cost of the method at large k (Sec. 5); with FP64 arithmetic they run at the FP64
+// issue rate, which on this GPU is far below what HBM delivers for 16 bytes per complex element.
+// Double-float values (hi + lo, about 48 significant bits) take the same 16 bytes per complex
+// element and their products and sums run on the FP32 pipe, so the sweeps become bandwidth
+// bound.  The coefficients h, H and the inner sign stay FP64; every product enters its sum through
+// the exact FMA split (dfacc), and every sum of per-lane, per-warp and per-block partials is
+// deterministic (fixed order).
+#include "ovl_kernels.h"
+#include "df32.cuh"
+
+namespace ovl {
+
+static constexpr int AD_T = 256;    // threads per block
+static constexpr int AD_W = AD_T / 32;
+static constexpr int AD_CH = 1024;  // elements of x per block in the many-vector dot
+
+__device__ __forceinline__ float4 to_f4(cx<df> z) { return make_float4(z.r.hi, z.r.lo, z.i.hi, z.i.lo); }
+__device__ __forceinline__ cx<df> from_f4(float4 v) { return mk(df(v.x, v.y), df(v.z, v.w)); }
+
+// sum over the 32 lanes of a warp (butterfly; every lane ends with the same value)
+__device__ __forceinline__ df warp_sum_df(df a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const df b(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
+        a = a + b;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------------ helpers --
+// xdf = x (FP64 -> double-float split), n complex values
+__global__ void k_adf_todf(const double2* __restrict__ x, float4* __restrict__ xdf, const KState* ks, size_t n) {
+    if (ks->done || ks->status) return;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        xdf[e] = to_f4(d2df(x[e]));
+}
+
+// v_1 = x / |x| (|x| = nR from the deflation split): the double-float split into V_0 and its
+// exact FP64 value (hi + lo fits a double) into x64, the stencil's input of step 0
+__global__ void k_adf_start(const double2* __restrict__ x, float4* __restrict__ v, double2* __restrict__ x64,
+                            const KState* ks, size_t n) {
+    if (ks->status || ks->nR == 0.0) return;
+    const double s = 1.0 / ks->nR;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const double2 a = x[e];
+        const cx<df> z = d2df(make_double2(a.x * s, a.y * s));
+        v[e] = to_f4(z);
+        x64[e] = df2d(z);
+    }
+}
+
+// ---------------------------------------------------------- many-vector dot --
+// The sweeps stream the basis from HBM with one 16-byte load per lane and a chain of dependent
+// double-float operations behind it, so a warp has about one load in flight; L2 prefetches a
+// fixed distance ahead (no registers held) keep more bytes in flight per SM.
+static constexpr int AD_PF = 256;  // dot: elements ahead within the warp's vector chunk(s)
+static constexpr int AD_PFV = 4;   // update: vectors (of this warp) ahead
+__device__ __forceinline__ void prefetch_l2(const float4* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// re + i im += conj(v) x
+__device__ __forceinline__ void adf_dot_term(dfacc& re, dfacc& im, const cx<df>& v, const cx<df>& xx) {
+    dfacc_add(re, v.r, xx.r, false);
+    dfacc_add(re, v.i, xx.i, false);
+    dfacc_add(im, v.r, xx.i, false);
+    dfacc_add(im, v.i, xx.r, true);
+}
+// re + i im += h v
+__device__ __forceinline__ void adf_axpy_term(dfacc& re, dfacc& im, const cx<df>& h, const cx<df>& v) {
+    dfacc_add(re, h.r, v.r, false);
+    dfacc_add(re, h.i, v.i, true);
+    dfacc_add(im, h.r, v.i, false);
+    dfacc_add(im, h.i, v.r, false);
+}
+
+// stage 1, grid (chunks, vector groups): block (c, g) stages elements [c*AD_CH, (c+1)*AD_CH) of
+// x in shared memory; warp w forms the partial dots V_l^dag x over that chunk for
+// l = g*vpb + w, g*vpb + w + AD_W, ... < min(nvec, (g+1)*vpb).
+__global__ void __launch_bounds__(AD_T) k_adf_dot(const float4* __restrict__ V, size_t ld, int nvec, int vpb,
+                                                  const float4* __restrict__ x, double2* __restrict__ part,
+                                                  size_t n, const KState* ks) {
+    __shared__ float4 xs[AD_CH];
+    if (ks->done || ks->status) return;
+    const size_t base = (size_t)blockIdx.x * AD_CH;
+    const int lim = (int)(n - base < (size_t)AD_CH ? n - base : (size_t)AD_CH);
+    for (int q = threadIdx.x; q < lim; q += AD_T) xs[q] = x[base + q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int l0 = blockIdx.y * vpb;
+    const int l1 = min(nvec, l0 + vpb);
+    for (int l = l0 + wid; l < l1; l += AD_W) {
+        const float4* Vl = V + (size_t)l * ld + base;
+        dfacc re = {0.f, 0.f}, im = {0.f, 0.f};
+        // the next vector of this warp, for the prefetches that run past the end of this one
+        const float4* Vn = l + AD_W < l1 ? V + (size_t)(l + AD_W) * ld + base : nullptr;
+#pragma unroll 4
+        for (int q = lane; q < lim; q += 32) {
+            if ((lane & 7) == 0) {  // one lane per 128-byte line
+                const int tq = q + AD_PF;
+                if (tq < lim) prefetch_l2(Vl + tq);
+                else if (Vn && tq - lim < lim) prefetch_l2(Vn + (tq - lim));
+            }
+            adf_dot_term(re, im, from_f4(__ldg(Vl + q)), from_f4(xs[q]));
+        }
+        const df sr = warp_sum_df(dfacc_value(re)), si = warp_sum_df(dfacc_value(im));
+        if (lane == 0) part[(size_t)l * gridDim.x + blockIdx.x] = make_double2(sr.to_double(), si.to_double());
+    }
+}
+
+// stage 2: one warp per vector sums its block partials in FP64 (fixed order); h in FP64 and as a
+// double-float split for the update kernels
+__global__ void k_adf_dot_reduce(const double2* __restrict__ part, int nblk, int nvec, double2* __restrict__ h,
+                                 float4* __restrict__ hdf, const KState* ks) {
+    if (ks->done || ks->status) return;
+    const int lane = threadIdx.x & 31;
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (l >= nvec) return;
+    double re = 0.0, im = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
+        const double2 v = part[(size_t)l * nblk + b];
+        re += v.x;
+        im += v.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+        h[l] = make_double2(re, im);
+        hdf[l] = to_f4(d2df(make_double2(re, im)));
+    }
+}
+
+// ------------------------------------------------------- many-vector update --
+// Block = 32 consecutive elements (lane) x AD_W warps; warp w sums c_l V_l[e] over l = w, w + AD_W,
+// ... < nvec, the warps' sums are added in shared memory in warp order.
+__device__ __forceinline__ void adf_lincomb(const float4* __restrict__ V, size_t ld, int nvec,
+                                            const float4* __restrict__ c, size_t e, bool in, int wid, int lane,
+                                            float4 (&red)[AD_W][32], cx<df>& sum) {
+    dfacc re = {0.f, 0.f}, im = {0.f, 0.f};
+    if (in) {
+#pragma unroll 4
+        for (int l = wid; l < nvec; l += AD_W) {
+            if ((lane & 7) == 0 && l + AD_PFV * AD_W < nvec)  // one lane per 128-byte line
+                prefetch_l2(V + (size_t)(l + AD_PFV * AD_W) * ld + e);
+            adf_axpy_term(re, im, from_f4(__ldg(c + l)), from_f4(__ldg(V + (size_t)l * ld + e)));
+        }
+    }
+    red[wid][lane] = make_float4(re.s, re.e, im.s, im.e);
+    __syncthreads();
+    if (wid == 0) {
+        df sr = df_fast2sum(red[0][lane].x, red[0][lane].y), si = df_fast2sum(red[0][lane].z, red[0][lane].w);
+#pragma unroll
+        for (int w = 1; w < AD_W; ++w) {
+            const float4 p = red[w][lane];
+            sr = sr + df_fast2sum(p.x, p.y);
+            si = si + df_fast2sum(p.z, p.w);
+        }
+        sum = mk(sr, si);
+    }
+}
+
+struct ArnoldiFinDf {
+    double2* H;
+    int ldH;
+    const double2* h1;
+    const double2* h2;
+    int j;
+    int jlast;
+    double bdtol;  // lucky breakdown when H[j+1, j] <= bdtol * (largest column norm of H so far)
+};
+
+// x -= sum_l h_l V_l (x double-float, in place).  fin = 1 (second pass of step j): also |x|^2 over
+// the grid, and the last block writes H[0..j, j] = h1 + h2, H[j+1, j] = |x|, kused = j + 1 and
+// marks the solve done on a lucky breakdown or at j = jlast.
+__global__ void __launch_bounds__(AD_T) k_adf_update(const float4* __restrict__ V, size_t ld, int nvec,
+                                                     const float4* __restrict__ hdf, float4* __restrict__ x,
+                                                     size_t n, KState* ks, int fin, ArnoldiFinDf af,
+                                                     double* partials, unsigned int* counter) {
+    __shared__ float4 red[AD_W][32];
+    __shared__ double rsm[32];
+    if (ks->done || ks->status) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t ntile = (n + 31) / 32;
+    double part[1] = {0.0};
+    for (size_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const size_t e = tile * 32 + lane;
+        const bool in = e < n;
+        cx<df> s;
+        adf_lincomb(V, ld, nvec, hdf, e, in, wid, lane, red, s);
+        if (wid == 0 && in) {
+            const cx<df> xv = from_f4(x[e]);
+            const cx<df> z = mk(xv.r - s.r, xv.i - s.i);
+            x[e] = to_f4(z);
+            const double2 zd = df2d(z);
+            part[0] += zd.x * zd.x + zd.y * zd.y;
+        }
+        __syncthreads();  // red is reused by the next tile
+    }
+    if (!fin) return;
+    double out[1];
+    if (grid_sum_last<1>(part, partials, counter, out, rsm)) {
+        const int j = af.j;
+        double hh = 0.0;
+        for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+            const double2 a = af.h1[r], b = af.h2[r];
+            const double2 v = make_double2(a.x + b.x, a.y + b.y);
+            af.H[r + (size_t)j * af.ldH] = v;
+            hh += v.x * v.x + v.y * v.y;
+        }
+        double hv[1] = {hh};
+        block_sum<1>(hv, rsm);
+        if (threadIdx.x == 0) {
+            const double hn = sqrt(out[0]);
+            af.H[(j + 1) + (size_t)j * af.ldH] = make_double2(hn, 0.0);
+            const double colnorm = sqrt(hv[0] + out[0]);
+            if (colnorm > ks->anorm) ks->anorm = colnorm;
+            ks->kused = j + 1;
+            ks->red[0] = make_double2(hn, 0.0);
+            if (hn <= af.bdtol * fmax(ks->anorm, 1e-300) || j == af.jlast) ks->done = 1;
+        }
+    }
+}
+
+// v_{j+1} = t / |t| in place (double-float), and its exact FP64 value into x64 (the next step's
+// stencil input); skipped after the last step or a lucky breakdown
+__global__ void k_adf_normalize(float4* __restrict__ t, double2* __restrict__ x64, const KState* ks, size_t n) {
+    if (ks->done || ks->status) return;
+    const df inv(1.0 / ks->red[0].x);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const cx<df> z = from_f4(t[e]);
+        const cx<df> v = mk(z.r * inv, z.i * inv);
+        t[e] = to_f4(v);
+        x64[e] = df2d(v);
+    }
+}
+
+// c_l as double-float splits for l < kused
+__global__ void k_adf_coef(const double2* __restrict__ c, float4* __restrict__ cdf, const KState* ks) {
+    if (ks->status) return;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < ks->kused; l += gridDim.x * blockDim.x)
+        cdf[l] = to_f4(d2df(c[l]));
+}
+
+// y += sum_{l < kused} c_l V_l (Eq. 2.6), y FP64
+__global__ void __launch_bounds__(AD_T) k_adf_combine(const float4* __restrict__ V, size_t ld,
+                                                      const float4* __restrict__ cdf, const KState* ks,
+                                                      double2* __restrict__ y, size_t n) {
+    __shared__ float4 red[AD_W][32];
+    if (ks->status) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t e = (size_t)blockIdx.x * 32 + lane;
+    const bool in = e < n;
+    cx<df> s;
+    adf_lincomb(V, ld, ks->kused, cdf, e, in, wid, lane, red, s);
+    if (wid == 0 && in) {
+        const double2 a = y[e], d = df2d(s);
+        y[e] = make_double2(a.x + d.x, a.y + d.y);
+    }
+}
+
+// ---------------------------------------------------------------- launchers --
+// the update kernel's grid: one block per 32 elements up to AD_MAXB blocks (its norm partials,
+// one double per block, must fit the solve's partials buffer of at least 2^16 doubles)
+static constexpr unsigned AD_MAXB = 16384;
+static unsigned adf_update_grid(size_t n) {
+    const size_t t = (n + 31) / 32;
+    return (unsigned)(t < AD_MAXB ? (t ? t : 1) : AD_MAXB);
+}
+
+static int adf_grid(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 1024 ? (b ? b : 1) : 1024);
+}
+
+void launch_adf_todf(const double2* x, float4* xdf, const KState* ks, size_t n, cudaStream_t st) {
+    k_adf_todf<<<adf_grid(n), 256, 0, st>>>(x, xdf, ks, n);
+}
+
+void launch_adf_start(const double2* x, float4* v, double2* x64, const KState* ks, size_t n, cudaStream_t st) {
+    k_adf_start<<<adf_grid(n), 256, 0, st>>>(x, v, x64, ks, n);
+}
+
+int adf_dot_blocks(size_t n) { return (int)((n + AD_CH - 1) / AD_CH); }
+
+void launch_adf_dot(const float4* V, size_t ld, int nvec, const float4* x, double2* h, float4* hdf,
+                    double* partials, size_t n, int num_sms, const KState* ks, cudaStream_t st) {
+    if (nvec <= 0) return;
+    const int nchunk = adf_dot_blocks(n);
+    // vectors per warp: about eight resident blocks per SM in total, at least one vector per warp
+    const long long target = 8ll * (num_sms > 0 ? num_sms : 1);
+    long long vpw = ((long long)nvec * nchunk + (long long)AD_W * target - 1) / ((long long)AD_W * target);
+    if (vpw < 1) vpw = 1;
+    const int vpb = (int)(vpw * AD_W);
+    const int ngroup = (nvec + vpb - 1) / vpb;
+    double2* part = reinterpret_cast<double2*>(partials);
+    k_adf_dot<<<dim3(nchunk, ngroup), AD_T, 0, st>>>(V, ld, nvec, vpb, x, part, n, ks);
+    k_adf_dot_reduce<<<(nvec + 7) / 8, 256, 0, st>>>(part, nchunk, nvec, h, hdf, ks);
+}
+
+void launch_adf_update(const float4* V, size_t ld, int nvec, const float4* hdf, float4* x, size_t n, KState* ks,
+                       double* partials, unsigned int* counter, cudaStream_t st) {
+    if (nvec <= 0) return;
+    ArnoldiFinDf af = {nullptr, 0, nullptr, nullptr, 0, 0, 0.0};
+    k_adf_update<<<adf_update_grid(n), AD_T, 0, st>>>(V, ld, nvec, hdf, x, n, ks, 0, af, partials, counter);
+}
+
+void launch_adf_update_fin(const float4* V, size_t ld, int nvec, const float4* hdf, float4* x, double2* H, int ldH,
+                           const double2* h1, const double2* h2, int j, int jlast, double* partials,
+                           unsigned int* counter, KState* ks, size_t n, cudaStream_t st) {
+    // double-float sweeps leave a residual of about 2^-46 |A v_j| where the Krylov space is
+    // exhausted (FP64: 2^-53), so the breakdown test sits at 1e-11 instead of FP64's 1e-13
+    ArnoldiFinDf af = {H, ldH, h1, h2, j, jlast, 1e-11};
+    k_adf_update<<<adf_update_grid(n), AD_T, 0, st>>>(V, ld, nvec, hdf, x, n, ks, 1, af, partials, counter);
+}
+
+void launch_adf_normalize(float4* t, double2* x64, const KState* ks, size_t n, cudaStream_t st) {
+    k_adf_normalize<<<adf_grid(n), 256, 0, st>>>(t, x64, ks, n);
+}
+
+void launch_adf_combine(const float4* V, size_t ld, const double2* c, float4* cdf, const KState* ks, int kmax,
+                        double2* y, size_t n, cudaStream_t st) {
+    k_adf_coef<<<(kmax + 255) / 256 > 0 ? (kmax + 255) / 256 : 1, 256, 0, st>>>(c, cdf, ks);
+    k_adf_combine<<<(unsigned)((n + 31) / 32), AD_T, 0, st>>>(V, ld, cdf, ks, y, n);
+}
+
+}  // namespace ovl

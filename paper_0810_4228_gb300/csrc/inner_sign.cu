@@ -54,6 +54,12 @@ size_t inner_work_elems(int kmax, int method) {
         // copies of alpha, beta, gamma
         return (size_t)quad_threads(QUAD_LEVELS - 1) * (size_t)kmax * 3 + 5 * (size_t)kmax + 64;
     }
+    if (method == 2) {
+        // Hessenberg quadrature: per thread and row x and the two rotation coefficients, T and S
+        // sums, the double-float copy of H (kmax x kmax)
+        return (size_t)quad_threads(QUAD_LEVELS - 1) * (size_t)kmax * 3 + 2 * (size_t)kmax + 64 +
+               (size_t)kmax * kmax;
+    }
     // Newton: S, X (kmax^2 each) + pivots, slots, scalars, barrier, partials
     return 2 * (size_t)kmax * kmax + 4 * (size_t)kmax + 8192;
 }
@@ -304,6 +310,212 @@ int launch_inner_quadrature_batched(int nseq, const double2* alpha, const double
     if (inner_work_elems(kmax, 0) > work_stride || nseq < 1) return -1;
     quad_launch(alpha, beta, gamma, ks, c, work, kmax, partials, counters, nseq,
                 QStride{coef_stride, work_stride, part_stride}, st);
+    return 0;
+}
+
+// ------------------------------------------------- Hessenberg quadrature --
+// The same trapezoidal rule for the upper Hessenberg H_k of Arnoldi (Sec. 2, Eq. 2.6).  Each node
+// needs x = M^-1 e_1 for M = H + s i e^u.  Givens rotations applied to pairs of columns from the
+// right, (k-2, k-1) first and (0, 1) last, each annihilating one subdiagonal entry, reduce M to
+// upper triangular form: M Q = R.  Then M x = e_1 gives R (Q^dag x) = e_1, and since R is upper
+// triangular, Q^dag x = e_1 / R_00, i.e.  x = Q e_1 / R_00.  So the sweep needs only the
+// rotations and R_00: it carries one column (the one being rotated next) instead of the
+// triangular factor, O(k^2) operations and O(k) memory per node.  Rotations are unitary, so the
+// solve is backward stable without pivoting.  With the rotation on columns (j, j+1) written as
+// G = [[b, conj(a)], [-a, conj(b)]] / rho (a, b the row-(j+1) entries of column j and of the carried
+// column, rho = sqrt(|a|^2 + |b|^2)), Q e_1 has components x_j = p_j b_j / rho_j (j < k-1) and
+// x_{k-1} = p_{k-1}, with p_0 = 1 and p_{j+1} = -p_j a_j / rho_j.
+//
+// One warp per (node, sign), its carried column in shared memory, double-float arithmetic.
+
+// log of the Frobenius norm of H (a bound on its spectral radius) -> ks->red[7].x; H -> double-float
+__global__ void __launch_bounds__(256) k_hess_prep(const double2* __restrict__ H, int ldH, KState* ks,
+                                                   dfc* __restrict__ Hd, int ldd, double* partials,
+                                                   unsigned int* counter) {
+    __shared__ double red[32];
+    if (ks->status || ks->timeout) return;
+    const int n = ks->kused;
+    double part[1] = {0.0};
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const int rmax = j + 1 < n - 1 ? j + 1 : n - 1;  // column j: rows 0..j+1
+        for (int r = threadIdx.x; r <= rmax; r += blockDim.x) {
+            const double2 v = H[r + (size_t)j * ldH];
+            Hd[r + (size_t)j * ldd] = c2dfc(d2df(v));
+            part[0] += v.x * v.x + v.y * v.y;
+        }
+    }
+    double out[1];
+    if (grid_sum_last<1>(part, partials, counter, out, red)) {
+        if (threadIdx.x == 0) {
+            ks->red[7] = make_double2(log(fmax(sqrt(out[0]), 1e-300)), 0.0);
+            ks->inner_done = (n == 0);
+            ks->inner_iters = 0;
+            ks->inner_method = 0;
+            ks->inner_err = 0.0;
+        }
+    }
+}
+
+__device__ __forceinline__ cx<df> cscale(const cx<df>& z, float s) { return mk(df_scale(z.r, s), df_scale(z.i, s)); }
+// 1 / sqrt(x) for x in [1/4, 8): one Newton step y + y (1 - x y^2) / 2 from the FP32 estimate
+__device__ __forceinline__ df df_rsqrt(df x) {
+    const df y0(rsqrtf(x.hi), 0.f);
+    const df e = df(1) - x * y0 * y0;
+    return y0 + df_scale(y0 * e, 0.5f);
+}
+// (ca, cb) = (a, b) / sqrt(|a|^2 + |b|^2), scaled by a power of two first (FP32 exponent range)
+__device__ __forceinline__ void givens_df(const cx<df>& a, const cx<df>& b, cx<df>& ca, cx<df>& cb) {
+    const float mx = fmaxf(fmaxf(fabsf(a.r.hi), fabsf(a.i.hi)), fmaxf(fabsf(b.r.hi), fabsf(b.i.hi)));
+    if (mx == 0.f) {  // row already zero in both columns: identity
+        ca = mk(df(0), df(0));
+        cb = mk(df(1), df(0));
+        return;
+    }
+    int e;
+    frexpf(mx, &e);
+    const float sc = ldexpf(1.f, -e);
+    const cx<df> as = cscale(a, sc), bs = cscale(b, sc);
+    const df nn = (as.r * as.r + as.i * as.i) + (bs.r * bs.r + bs.i * bs.i);
+    const df ri = df_rsqrt(nn);
+    ca = mk(as.r * ri, as.i * ri);
+    cb = mk(bs.r * ri, bs.i * ri);
+}
+// cb h - ca c, each component one sum of four double-float products
+__device__ __forceinline__ cx<df> rot_combine(const cx<df>& cb, const cx<df>& h, const cx<df>& ca, const cx<df>& c) {
+    dfacc re, im;
+    dfacc_first(re, cb.r, h.r, false);
+    dfacc_add(re, cb.i, h.i, true);
+    dfacc_add(re, ca.r, c.r, true);
+    dfacc_add(re, ca.i, c.i, false);
+    dfacc_first(im, cb.r, h.i, false);
+    dfacc_add(im, cb.i, h.r, false);
+    dfacc_add(im, ca.r, c.i, true);
+    dfacc_add(im, ca.i, c.r, true);
+    return mk(dfacc_value(re), dfacc_value(im));
+}
+__device__ __forceinline__ cx<df> shfl_cdf(const cx<df>& z, int src) {
+    return mk(df(__shfl_sync(0xffffffffu, z.r.hi, src), __shfl_sync(0xffffffffu, z.r.lo, src)),
+              df(__shfl_sync(0xffffffffu, z.i.hi, src), __shfl_sync(0xffffffffu, z.i.lo, src)));
+}
+
+static constexpr int HQ_WPB_MAX = 4;  // warps (nodes) per block
+
+__global__ void k_hess_solve(KState* ks, double2* __restrict__ work, size_t hoff, int ldd, int kmax, int level,
+                             int nthreads) {
+    extern __shared__ float4 hq_col[];
+    if (ks->inner_done || ks->status || ks->timeout) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int t = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (t >= nthreads) return;  // whole warps
+    const int n = ks->kused;
+    const dfc* Hd = reinterpret_cast<const dfc*>(work + hoff);
+    float4* col = hq_col + (size_t)wid * kmax;
+    const double lo = ks->red[7].x - QUAD_HALFWIDTH;
+    const int node = t >> 1;
+    const float sgn = (t & 1) ? -1.f : 1.f;
+    const double u = level == 0 ? lo + node * QUAD_H0 : lo + (2 * node + 1) * (QUAD_H0 / (double)(1 << level));
+    const df tau(exp(u));
+    const cx<df> sig = mk(df(0), df(tau.hi * sgn, tau.lo * sgn));
+    dfc* X = reinterpret_cast<dfc*>(work);
+    dfc* CA = X + (size_t)n * nthreads;
+    dfc* CB = X + 2 * (size_t)n * nthreads;
+#define IDX(i) ((size_t)(i) * nthreads + t)
+    // carried column: column n-1 of M
+    for (int r = lane; r < n; r += 32) {
+        cx<df> h = dfc2c(Hd[r + (size_t)(n - 1) * ldd]);
+        if (r == n - 1) h = h + sig;
+        col[r] = make_float4(h.r.hi, h.r.lo, h.i.hi, h.i.lo);
+    }
+    __syncwarp();
+    for (int i = n - 1; i >= 1; --i) {
+        // rotate columns (i-1, i): a = M[i, i-1] (subdiagonal, unshifted), b = carried M[i, i]
+        const cx<df> a = dfc2c(Hd[i + (size_t)(i - 1) * ldd]);
+        const float4 bv = col[i];
+        const cx<df> b = mk(df(bv.x, bv.y), df(bv.z, bv.w));
+        cx<df> ca, cb;
+        givens_df(a, b, ca, cb);
+        if (lane == 0) {
+            CA[IDX(i - 1)] = c2dfc(ca);
+            CB[IDX(i - 1)] = c2dfc(cb);
+        }
+        // new carried column (column i-1 after the rotation), rows 0..i-1; its row i is zero
+        for (int r = lane; r < i; r += 32) {
+            cx<df> h = dfc2c(Hd[r + (size_t)(i - 1) * ldd]);
+            if (r == i - 1) h = h + sig;
+            const float4 cv = col[r];
+            const cx<df> z = rot_combine(cb, h, ca, mk(df(cv.x, cv.y), df(cv.z, cv.w)));
+            col[r] = make_float4(z.r.hi, z.r.lo, z.i.hi, z.i.lo);
+        }
+        __syncwarp();
+    }
+    const float4 r0 = col[0];
+    const cx<df> R00 = mk(df(r0.x, r0.y), df(r0.z, r0.w));
+    if (R00.r.hi == 0.f && R00.i.hi == 0.f) {
+        if (lane == 0) atomicExch(&ks->status, 5);  // singular shifted matrix
+        return;
+    }
+    __syncwarp();  // CA, CB written by lane 0 are read by every lane below
+    const cx<df> ir = crcp(R00);
+    const cx<df> s0 = mk(tau * ir.r, tau * ir.i);  // e^u / R_00
+    // p_j = prod_{l < j} (-a_l / rho_l): segments of the rotation list per lane, then an exclusive
+    // scan of the segment products across the warp
+    const int nr = n - 1;  // rotations
+    const int seg = (nr + 31) / 32;
+    const int j0 = lane * seg, j1 = min(nr, j0 + seg);
+    cx<df> pr = mk(df(1), df(0));
+    for (int j = j0; j < j1; ++j) pr = pr * (-dfc2c(CA[IDX(j)]));
+    // inclusive scan (Hillis-Steele): pr becomes the product of the segments of lanes 0..lane
+    for (int o = 1; o < 32; o <<= 1) {
+        const cx<df> other = shfl_cdf(pr, (lane - o) & 31);
+        if (lane >= o) pr = other * pr;
+    }
+    // exclusive prefix: the inclusive product of the previous lane
+    cx<df> p = shfl_cdf(pr, (lane - 1) & 31);
+    if (lane == 0) p = mk(df(1), df(0));
+    for (int j = j0; j < j1; ++j) {
+        const cx<df> x = p * dfc2c(CB[IDX(j)]) * s0;
+        X[IDX(j)] = c2dfc(x);
+        p = p * (-dfc2c(CA[IDX(j)]));
+    }
+    // x_{n-1} = p_{n-1} / R_00: p after the last rotation (the lane holding it, or lane 0 if n = 1)
+    const int last = nr > 0 ? (nr - 1) / seg : 0;
+    if (lane == last) X[IDX(n - 1)] = c2dfc((nr > 0 ? p : mk(df(1), df(0))) * s0);
+#undef IDX
+}
+
+static void hess_quad_launch(const double2* H, int ldH, KState* ks, double2* c, double2* work, int kmax,
+                             double* partials, unsigned int* counter, cudaStream_t st) {
+    const int tmax = quad_threads(QUAD_LEVELS - 1);
+    double2* T = work + (size_t)tmax * kmax * 3;
+    const size_t hoff = (size_t)tmax * kmax * 3 + 2 * (size_t)kmax + 64;
+    int pb = (kmax + 7) / 8;
+    if (pb > 1024) pb = 1024;
+    k_hess_prep<<<pb, 256, 0, st>>>(H, ldH, ks, reinterpret_cast<dfc*>(work + hoff), kmax, partials, counter);
+    const size_t per_warp = sizeof(float4) * (size_t)kmax;
+    int wpb = (int)((96u * 1024u) / per_warp);
+    if (wpb > HQ_WPB_MAX) wpb = HQ_WPB_MAX;
+    if (wpb < 1) wpb = 1;
+    const size_t smem = per_warp * wpb;
+    static size_t smem_set = 0;
+    if (smem > 48 * 1024 && smem > smem_set) {
+        cudaFuncSetAttribute(k_hess_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_set = smem;
+    }
+    for (int level = 0; level < QUAD_LEVELS; ++level) {
+        const int nt = quad_threads(level);
+        k_hess_solve<<<(nt + wpb - 1) / wpb, 32 * wpb, smem, st>>>(ks, work, hoff, kmax, kmax, level, nt);
+        int blocks = (kmax + 7) / 8;
+        if (blocks > 256) blocks = 256;
+        k_quad_sum<<<dim3(blocks, 1), 256, 0, st>>>(work, T, c, ks, level, nt, partials, counter, QStride{0, 0, 0});
+    }
+}
+
+int launch_inner_quadrature_hess(const double2* H, int ldH, KState* ks, double2* c, double2* work,
+                                 size_t work_elems, int kmax, double* partials, unsigned int* counter,
+                                 cudaStream_t st) {
+    if (inner_work_elems(kmax, 2) > work_elems) return -1;
+    if ((size_t)kmax * sizeof(float4) > 200u * 1024u) return -1;  // carried column beyond shared memory
+    hess_quad_launch(H, ldH, ks, c, work, kmax, partials, counter, st);
     return 0;
 }
 

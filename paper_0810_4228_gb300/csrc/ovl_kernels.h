@@ -103,6 +103,29 @@ void launch_scale_start(const double2* x, double2* v, double2* y, const double2*
 void launch_combine(const double2* V, size_t ld, const double2* vscale, const double2* c, const KState* ks,
                     int kmax, double2* y, size_t n, cudaStream_t st);
 
+// ---- arnoldi_df.cu: Arnoldi with the basis as double-float pairs (float4 {re.hi, re.lo, im.hi, im.lo}
+// per complex element, n per vector, ld = n) and the Gram-Schmidt sweeps in double-float arithmetic
+void launch_adf_todf(const double2* x, float4* xdf, const KState* ks, size_t n, cudaStream_t st);
+// V_0 = x / nR (double-float) and its FP64 value into x64
+void launch_adf_start(const double2* x, float4* v, double2* x64, const KState* ks, size_t n, cudaStream_t st);
+int adf_dot_blocks(size_t n);
+// h[l] = V_l^dag x for l < nvec (FP64 and double-float copies); partials: nvec * adf_dot_blocks(n) double2
+void launch_adf_dot(const float4* V, size_t ld, int nvec, const float4* x, double2* h, float4* hdf,
+                    double* partials, size_t n, int num_sms, const KState* ks, cudaStream_t st);
+// x -= sum_{l < nvec} h[l] V_l
+void launch_adf_update(const float4* V, size_t ld, int nvec, const float4* hdf, float4* x, size_t n, KState* ks,
+                       double* partials, unsigned int* counter, cudaStream_t st);
+// second update of Arnoldi step j, then H[0..j, j] = h1 + h2, H[j+1, j] = |x|, kused = j + 1, done on a
+// lucky breakdown or at j = jlast
+void launch_adf_update_fin(const float4* V, size_t ld, int nvec, const float4* hdf, float4* x, double2* H, int ldH,
+                           const double2* h1, const double2* h2, int j, int jlast, double* partials,
+                           unsigned int* counter, KState* ks, size_t n, cudaStream_t st);
+// t <- t / |t| (|t| from the last update) and its FP64 value into x64
+void launch_adf_normalize(float4* t, double2* x64, const KState* ks, size_t n, cudaStream_t st);
+// y += sum_{l < kused} c_l V_l; cdf: kmax float4 scratch
+void launch_adf_combine(const float4* V, size_t ld, const double2* c, float4* cdf, const KState* ks, int kmax,
+                        double2* y, size_t n, cudaStream_t st);
+
 // ---- persistent.cu
 bool persistent_ok(const Geom& g, int num_sms);
 int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const w[3], KState* ks, double2* alpha,
@@ -118,6 +141,13 @@ int launch_pass2_persistent(const double2* U64, const float4* Udf, double2* cons
                             const Geom& g, int num_sms, cudaStream_t st);
 
 // ---- inner_sign.cu
+// c[0..n) = nR * sgn(H) e_1 for the upper Hessenberg H (column-major, leading dimension ldH) of
+// size ks->kused, by the same quadrature with Givens-rotation solves of the shifted Hessenberg
+// systems; needs inner_work_elems(kmax, 2) elements of work and kmax * 16 bytes of shared memory
+// per node (-1: too small / too large, nothing launched).
+int launch_inner_quadrature_hess(const double2* H, int ldH, KState* ks, double2* c, double2* work,
+                                 size_t work_elems, int kmax, double* partials, unsigned int* counter,
+                                 cudaStream_t st);
 // c[0..n) = nR * sgn(G) e_1 for the tridiagonal G (alpha, beta, gamma) of size ks->kused, by the
 // resolvent quadrature sgn(G) = (2/pi) int_0^inf G (G^2 + t^2)^-1 dt (see inner_sign.cu).
 int launch_inner_quadrature(const double2* alpha, const double2* beta, const double2* gamma, KState* ks,

@@ -53,8 +53,11 @@ def test_8x4_deflated_arnoldi_and_lanczos2(ovl, mu):
     y2 = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, b)[0].clone()
     ya = ctx.sign_krylov(ovl.ARNOLDI, 1000, mu, KAPPA, b)[0].clone()
     ym = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
+    yad = ctx.sign_krylov(ovl.ARNOLDI, 1000, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
     assert rel(y2.cpu().numpy(), ya.cpu().numpy()) < 1e-9
     assert rel(ym.cpu().numpy(), y2.cpu().numpy()) < 1e-8
+    # double-float Arnoldi: the FP64 Arnoldi process at 48-bit precision
+    assert rel(yad.cpu().numpy(), ya.cpu().numpy()) < 1e-11
     # sgn(A)^2 b = b
     z = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, y2)[0]
     assert rel(z.cpu().numpy(), b.cpu().numpy()) < 1e-8

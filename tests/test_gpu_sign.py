@@ -53,7 +53,22 @@ def test_arnoldi_fp64_matches_dense(ovl, c4):
     assert rel(y, c4["ref"]) < 1e-10
 
 
-@pytest.mark.parametrize("method", ["arnoldi", "lanczos2"])
+def test_arnoldi_doublefloat_matches_dense_and_fp64(ovl, c4):
+    """Arnoldi with the basis and the Gram-Schmidt sweeps in double-float arithmetic (about 48
+    significant bits): the same process as the FP64 run, so within 1e-10 of the dense sgn(A) b at
+    k = 300 and within 1e-11 of the FP64 Arnoldi result at equal k."""
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    y, info = _solve(ovl, ctx, ovl.ARNOLDI, 300, c4["mu"], c4["b"], flags=ovl.MIXED)
+    assert info["status"] == 0 and info["k_used"] == 300
+    assert rel(y, c4["ref"]) < 1e-10
+    y64, _ = _solve(ovl, ctx, ovl.ARNOLDI, 300, c4["mu"], c4["b"])
+    assert rel(y, y64) < 1e-11
+    yo, _ = _solve(ovl, ctx, ovl.ARNOLDI, 300, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.OVERLAP)
+    g5 = np.tile(np.repeat([1.0, 1, -1, -1], 3), 256)
+    assert rel(yo, c4["b"] + g5 * y) < 1e-14
+
+
+@pytest.mark.parametrize("method", ["arnoldi", "arnoldi_df", "lanczos2"])
 @pytest.mark.parametrize("k", [1, 2, 7, 60])
 def test_same_algorithm_parity(ovl, c4, method, k):
     """At equal k the GPU and the oracle run the same algorithm; before the
@@ -61,9 +76,9 @@ def test_same_algorithm_parity(ovl, c4, method, k):
     approximation error itself."""
     A = c4["A"]
     ctx = _ctx(ovl, c4["dims"], c4["U"])
-    if method == "arnoldi":
+    if method.startswith("arnoldi"):
         yo = K.sign_arnoldi(A.dot, c4["b"], k)
-        y, _ = _solve(ovl, ctx, ovl.ARNOLDI, k, c4["mu"], c4["b"])
+        y, _ = _solve(ovl, ctx, ovl.ARNOLDI, k, c4["mu"], c4["b"], flags=ovl.MIXED if method == "arnoldi_df" else 0)
     else:
         Ad = A.conj().T.tocsr()
         yo = K.sign_lanczos2(A.dot, Ad.dot, c4["b"], k)
@@ -92,7 +107,7 @@ def test_overlap_output(ovl, c4):
     assert rel(y, ref) < 1e-10
 
 
-@pytest.mark.parametrize("method", ["arnoldi", "lanczos2"])
+@pytest.mark.parametrize("method", ["arnoldi", "arnoldi_df", "lanczos2"])
 def test_deflated_matches_dense(ovl, c4, method):
     """m = 20 exact eigenpairs of smallest |Re lambda| (Sec. 3, Eq. 3.4; Sec. 4, Eq. 4.5)."""
     lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
@@ -101,18 +116,19 @@ def test_deflated_matches_dense(ovl, c4, method):
     L = np.ascontiguousarray(Xi[idx, :].conj())
     ctx = _ctx(ovl, c4["dims"], c4["U"])
     ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(R), torch_c128(L))
-    m = ovl.ARNOLDI if method == "arnoldi" else ovl.LANCZOS2
-    y, info = _solve(ovl, ctx, m, 300, c4["mu"], c4["b"])
+    m = ovl.LANCZOS2 if method == "lanczos2" else ovl.ARNOLDI
+    fl = ovl.MIXED if method == "arnoldi_df" else 0
+    y, info = _solve(ovl, ctx, m, 300, c4["mu"], c4["b"], flags=fl)
     assert info["status"] == 0
     assert rel(y, c4["ref"]) < 1e-10
     # same algorithm at small k
     defl = Dm.Deflation(lam=lam[idx], R=X[:, idx], L=Xi[idx, :].conj().T)
     A = c4["A"]
-    if method == "arnoldi":
+    if m == ovl.ARNOLDI:
         yo = K.sign_arnoldi(A.dot, c4["b"], 40, defl)
     else:
         yo = K.sign_lanczos2(A.dot, A.conj().T.tocsr().dot, c4["b"], 40, defl)
-    y40, _ = _solve(ovl, ctx, m, 40, c4["mu"], c4["b"])
+    y40, _ = _solve(ovl, ctx, m, 40, c4["mu"], c4["b"], flags=fl)
     assert rel(y40, yo) < 1e-9
 
 
@@ -129,22 +145,55 @@ def test_deflation_biorthonormalises(ovl, c4):
     assert rel(y, c4["ref"]) < 1e-10
 
 
-def test_fully_deflated_source(ovl, c4):
+_METHODS = {"lanczos2": ("LANCZOS2", 0), "arnoldi": ("ARNOLDI", 0), "arnoldi_df": ("ARNOLDI", "MIXED")}
+
+
+def _method(ovl, name):
+    m, f = _METHODS[name]
+    return getattr(ovl, m), (getattr(ovl, f) if f else 0)
+
+
+@pytest.mark.parametrize("method", list(_METHODS))
+def test_fully_deflated_source(ovl, c4, method):
     """b an eigenvector in the deflated set: b_perp = 0 and sgn(A) b is exact."""
     lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
     idx = np.argsort(np.abs(lam.real))[:4]
     ctx = _ctx(ovl, c4["dims"], c4["U"])
     ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(X[:, idx].T.copy()), torch_c128(Xi[idx, :].conj().copy()))
     b = X[:, idx[1]].copy()
-    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 10, c4["mu"], b)
+    m, fl = _method(ovl, method)
+    y, info = _solve(ovl, ctx, m, 10, c4["mu"], b, flags=fl)
     assert info["k_used"] == 0 and info["bperp_norm"] < 1e-12
     assert rel(y, np.sign(lam[idx[1]].real) * b) < 1e-12
 
 
-def test_zero_source(ovl, c4):
+@pytest.mark.parametrize("method", list(_METHODS))
+def test_zero_source(ovl, c4, method):
     ctx = _ctx(ovl, c4["dims"], c4["U"])
-    y, info = _solve(ovl, ctx, ovl.LANCZOS2, 10, c4["mu"], np.zeros_like(c4["b"]))
+    m, fl = _method(ovl, method)
+    y, info = _solve(ovl, ctx, m, 10, c4["mu"], np.zeros_like(c4["b"]), flags=fl)
     assert np.abs(y).max() == 0.0
+
+
+def test_arnoldi_lucky_breakdown(ovl):
+    """A source spanned by a few plane waves of the free field (U = 1) has a Krylov space of
+    small dimension: the Arnoldi process stops early (H[j+1, j] ~ 0, Sec. 2) in FP64 and in
+    double-float, and the result is the closed form."""
+    dims, mu = (4, 4, 4, 4), 0.3
+    V = 256
+    x = np.arange(V)
+    t = x % 4  # t fastest
+    rng = np.random.default_rng(77)
+    spin = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    b = (np.exp(1j * np.pi * (2 * 1 + 1) * t / 4)[:, None] * spin[None, :]).reshape(-1)  # one momentum
+    ref = F.overlap_free_apply(dims, mu, KAPPA, b) - b
+    g5 = np.tile(np.repeat([1.0, 1, -1, -1], 3), V)
+    ref = g5 * ref
+    ctx = _ctx(ovl, dims, synth.free_gauge_field(dims))
+    for fl in (0, ovl.MIXED):
+        y, info = _solve(ovl, ctx, ovl.ARNOLDI, 60, mu, b, flags=fl)
+        assert info["status"] == 0 and info["k_used"] <= 4, info
+        assert rel(y, ref) < 1e-10
 
 
 @pytest.mark.parametrize("flags,tol", [("TWO_PASS", 1e-10), ("MIXED", 1e-8), ("MIXED|STEPWISE", 1e-8)])
@@ -166,6 +215,19 @@ def test_inner_newton_equals_quadrature(ovl, c4):
     y2, i2 = _solve(ovl, ctx, ovl.LANCZOS2, 250, c4["mu"], c4["b"], flags=ovl.INNER_NEWTON)
     assert i1["inner_method"] == 0 and i2["inner_method"] == 1
     assert rel(y1, y2) < 1e-11
+
+
+@pytest.mark.parametrize("method", ["arnoldi", "arnoldi_df"])
+def test_arnoldi_quadrature_equals_newton(ovl, c4, method):
+    """The inner sign of the Hessenberg H_k by the resolvent quadrature (Givens-rotation solves of the
+    shifted systems) and by Roberts' iteration (Sec. 2) agree far below the 1e-10 target."""
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    m, fl = _method(ovl, method)
+    for k in (1, 2, 40, 250):
+        y1, i1 = _solve(ovl, ctx, m, k, c4["mu"], c4["b"], flags=fl)
+        y2, i2 = _solve(ovl, ctx, m, k, c4["mu"], c4["b"], flags=fl | ovl.INNER_NEWTON)
+        assert i1["inner_method"] == 0 and i2["inner_method"] == 1, (k, i1, i2)
+        assert rel(y1, y2) < 1e-11, k
 
 
 def test_host_buffers_and_no_graph(ovl, c4):
@@ -220,13 +282,14 @@ def test_small_ragged_lattices(ovl, dims):
     b = synth.gaussian_source(dims, 42)
     ctx = _ctx(ovl, dims, U)
     N = A.shape[0]
-    if N <= 400:  # Krylov space exhausted: exact (Sec. 2, Eq. 2.1)
-        ref = S.sign_spectral(A.toarray()) @ b
-        y, _ = _solve(ovl, ctx, ovl.ARNOLDI, N, 0.3, b)
-        assert rel(y, ref) < 1e-9
-    k = 150
-    y, _ = _solve(ovl, ctx, ovl.ARNOLDI, k, 0.3, b)
-    assert rel(y, K.sign_arnoldi(A.dot, b, k)) < 1e-9
+    for fl in (0, ovl.MIXED):  # FP64 and double-float Arnoldi
+        if N <= 400:  # Krylov space exhausted: exact (Sec. 2, Eq. 2.1)
+            ref = S.sign_spectral(A.toarray()) @ b
+            y, _ = _solve(ovl, ctx, ovl.ARNOLDI, N, 0.3, b, flags=fl)
+            assert rel(y, ref) < 1e-9
+        k = 150
+        y, _ = _solve(ovl, ctx, ovl.ARNOLDI, k, 0.3, b, flags=fl)
+        assert rel(y, K.sign_arnoldi(A.dot, b, k)) < 1e-9
     k = 40
     yl, _ = _solve(ovl, ctx, ovl.LANCZOS2, k, 0.3, b)
     assert rel(yl, K.sign_lanczos2(A.dot, Ad.dot, b, k)) < 1e-8
@@ -278,6 +341,10 @@ def test_newton_fallback_on_hard_spectrum(ovl):
     yn, infon = _solve(ovl, ctx, ovl.LANCZOS2, 300, 0.3, b, flags=ovl.INNER_NEWTON)
     assert rel(yn, y) < 1e-9
     assert rel(y, ref) < 1e-5
+    for fl in (0, ovl.MIXED):  # Arnoldi: exhausted Krylov space (k = N = 384), exact up to rounding
+        ya, _ = _solve(ovl, ctx, ovl.ARNOLDI, 384, 0.3, b, flags=fl)
+        yan, _ = _solve(ovl, ctx, ovl.ARNOLDI, 384, 0.3, b, flags=fl | ovl.INNER_NEWTON)
+        assert rel(ya, ref) < 1e-8 and rel(yan, ref) < 1e-8
 
 
 @pytest.mark.parametrize("k", [60, 400])
