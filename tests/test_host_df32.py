@@ -1,0 +1,149 @@
+"""CPU test of the double-float arithmetic (csrc/df32.cuh) that the regeneration pass, the inner
+quadrature and the double-float Arnoldi basis run on: its host instantiation (the same header,
+compiled by nvcc for the CPU with FMA contraction off) is checked against exact rational arithmetic
+(fractions.Fraction) on random and adversarial inputs.
+
+Bounds (u = 2^-24, the FP32 unit roundoff): a double split into hi + lo is within u^2 of it; a
+product of two double-float numbers within 8 u^2 of the exact product of their values; a sum
+within 8 u^2 of the sum of the magnitudes; a sum of n products accumulated by dfacc within
+(n + 8) u^2 of the sum of the products' magnitudes.  These are the accuracy claims the kernels'
+tolerances rest on (48 significant bits, 1e-11 agreement with FP64)."""
+import ctypes
+import os
+import random
+import shutil
+import subprocess
+import tempfile
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_0810_4228_gb300", "csrc")
+U2 = Fraction(1, 2 ** 48)
+
+WRAP = r"""
+#include "df32.cuh"
+using ovl::df;
+extern "C" {
+void w_split(double a, float* o) { df x(a); o[0] = x.hi; o[1] = x.lo; }
+void w_mul(float ah, float al, float bh, float bl, float* o) {
+    df z = df(ah, al) * df(bh, bl); o[0] = z.hi; o[1] = z.lo;
+}
+void w_add(float ah, float al, float bh, float bl, float* o) {
+    df z = df(ah, al) + df(bh, bl); o[0] = z.hi; o[1] = z.lo;
+}
+void w_add_lazy(float ah, float al, float bh, float bl, float* o) {
+    df z = ovl::df_add_lazy(df(ah, al), df(bh, bl)); o[0] = z.hi; o[1] = z.lo;
+}
+// sum_i s_i a_i b_i with dfacc (s_i = -1 where neg[i])
+void w_dot(int n, const float* a, const float* b, const int* neg, float* o) {
+    ovl::dfacc A;
+    for (int i = 0; i < n; ++i) {
+        df x(a[2 * i], a[2 * i + 1]), y(b[2 * i], b[2 * i + 1]);
+        if (i == 0) ovl::dfacc_first(A, x, y, neg[i] != 0);
+        else ovl::dfacc_add(A, x, y, neg[i] != 0);
+    }
+    df z = ovl::dfacc_value(A); o[0] = z.hi; o[1] = z.lo;
+}
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    d = tempfile.mkdtemp()
+    src = os.path.join(d, "wrap.cu")
+    with open(src, "w") as f:
+        f.write(WRAP)
+    so = os.path.join(d, "libdfhost.so")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", CSRC,
+                    "-o", so, src], check=True, capture_output=True)
+    L = ctypes.CDLL(so)
+    f, pf, pi = ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)
+    L.w_split.argtypes = [ctypes.c_double, pf]
+    for nm in ("w_mul", "w_add", "w_add_lazy"):
+        getattr(L, nm).argtypes = [f, f, f, f, pf]
+    L.w_dot.argtypes = [ctypes.c_int, pf, pf, pi, pf]
+    return L
+
+
+def _out():
+    return (ctypes.c_float * 2)()
+
+
+def _val(o):
+    return Fraction(float(o[0])) + Fraction(float(o[1]))
+
+
+def _rand_df(rng, scale_exp=20):
+    """A normalised double-float number (hi + lo, |lo| <= ulp(hi)/2) from a random double."""
+    x = rng.uniform(-1, 1) * 2.0 ** rng.randint(-scale_exp, scale_exp)
+    hi = np.float32(x)
+    lo = np.float32(x - float(hi))
+    return float(hi), float(lo)
+
+
+def test_split_of_a_double(lib):
+    rng = random.Random(1)
+    for _ in range(2000):
+        x = rng.uniform(-1, 1) * 2.0 ** rng.randint(-60, 60)
+        o = _out()
+        lib.w_split(x, o)
+        assert abs(_val(o) - Fraction(x)) <= U2 * abs(Fraction(x))
+        assert abs(o[1]) <= abs(o[0]) * 2.0 ** -23  # normalised: lo below ulp(hi)
+    o = _out()
+    lib.w_split(0.0, o)
+    assert o[0] == 0.0 and o[1] == 0.0
+
+
+def test_product(lib):
+    rng = random.Random(2)
+    for _ in range(3000):
+        a, b = _rand_df(rng), _rand_df(rng)
+        o = _out()
+        lib.w_mul(a[0], a[1], b[0], b[1], o)
+        exact = (Fraction(a[0]) + Fraction(a[1])) * (Fraction(b[0]) + Fraction(b[1]))
+        assert abs(_val(o) - exact) <= 8 * U2 * abs(exact)
+
+
+@pytest.mark.parametrize("lazy", [False, True])
+def test_sum_including_cancellation(lib, lazy):
+    rng = random.Random(3)
+    fn = lib.w_add_lazy if lazy else lib.w_add
+    for it in range(3000):
+        a = _rand_df(rng)
+        if it % 3 == 0:  # near cancellation: b close to -a
+            b0 = -a[0]
+            b = (b0, float(np.float32(-a[1] * rng.uniform(0.5, 1.5))))
+        else:
+            b = _rand_df(rng)
+        o = _out()
+        fn(a[0], a[1], b[0], b[1], o)
+        A, B = Fraction(a[0]) + Fraction(a[1]), Fraction(b[0]) + Fraction(b[1])
+        assert abs(_val(o) - (A + B)) <= 8 * U2 * (abs(A) + abs(B))
+
+
+@pytest.mark.parametrize("n", [1, 4, 24, 200])
+def test_sum_of_products(lib, n):
+    """dfacc: the link products (n = 6 complex terms), the sweeps' per-lane sums (n up to a few
+    hundred) and the quadrature's solves all reduce to sums of products like this one."""
+    rng = random.Random(10 + n)
+    for _ in range(200):
+        xs = [_rand_df(rng, 6) for _ in range(n)]
+        ys = [_rand_df(rng, 6) for _ in range(n)]
+        neg = [rng.random() < 0.5 for _ in range(n)]
+        a = (ctypes.c_float * (2 * n))(*[v for p in xs for v in p])
+        b = (ctypes.c_float * (2 * n))(*[v for p in ys for v in p])
+        s = (ctypes.c_int * n)(*[int(v) for v in neg])
+        o = _out()
+        lib.w_dot(n, a, b, s, o)
+        terms = [(Fraction(x[0]) + Fraction(x[1])) * (Fraction(y[0]) + Fraction(y[1])) * (-1 if g else 1)
+                 for x, y, g in zip(xs, ys, neg)]
+        exact = sum(terms, Fraction(0))
+        mag = sum((abs(t) for t in terms), Fraction(0))
+        assert abs(_val(o) - exact) <= (n + 8) * U2 * mag
