@@ -308,7 +308,9 @@ class Context:
         return out
 
     def sign_krylov(self, method: int, k: int, mu: float, kappa: float, b, out=None, flags: int = 0):
-        """out = sgn(gamma5 D_w(mu)) b, or D_ov(mu) b with flags |= OVERLAP.
+        """out = sgn(gamma5 D_w(mu)) b, or D_ov(mu) b with flags |= OVERLAP, by ARNOLDI or LANCZOS2.
+        flags |= MIXED: two-sided Lanczos in two passes (FP32 pass 1, FP64-accurate regeneration);
+        Arnoldi with its basis and Gram-Schmidt sweeps in double-float arithmetic.
         Returns (out, info dict).  b may be a CUDA tensor or host memory."""
         import torch
         if out is None:
