@@ -57,13 +57,22 @@ __global__ void k_adf_start(const double2* __restrict__ x, float4* __restrict__ 
 }
 
 // ---------------------------------------------------------- many-vector dot --
-// The sweeps stream the basis from HBM with one 16-byte load per lane and a chain of dependent
-// double-float operations behind it, so a warp has about one load in flight; L2 prefetches a
-// fixed distance ahead (no registers held) keep more bytes in flight per SM.
-static constexpr int AD_PF = 256;  // dot: elements ahead within the warp's vector chunk(s)
+// The update sweep streams the basis from HBM with one 16-byte load per lane and a chain of
+// dependent double-float operations behind it, so a warp has about one load in flight; L2
+// prefetches a fixed distance ahead (no registers held) keep more bytes in flight per SM.
 static constexpr int AD_PFV = 4;   // update: vectors (of this warp) ahead
 __device__ __forceinline__ void prefetch_l2(const float4* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+// 16-byte asynchronous global -> shared copies (completion waited for per thread with
+// cp.async.wait_group, a hardware wait)
+__device__ __forceinline__ void cp_async16(float4* smem, const float4* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // re + i im += conj(v) x
@@ -83,35 +92,65 @@ __device__ __forceinline__ void adf_axpy_term(dfacc& re, dfacc& im, const cx<df>
 
 // stage 1, grid (chunks, vector groups): block (c, g) stages elements [c*AD_CH, (c+1)*AD_CH) of
 // x in shared memory; warp w forms the partial dots V_l^dag x over that chunk for
-// l = g*vpb + w, g*vpb + w + AD_W, ... < min(nvec, (g+1)*vpb).
+// l = g*vpb + w, g*vpb + w + AD_W, ... < min(nvec, (g+1)*vpb).  The warp streams its
+// (vector, tile of AD_SUB elements) pieces through two shared-memory tiles: the copy of the next
+// tile is in flight while the current one is summed, so every warp keeps 4 KB of the basis in
+// flight instead of one 16-byte load per lane.
+static constexpr int AD_SUB = 256;
+static size_t adf_dot_smem() { return sizeof(float4) * ((size_t)AD_CH + (size_t)AD_W * 2 * AD_SUB); }
+
 __global__ void __launch_bounds__(AD_T) k_adf_dot(const float4* __restrict__ V, size_t ld, int nvec, int vpb,
                                                   const float4* __restrict__ x, double2* __restrict__ part,
                                                   size_t n, const KState* ks) {
-    __shared__ float4 xs[AD_CH];
+    extern __shared__ float4 adf_sm[];
+    float4* xs = adf_sm;
     if (ks->done || ks->status) return;
     const size_t base = (size_t)blockIdx.x * AD_CH;
     const int lim = (int)(n - base < (size_t)AD_CH ? n - base : (size_t)AD_CH);
     for (int q = threadIdx.x; q < lim; q += AD_T) xs[q] = x[base + q];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int l0 = blockIdx.y * vpb;
-    const int l1 = min(nvec, l0 + vpb);
-    for (int l = l0 + wid; l < l1; l += AD_W) {
-        const float4* Vl = V + (size_t)l * ld + base;
-        dfacc re = {0.f, 0.f}, im = {0.f, 0.f};
-        // the next vector of this warp, for the prefetches that run past the end of this one
-        const float4* Vn = l + AD_W < l1 ? V + (size_t)(l + AD_W) * ld + base : nullptr;
-#pragma unroll 4
-        for (int q = lane; q < lim; q += 32) {
-            if ((lane & 7) == 0) {  // one lane per 128-byte line
-                const int tq = q + AD_PF;
-                if (tq < lim) prefetch_l2(Vl + tq);
-                else if (Vn && tq - lim < lim) prefetch_l2(Vn + (tq - lim));
-            }
-            adf_dot_term(re, im, from_f4(__ldg(Vl + q)), from_f4(xs[q]));
+    float4* wb = adf_sm + AD_CH + (size_t)wid * 2 * AD_SUB;
+    const int l0 = blockIdx.y * vpb + wid;
+    const int l1 = min(nvec, blockIdx.y * vpb + vpb);
+    const int nv = l0 < l1 ? (l1 - l0 + AD_W - 1) / AD_W : 0;
+    const int ntile = (lim + AD_SUB - 1) / AD_SUB;
+    const int total = nv * ntile;
+    // each lane copies (and later reads) the elements lane, lane + 32, ... of a tile
+    auto issue = [&](int it) {
+        const int a = it / ntile, si = it - a * ntile;
+        const float4* src = V + (size_t)(l0 + a * AD_W) * ld + base + (size_t)si * AD_SUB;
+        float4* dst = wb + (it & 1) * AD_SUB;
+        const int cnt = min(AD_SUB, lim - si * AD_SUB);
+        for (int u = lane; u < cnt; u += 32) cp_async16(dst + u, src + u);
+        cp_async_commit();
+    };
+    if (total > 0) issue(0);
+    dfacc re = {0.f, 0.f}, im = {0.f, 0.f};
+    for (int it = 0; it < total; ++it) {
+        if (it + 1 < total) {
+            issue(it + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        const df sr = warp_sum_df(dfacc_value(re)), si = warp_sum_df(dfacc_value(im));
-        if (lane == 0) part[(size_t)l * gridDim.x + blockIdx.x] = make_double2(sr.to_double(), si.to_double());
+        __syncwarp();
+        const int a = it / ntile, si = it - a * ntile;
+        const float4* cur = wb + (it & 1) * AD_SUB;
+        const float4* xt = xs + si * AD_SUB;
+        const int cnt = min(AD_SUB, lim - si * AD_SUB);
+        if (si == 0) {
+            re = {0.f, 0.f};
+            im = {0.f, 0.f};
+        }
+#pragma unroll 4
+        for (int u = lane; u < cnt; u += 32) adf_dot_term(re, im, from_f4(cur[u]), from_f4(xt[u]));
+        if (si == ntile - 1) {
+            const df sr = warp_sum_df(dfacc_value(re)), si2 = warp_sum_df(dfacc_value(im));
+            if (lane == 0)
+                part[(size_t)(l0 + a * AD_W) * gridDim.x + blockIdx.x] = make_double2(sr.to_double(), si2.to_double());
+        }
+        __syncwarp();  // this tile's buffer receives the copy issued two iterations on
     }
 }
 
@@ -300,7 +339,14 @@ void launch_adf_dot(const float4* V, size_t ld, int nvec, const float4* x, doubl
     const int vpb = (int)(vpw * AD_W);
     const int ngroup = (nvec + vpb - 1) / vpb;
     double2* part = reinterpret_cast<double2*>(partials);
-    k_adf_dot<<<dim3(nchunk, ngroup), AD_T, 0, st>>>(V, ld, nvec, vpb, x, part, n, ks);
+    static int smem_dev_mask = 0;  // devices on which the shared-memory limit was raised
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 31 || !(smem_dev_mask & (1 << dev))) {
+        cudaFuncSetAttribute(k_adf_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adf_dot_smem());
+        if (dev < 31) smem_dev_mask |= 1 << dev;
+    }
+    k_adf_dot<<<dim3(nchunk, ngroup), AD_T, adf_dot_smem(), st>>>(V, ld, nvec, vpb, x, part, n, ks);
     k_adf_dot_reduce<<<(nvec + 7) / 8, 256, 0, st>>>(part, nchunk, nvec, h, hdf, ks);
 }
 
