@@ -66,7 +66,7 @@ def peaks():
 
 # FP64 ALU roof: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz = 1.259 TFLOP/s
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# algorithmic work per site (see DESIGN.md): Wilson hopping term 1320 flop, diagonal and
+# algorithmic work per site: Wilson hopping term 1320 flop, diagonal and
 # gamma5 48 flop; FP64 bytes: 4 links (576) + x (192) + y (192)
 DW_FLOP_SITE = 1368
 DW_BYTES = {"f64": 960, "f32_12": 384, "f32_18": 480}

@@ -5,7 +5,7 @@ Eq. 1.2 (D_w(mu) = 1 - kappa sum_i (T_i^+ + T_i^-)
                      - kappa (e^mu T_4^+ + e^-mu T_4^-)),
 and the hopping terms T_nu^+-, kappa = 1/(8 + 2 m_w), U in SU(3).
 
-Readings taken where the paper is silent or ambiguous (listed in the design doc):
+Readings taken where the paper is silent or ambiguous:
 
 * T_nu^+ is the hop to the forward neighbour with projector (1 + gamma_nu):
   (T_nu^+ psi)(x) = (1 + gamma_nu) U_{x,nu} psi(x + nu);
