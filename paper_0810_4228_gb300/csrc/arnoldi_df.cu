@@ -339,13 +339,9 @@ void launch_adf_dot(const float4* V, size_t ld, int nvec, const float4* x, doubl
     const int vpb = (int)(vpw * AD_W);
     const int ngroup = (nvec + vpb - 1) / vpb;
     double2* part = reinterpret_cast<double2*>(partials);
-    static int smem_dev_mask = 0;  // devices on which the shared-memory limit was raised
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 31 || !(smem_dev_mask & (1 << dev))) {
+    static unsigned long long attr_dev = 0;
+    if (first_use_on_device(attr_dev))
         cudaFuncSetAttribute(k_adf_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adf_dot_smem());
-        if (dev < 31) smem_dev_mask |= 1 << dev;
-    }
     k_adf_dot<<<dim3(nchunk, ngroup), AD_T, adf_dot_smem(), st>>>(V, ld, nvec, vpb, x, part, n, ks);
     k_adf_dot_reduce<<<(nvec + 7) / 8, 256, 0, st>>>(part, nchunk, nvec, h, hdf, ks);
 }

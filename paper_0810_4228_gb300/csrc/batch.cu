@@ -1100,8 +1100,8 @@ void pass1_step(ovl_batch* b, int i, int k, double mu, double kappa, bool mixed,
 template <int MINB>
 void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStream_t st) {
     const size_t smr = (size_t)8 * ovl::TT * 6 * 16;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr_dev = 0;
+    if (ovl::first_use_on_device(attr_dev)) {
         cudaFuncSetAttribute(ovl::k_b_regen<ovl::df, ovl::LINK_DF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smr);
         cudaFuncSetAttribute(ovl::k_b_regen<double, ovl::LINK_F64, MINB>,
@@ -1110,7 +1110,6 @@ void regen_step(ovl_batch* b, int i, double mu, double kappa, bool dfm, cudaStre
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smr));
         cudaFuncSetAttribute(ovl::k_b_regen2<double, ovl::LINK_F64, MINB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smr));
-        attr = true;
     }
     const ovl::BSeq* S = b->dseq;
     if (b->regen_pair) {

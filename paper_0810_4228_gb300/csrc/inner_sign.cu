@@ -496,10 +496,13 @@ static void hess_quad_launch(const double2* H, int ldH, KState* ks, double2* c, 
     if (wpb > HQ_WPB_MAX) wpb = HQ_WPB_MAX;
     if (wpb < 1) wpb = 1;
     const size_t smem = per_warp * wpb;
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-        cudaFuncSetAttribute(k_hess_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        smem_set = smem;
+    // the limit needed grows with kmax: kept per device (the attribute is per device)
+    static size_t smem_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (smem > 48 * 1024 && smem > smem_set[dev]) {
+        if (cudaFuncSetAttribute(k_hess_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+            smem_set[dev] = smem;
     }
     for (int level = 0; level < QUAD_LEVELS; ++level) {
         const int nt = quad_threads(level);
@@ -752,11 +755,9 @@ int launch_inner_newton(const double2* alpha, const double2* beta, const double2
     NewtonWork w = newton_layout(work, kmax);
     const int max_it = 40;
     const size_t smem = sizeof(double2) * kmax;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static unsigned long long attr_dev = 0;
+    if (first_use_on_device(attr_dev))
         cudaFuncSetAttribute(k_newton_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
     k_newton_bar_reset<<<1, 1, 0, st>>>(w);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(num_sms);

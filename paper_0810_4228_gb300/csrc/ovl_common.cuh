@@ -13,6 +13,18 @@
 
 namespace ovl {
 
+// True the first time it is called on the current device with this `seen` mask (one bit per device
+// ordinal below 64; always true beyond): kernel attributes such as the dynamic shared-memory limit
+// belong to the device they are set on, so a launcher sets them once per device.
+inline bool first_use_on_device(unsigned long long& seen) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    const unsigned long long bit = 1ull << dev;
+    if (seen & bit) return false;
+    seen |= bit;
+    return true;
+}
+
 // ---------------------------------------------------------------- complex --
 template <class R> struct cx {
     R r, i;

@@ -602,12 +602,10 @@ int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const
     a.hw = make_coef<float>(-mu, kappa);
     a.g = g;
     a.k = k;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr_dev = 0;
+    if (first_use_on_device(attr_dev))
         cudaFuncSetAttribute(k_pass1_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pass1_smem(PMAX_TPB));
-        attr = true;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(32 * PW1);
@@ -624,12 +622,10 @@ int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const
 template <class R, int LF>
 static int launch_p2(P2Args<R> a, HopCoef<R> hc, int G, int tpb, cudaStream_t st) {
     a.hc[0] = hc;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr_dev = 0;
+    if (first_use_on_device(attr_dev))
         cudaFuncSetAttribute(k_pass2_persistent<R, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pass2_smem(PMAX_TPB));
-        attr = true;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(32 * PW2);

@@ -327,12 +327,10 @@ void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, v
                         double kappa, KState* ks, double2* alpha, int step, int klast, double* partials,
                         unsigned int* counter, const Geom& g, cudaStream_t st) {
     if (pick_ds(g)) {
-        static bool attr = false;
-        if (!attr) {
+        static unsigned long long attr_dev = 0;
+        if (first_use_on_device(attr_dev))
             cudaFuncSetAttribute(k_dslash_pair_ds<LINK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ds_smem(16, 2));
-            attr = true;
-        }
         if (prec == 0)
             k_dslash_pair_ds<LINK_F64><<<ds_grid(g), 128, ds_smem(16, 2), st>>>(
                 U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s, make_coef<double>(mu, kappa),
