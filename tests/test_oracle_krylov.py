@@ -175,6 +175,30 @@ def test_free_field_4x4_closed_form(gauge):
     assert _rel(b + g5 * yl, ref) < 1e-10
 
 
+def test_free_plane_wave_two_steps():
+    """On the free field a source of one momentum p (any spin-colour part) spans an
+    A-invariant space of dimension two: A(p) = 2 kappa gamma5 (a - i gamma.s) gives
+    A(p)^2 = 4 kappa^2 (a^2 + s.s) (gamma5 anticommutes with every gamma_nu), so the Arnoldi
+    process stops with a lucky breakdown after two steps and its result is the closed form."""
+    dims, mu, kappa = (4, 4, 4, 4), 0.3, 0.2
+    V = 256
+    t = np.arange(V) % 4  # time fastest
+    rng = np.random.default_rng(77)
+    spin = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    b = (np.exp(1j * np.pi * 3 * t / 4)[:, None] * spin[None, :]).reshape(-1)  # p_4 = 3 pi / 4
+    A = W.a_operator(synth.free_gauge_field(dims), dims, mu, kappa)
+    # A^2 b is a multiple of b, with the closed-form factor
+    p4 = 3 * np.pi / 4 - 1j * mu
+    a = -1.5 + (1 - np.cos(p4))  # m_w = 1/(2 kappa) - 4 = -1.5; spatial momenta zero
+    ss = np.sin(p4) ** 2
+    np.testing.assert_allclose(A.dot(A.dot(b)), 4 * kappa ** 2 * (a * a + ss) * b, rtol=1e-12, atol=1e-12)
+    _, H, _ = K.arnoldi(A.dot, b, 10)
+    assert H.shape[1] == 2 and abs(H[2, 1]) < 1e-13
+    g5 = np.tile(np.repeat([1.0, 1, -1, -1], 3), V)
+    ref = F.overlap_free_apply(dims, mu, kappa, b)
+    assert _rel(b + g5 * K.sign_arnoldi(A.dot, b, 10), ref) < 1e-12
+
+
 def test_breakdowns():
     """Lucky breakdown (v_hat = 0: K_1 is invariant, the process stops and the
     result is exact) and serious breakdown (v_hat, w_hat nonzero, w_hat^dag
