@@ -349,6 +349,77 @@ def calibrate_batch(torch, bt, srcs, refs, flags, grid):
     return chosen, err
 
 
+# row a10: per site of ovl_dw_grad, algorithmic bytes (x 192 + g 192 read, the link force
+# 36 complex = 576 written, the temporal link 144 read for d/dmu) and FP64 operations counted
+# from the kernel (per direction two projections and 72 complex multiply-adds of the
+# spin-traced colour outer products, about 780; the d/dmu term about 460)
+DWGRAD_BYTES_SITE = 192 + 192 + 576 + 144
+DWGRAD_FLOP_SITE = 4 * 780 + 460
+
+
+def autograd_timing(torch, ovl, U_np, b, flush, k=800, gdims=(24, 24, 24, 24)):
+    """Row a10 on the GPU.  ovl_sign_grad (derivatives of Re <g, sgn(A) b> with respect to the links,
+    mu and b, resolvent form: one FP64 two-sided Lanczos process from (b, g)) on the 8^4 workload at
+    k = 800 (where the 8^4 gradient test meets central differences to 1e-5), against the FP64
+    forward solve at the same k; ovl_dw_grad (adjoint of y = A x: link force and d/dmu) on a lattice
+    far larger than L2.  CUDA events on the library's stream around each call (each call ends with
+    its own host synchronisation, included).  Failures are reported, not raised."""
+    from paper_0810_4228_gb300 import synth
+    out = {}
+
+    def timed(fn, reps):
+        st = torch.cuda.current_stream()
+        ts = []
+        for i in range(reps + 1):  # the first call warms up
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[1:])
+
+    try:
+        lat = ovl.Context(DIMS)
+        lat.set_gauge(torch.from_numpy(U_np).cuda())
+        g = torch.from_numpy(synth.gaussian_source(DIMS, SEED_B + 600)).cuda()
+        bb = b.clone()
+        gU = torch.empty((lat.V, 4, 3, 3), dtype=torch.complex128, device="cuda")
+        gb, y = torch.empty_like(bb), torch.empty_like(bb)
+        t_grad = timed(lambda: lat.sign_grad(k, MU, KAPPA, bb, g, y=y, grad_U=gU, grad_b=gb), 3)
+        t_fwd = timed(lambda: lat.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, bb, y), 3)
+        out["sign_grad_8x4"] = {"k": k, "ms": round(t_grad, 3), "forward_fp64_ms": round(t_fwd, 3),
+                                "ratio_to_forward": round(t_grad / t_fwd, 2),
+                                "outputs": "sgn(A) b, grad_U, grad_mu, grad_b"}
+        lat.close()
+        del gU, gb, y, g, bb
+    except Exception as exc:  # report, keep the rest of the line
+        out["sign_grad_8x4"] = {"error": repr(exc)[:200]}
+    try:
+        V2 = gdims[0] * gdims[1] * gdims[2] * gdims[3]
+        lat2 = ovl.Context(gdims)
+        U2 = synth.gauge_field_torch(gdims, EPS, SEED_U + 7, device="cuda")
+        lat2.set_gauge(U2)
+        del U2
+        x = torch.randn(V2 * 12, dtype=torch.complex128, device="cuda")
+        gg = torch.randn(V2 * 12, dtype=torch.complex128, device="cuda")
+        gU2 = torch.empty((V2, 4, 3, 3), dtype=torch.complex128, device="cuda")
+        ms = timed(lambda: lat2.dw_grad(MU, KAPPA, x, gg, gU2), 10)
+        out["dw_grad"] = {"dims": list(gdims), "sites": V2, "ms": round(ms, 4),
+                          "GB_s": round(DWGRAD_BYTES_SITE * V2 / ms / 1e6, 1),
+                          "GFLOP_s": round(DWGRAD_FLOP_SITE * V2 / ms / 1e6, 1),
+                          "frac_fp64_roof": round(DWGRAD_FLOP_SITE * V2 / ms / 1e9 / FP64_PEAK_TFLOPS, 3),
+                          "bytes_per_site": DWGRAD_BYTES_SITE, "flop_per_site": DWGRAD_FLOP_SITE,
+                          "bound": "FP64 ALU (3.2 flop/B against 0.19 at the FP64 roof)"}
+        lat2.close()
+        del x, gg, gU2
+        torch.cuda.empty_cache()
+    except Exception as exc:  # report, keep the rest of the line
+        out["dw_grad"] = {"error": repr(exc)[:200]}
+    return out
+
+
 def multi_lattice_batch(torch, ovl, flush):
     """12 point sources on each of four lattices of different sizes, 20 deflated eigenpairs each,
     mixed vs FP64, timed once."""
@@ -568,6 +639,14 @@ def run_ours(args, world, rank, local):
         except Exception as exc:  # report, keep the headline measurement
             multi = {"error": repr(exc)[:200]}
 
+    # ---- row a10: the gradients (sign function and stencil adjoint)
+    grads = None
+    if rank == 0 and not args.no_grad:
+        try:
+            grads = autograd_timing(torch, ovl, U, srcs[0], flush)
+        except Exception as exc:  # report, keep the headline measurement
+            grads = {"error": repr(exc)[:200]}
+
     # ---- stencil bandwidth on a lattice far larger than L2
     dw = None
     if rank == 0 and not args.no_dw:
@@ -626,6 +705,7 @@ def run_ours(args, world, rank, local):
             "profile_ms_per_batch": {kk: round(v, 4) for kk, v in prof.items()},
             "multi_lattice_batch": multi,
             "dw": dw,
+            "autograd": grads,
         }
         print(json.dumps(line))
     bt.close()
@@ -644,6 +724,7 @@ def main():
     ap.add_argument("--no-dw", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the four-lattice point-source batch")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient timings")
     ap.add_argument("--single", action="store_true", help="with --solves-only: single-source solves instead of batches")
     ap.add_argument("--dw-only", action="store_true", help="only the stencil bandwidth measurement (--steps repetitions)")
     ap.add_argument("--dw-dims", default="", help="lattice of the stencil bandwidth measurement, e.g. 32,32,32,32")
