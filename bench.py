@@ -578,6 +578,27 @@ def run_ours(args, world, rank, local):
                       bsingle, 2, nctx, flush)
     t_s64 = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s64, MU, KAPPA, b, out1, flags=fl_64),
                         bsingle, 2, nctx, flush)
+    # the single-source mixed solve by kernel class (rows a1-a8; CUDA events around each class,
+    # eager launches), and the optional re-projection of the deflated directions in pass 1 (row a4)
+    single_profile, reproj = None, None
+    try:
+        ctx.profile(reset=True)
+        ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, srcs[0], out1, flags=fl_mix | ovl.PROFILE)
+        torch.cuda.synchronize()
+        single_profile = {kk: round(v["ms"], 4) for kk, v in ctx.profile(reset=True).items() if v.get("launches")}
+    except Exception as exc:  # report, keep the rest of the line
+        single_profile = {"error": repr(exc)[:200]}
+    try:
+        t_rp = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, b, out1,
+                                                                 flags=fl_mix | ovl.REPROJ), bsingle, 2, nctx, flush)
+        reproj = {"k": k_s, "ms": round(statistics.mean(t_rp), 3),
+                  "ms_without": round(statistics.mean(t_s), 3), "m": args.m}
+        if not args.k:
+            yr = ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, srcs[0], flags=ovl.MIXED | ovl.REPROJ)[0]
+            reproj["rel_err_vs_k1000_fp64"] = (torch.linalg.vector_norm(yr - refs[0]) /
+                                               torch.linalg.vector_norm(refs[0])).item()
+    except Exception as exc:  # report, keep the rest of the line
+        reproj = {"error": repr(exc)[:200]}
     t_arn = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_arn, MU, KAPPA, b, out1,
                                                               flags=ovl.OVERLAP), bsingle, 1, 2, flush)
     t_adf = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_adf, MU, KAPPA, b, out1,
@@ -692,7 +713,9 @@ def run_ours(args, world, rank, local):
             "fp64_batched": {"solves_per_s": NRHS * 1e3 / statistics.mean(t_b64), "ms_per_batch": statistics.mean(t_b64),
                              "k": k_64, "max_rel_err_vs_k1000_fp64": err_64},
             "mixed_single_source": {"solves_per_s": 1e3 / statistics.mean(t_s), "ms": statistics.mean(t_s), "k": k_s,
-                                    "rel_err_vs_k1000_fp64": err_s, "kernels": "persistent passes"},
+                                    "rel_err_vs_k1000_fp64": err_s, "kernels": "persistent passes",
+                                    "profile_ms_by_kernel_class": single_profile,
+                                    "with_reprojection": reproj},
             "fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_s64), "ms": statistics.mean(t_s64),
                                    "k": k_s64, "rel_err_vs_k1000_fp64": err_s64},
             "arnoldi_fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_arn), "ms": statistics.mean(t_arn),
