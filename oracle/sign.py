@@ -10,12 +10,15 @@
   |det S|^(-1/n) scaling of the first iterates (the iteration converges to
   the same limit; scaling only shortens the initial phase).
 * ``overlap_dense``: D_ov = 1 + gamma5 sgn(gamma5 D_w) (Eq. 1.1).
+* ``overlap_eigenvalues``: the spectrum of that D_ov, nearest 0 first (the eigenvalue problem
+  the closing remark of Sec. 5 names as the methods' next application; the paper gives no
+  method for it, so the definition is the dense eigendecomposition).
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["csign", "sign_spectral", "sign_newton", "overlap_dense", "SignError"]
+__all__ = ["csign", "sign_spectral", "sign_newton", "overlap_dense", "overlap_eigenvalues", "SignError"]
 
 
 class SignError(ArithmeticError):
@@ -77,3 +80,9 @@ def overlap_dense(A: np.ndarray, gamma5_diag: np.ndarray, sign=None) -> np.ndarr
     """
     S = sign_spectral(A) if sign is None else sign
     return np.eye(A.shape[0], dtype=np.complex128) + gamma5_diag[:, None] * S
+
+
+def overlap_eigenvalues(A: np.ndarray, gamma5_diag: np.ndarray, sign=None) -> np.ndarray:
+    """All eigenvalues of D_ov = 1 + gamma5 sgn(A) (Eq. 1.1), sorted by modulus (nearest 0 first)."""
+    w = np.linalg.eigvals(overlap_dense(A, gamma5_diag, sign))
+    return w[np.argsort(np.abs(w), kind="stable")]
