@@ -332,7 +332,8 @@ void launch_adf_dot(const float4* V, size_t ld, int nvec, const float4* x, doubl
                     double* partials, size_t n, int num_sms, const KState* ks, cudaStream_t st) {
     if (nvec <= 0) return;
     const int nchunk = adf_dot_blocks(n);
-    // vectors per warp: about eight resident blocks per SM in total, at least one vector per warp
+    // vectors per warp: about eight blocks per SM in total (four waves of the two that fit an SM with
+    // their 80 KB of shared memory), at least one vector per warp
     const long long target = 8ll * (num_sms > 0 ? num_sms : 1);
     long long vpw = ((long long)nvec * nchunk + (long long)AD_W * target - 1) / ((long long)AD_W * target);
     if (vpw < 1) vpw = 1;
