@@ -159,7 +159,9 @@ int ovl_apply_pair(ovl_ctx* ctx, double mu, double kappa, int prec,
  *   - alpha_dev: DEVICE pointer to 2 doubles receiving alpha = w^dag t; nothing is copied
  *     to the host and the call does not synchronise (read alpha after the stream's work).
  *   - the context and its gauge field must exist already (they allocate when created).
- *   - lattices above 8388608 sites are rejected with OVL_EINVAL.
+ *   - lattices whose pair kernel needs more than 32768 thread blocks (more than 4194304
+ *     sites; ovl_apply_pair_noalloc_blocks tells) are rejected with OVL_EINVAL before any
+ *     launch.
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *     no allocation); make that first call before any stream capture that includes it.
  *   - all calls share the array and it keeps the last call's contents; each call resets
@@ -167,6 +169,14 @@ int ovl_apply_pair(ovl_ctx* ctx, double mu, double kappa, int prec,
  *     once) race on it and give wrong results. */
 int ovl_apply_pair_noalloc(ovl_ctx* ctx, double mu, double kappa, int prec,
                            const void* v, const void* w, void* t, void* s, double* alpha_dev);
+
+/* Host-only size check for ovl_apply_pair_noalloc (no GPU call, no context): *blocks = the
+ * number of thread blocks the pair kernel launches on a lattice of extents dims[4] (the same
+ * function decides the launch), *max_blocks (may be NULL) = the most the static scratch holds
+ * (32768).  Returns OVL_OK when the lattice fits, OVL_EINVAL when it does not or when dims is
+ * not a valid lattice (an extent below 2 or an odd time extent; *blocks is then 0).  The paper
+ * has no counterpart. */
+int ovl_apply_pair_noalloc_blocks(const int dims[4], int* blocks, int* max_blocks);
 
 /* Adjoint of y = A x, A = gamma5 D_w(mu; U) (Eq. 1.2), for a real function l(y), in PyTorch's
  * convention for complex gradients (g_z = dl/dRe z + i dl/dIm z, so dl = Re <g_z, dz>): given

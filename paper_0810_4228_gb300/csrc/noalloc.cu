@@ -13,7 +13,10 @@
 //
 // Limits and sharing: the static array holds the partial sums of at most
 // 32768 thread blocks (768 KiB in total, resident on every
-// GPU that loads the library until the process exits).  Every call shares
+// GPU that loads the library until the process exits).  The block count is
+// the pair kernel's own grid (dslash_pair_blocks, the function its launcher
+// uses): one block per 64 sites of each parity on large lattices, so at most
+// 4194304 sites.  Every call shares
 // the array and it keeps the last call's contents; the counter and state
 // record are cleared at the start of each call, so calls must not overlap on
 // the GPU (two concurrent calls on different streams race on the array).
@@ -69,15 +72,35 @@ __global__ void k_noalloc_reset(double* scratch) {
 
 }  // namespace
 
+extern "C" int ovl_apply_pair_noalloc_blocks(const int dims[4], int* blocks, int* max_blocks) {
+    if (max_blocks) *max_blocks = kMaxBlocks;
+    if (!dims || !blocks) return OVL_EINVAL;
+    *blocks = 0;
+    long long V = 1;
+    for (int d = 0; d < 4; ++d) {
+        if (dims[d] < 2) return OVL_EINVAL;
+        V *= dims[d];
+    }
+    if (dims[3] % 2 || V > (1ll << 28)) return OVL_EINVAL;
+    ovl::Geom g = {};
+    for (int d = 0; d < 4; ++d) g.L[d] = dims[d];
+    g.L4h = dims[3] / 2;
+    g.V = (int)V;
+    g.Vh = (int)(V / 2);
+    g.bc_t = -1;
+    *blocks = ovl::dslash_pair_blocks(g);
+    return *blocks <= kMaxBlocks ? OVL_OK : OVL_EINVAL;
+}
+
 extern "C" int ovl_apply_pair_noalloc(ovl_ctx* c, double mu, double kappa, int prec, const void* v, const void* w,
                                       void* t, void* s, double* alpha_dev) {
     if (!c || prec < 0 || prec > 1) return fail(c, OVL_EINVAL, "bad argument");
-    // the pair kernel uses one block per 32 sites (small lattices) or per 128 sites
-    const int blocks = c->g.V < 152 * 1024 ? (c->g.V + 31) / 32 : (c->g.Vh + 127) / 128;
+    // the grid the pair launcher will use: one partial-sum slot per block
+    const int blocks = ovl::dslash_pair_blocks(c->g);
     if (blocks > kMaxBlocks)
         return fail(c, OVL_EINVAL,
-                    "lattice too large for ovl_apply_pair_noalloc: at most 8388608 sites (its static scratch "
-                    "holds the partial sums of 32768 thread blocks)");
+                    "lattice too large for ovl_apply_pair_noalloc: at most 4194304 sites (its static scratch "
+                    "holds the partial sums of 32768 thread blocks, one per 64 sites of each parity)");
     if (!v || !w || !t || !s || !alpha_dev) return fail(c, OVL_EINVAL, "null argument");
     if (!c->have_gauge) return fail(c, OVL_ESTATE, "gauge field not set");
     int dev = 0;

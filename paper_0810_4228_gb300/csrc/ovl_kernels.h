@@ -59,6 +59,8 @@ void launch_dslash_regen(const double2* U, const double2* vi, const double2* vim
                          double mu, double kappa, const KState* ks, const double2* alpha, const double2* beta,
                          const double2* gamma, const double2* c, int step, const Geom& g, cudaStream_t st);
 int dslash_grid(const Geom& g, int threads);
+// thread blocks launch_dslash_pair launches on g (= the partial-sum slots its reduction writes)
+int dslash_pair_blocks(const Geom& g);
 // nvec FP64 device-layout vectors to the FP32 device layout (component pairs in float4)
 void launch_native_f64_to_f32(const double2* x, void* y, const Geom& g, int nvec, cudaStream_t st);
 // stencil thread layout: -1 automatic (by volume), 0 one thread per site, 1 direction split

@@ -323,25 +323,28 @@ __global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
     }
 }
 
+int dslash_pair_blocks(const Geom& g) { return pick_ds(g) ? ds_grid(g) : dslash_grid(g, 128); }
+
 void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, void* t, void* s, double mu,
                         double kappa, KState* ks, double2* alpha, int step, int klast, double* partials,
                         unsigned int* counter, const Geom& g, cudaStream_t st) {
+    const int B = dslash_pair_blocks(g);  // the partial-sum slots the fused reduction writes
     if (pick_ds(g)) {
         static unsigned long long attr_dev = 0;
         if (first_use_on_device(attr_dev))
             cudaFuncSetAttribute(k_dslash_pair_ds<LINK_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ds_smem(16, 2));
         if (prec == 0)
-            k_dslash_pair_ds<LINK_F64><<<ds_grid(g), 128, ds_smem(16, 2), st>>>(
+            k_dslash_pair_ds<LINK_F64><<<B, 128, ds_smem(16, 2), st>>>(
                 U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s, make_coef<double>(mu, kappa),
                 make_coef<double>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
         else
-            k_dslash_pair_ds<LINK_F32_12><<<ds_grid(g), 128, ds_smem(8, 2), st>>>(
+            k_dslash_pair_ds<LINK_F32_12><<<B, 128, ds_smem(8, 2), st>>>(
                 U, (const float4*)v, (const float4*)w, (float4*)t, (float4*)s, make_coef<float>(mu, kappa),
                 make_coef<float>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
         return;
     }
-    const int T = 128, B = dslash_grid(g, T);
+    const int T = 128;
     if (prec == 0)
         k_dslash_pair<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s,
                                                  make_coef<double>(mu, kappa), make_coef<double>(-mu, kappa), ks,

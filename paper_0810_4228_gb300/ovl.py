@@ -32,7 +32,8 @@ _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EB
              ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
 
 EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl_vector_bytes",
-           "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc", "ovl_pack", "ovl_unpack",
+           "ovl_set_gauge", "ovl_apply_Dw", "ovl_apply_pair", "ovl_apply_pair_noalloc",
+           "ovl_apply_pair_noalloc_blocks", "ovl_pack", "ovl_unpack",
            "ovl_set_deflation", "ovl_get_deflation", "ovl_deflation_eigs", "ovl_sign_krylov",
            "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad", "ovl_batch_create",
            "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_batch_profile", "ovl_batch_tuning",
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
         "ovl_apply_Dw": (I, [P, D, D, P, P, I]),
         "ovl_apply_pair": (I, [P, D, D, I, P, P, P, P, ctypes.POINTER(D)]),
         "ovl_apply_pair_noalloc": (I, [P, D, D, I, P, P, P, P, P]),
+        "ovl_apply_pair_noalloc_blocks": (I, [ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ovl_pack": (I, [P, P, P, I]),
         "ovl_unpack": (I, [P, P, P, I]),
         "ovl_set_deflation": (I, [P, D, D, I, ctypes.POINTER(D), P, P, I]),
@@ -116,6 +118,16 @@ def load(path: str = LIB_PATH):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def noalloc_pair_blocks(dims):
+    """(fits, blocks, max_blocks): the thread blocks ovl_apply_pair_noalloc's kernel launches on
+    a lattice of extents dims and the most its static scratch holds (host only, no GPU call)."""
+    lib = load()
+    arr = (ctypes.c_int * 4)(*[int(d) for d in dims])
+    nb, mx = ctypes.c_int(), ctypes.c_int()
+    r = lib.ovl_apply_pair_noalloc_blocks(arr, ctypes.byref(nb), ctypes.byref(mx))
+    return r == OK, nb.value, mx.value
 
 
 def _ptr(t) -> int:

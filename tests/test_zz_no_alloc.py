@@ -45,12 +45,27 @@ def test_noalloc_pair_matches_pair(ovl, dims, prec, tol):
         assert abs(a1 - a0) <= tol * abs(a0)
 
 
-def test_noalloc_rejects_oversized_lattice(ovl):
+# (48, 48, 48, 64) = 7077888 and (64, 64, 32, 40) = 5242880 sites lie between the true limit
+# (4194304: 32768 blocks of 64 sites per parity) and twice it; (64, 64, 64, 80) far above
+@pytest.mark.parametrize("dims", [(48, 48, 48, 64), (64, 64, 32, 40), (32, 32, 32, 130), (64, 64, 64, 80)])
+def test_noalloc_rejects_oversized_lattice(ovl, dims):
+    """Rejected with OVL_EINVAL before any launch (creating the context allocates nothing, and the
+    undersized buffers are never touched)."""
     import torch
-    ctx = ovl.Context((64, 64, 64, 80))  # 20971520 sites: creating the context allocates nothing
+    ctx = ovl.Context(dims)
     x = torch.zeros(2, dtype=torch.complex128, device="cuda")
     a = torch.zeros(2, dtype=torch.float64, device="cuda")
     with pytest.raises(ovl.OvlError) as e:
         ctx.apply_pair_noalloc(0.3, KAPPA, x, x, x, x, a, 1)
     assert e.value.code == ovl.EINVAL
     assert "too large" in str(e.value)
+
+
+def test_noalloc_accepts_the_largest_lattice_without_launching(ovl):
+    """At exactly the limit (32^3 x 128 = 4194304 sites) the size check passes: with null
+    buffers the call then stops at the null-argument check, before any launch."""
+    ctx = ovl.Context((32, 32, 32, 128))
+    with pytest.raises(ovl.OvlError) as e:
+        ctx._check(ctx._lib.ovl_apply_pair_noalloc(ctx._h, 0.3, KAPPA, 1, None, None, None, None, None))
+    assert e.value.code == ovl.EINVAL
+    assert "null argument" in str(e.value)
