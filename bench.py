@@ -5,24 +5,30 @@ Metric: sgn(gamma5 D_w(mu)) b solves/s at 1e-8 relative error, the mixed
 precision batched form (the headline) next to the FP64 form, the single-source
 forms and Arnoldi, plus the Wilson stencil's bandwidth against the HBM roof.
 
-Workload (one step = one batch): 12 Gaussian sources b on one 8^4 lattice
-(N = 49152), SU(3) links U = exp(i eps H) with eps = 1.0, m_w = -1.5
-(kappa = 0.2), mu = 0.3, antiperiodic time, the 20 eigenvalues of A nearest
-the imaginary axis deflated (left/right eigenvectors from the library's GPU
-eigensolver, set-up untimed); every source gives D_ov(mu) b = b + gamma5 sgn(A) b.
-The Krylov size k is the smallest on a grid for which every source of the batch
-agrees with a self-converged FP64 solve (k = 1000) to 1e-8.  Inputs are
+Workload (one step = one batch): the 12 spin-colour point sources at site 0 on
+each of four lattices of uneven sizes, 6^4, 8^4, 12^4 and 16^3 x 8 (48
+sequences, 58896 sites), SU(3) links U = exp(i eps H) with eps = 1.0 (seeds
+1003-1006), m_w = -1.5 (kappa = 0.2), mu = 0.2, antiperiodic time, the 20
+eigenvalues of A nearest the imaginary axis deflated on each lattice (left/right
+eigenvectors from the library's GPU eigensolver, set-up untimed); every source
+gives D_ov(mu) b = b + gamma5 sgn(A) b.  The Krylov size k is the smallest on a
+grid for which every source agrees to 1e-8 with a self-converged FP64 solve
+(k = 1500) and the sources the FP64 oracle reaches (6^4 and 8^4; stored by
+tests/golden/make_oracle_refs.py) agree with the oracle to 1e-8.  Inputs are
 resident in HBM when the timed region starts; L2 is flushed (a 512 MiB write)
 before every timed step and each step is timed on the device with CUDA events.
-A second batch, 12 point sources on each of 6^4, 8^4, 12^4 and 16^3 x 8
-(mu = 0.2), is timed once as context.
+Extras (context, not the headline): the same batch in FP64, 16^3 x 8 with 30
+deflated eigenpairs in single-source mixed precision, a batch of 12 Gaussian
+sources on 8^4 (mu = 0.3), single-source and Arnoldi solves on 8^4, the
+gradients and the stencil bandwidth on 48^3 x 64.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs under torchrun: each rank solves its own batch on its own GPU
 (replicas; the path has no data exchange), the max over ranks of the timed
 device time sets the aggregate rate.  --impl reference times the FP64 CPU
-oracle (scipy sparse matvec) on the same workload on the host cores.
+oracle (scipy sparse matvec + numpy) on a bounded sample of the same workload,
+one process per host core.
 """
 from __future__ import annotations
 
@@ -40,6 +46,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "sgn(γ5Dw(μ))b solves/s at 1e-8 rel err, mixed vs FP64; Dw GB/s vs HBM peak"
+# headline: 12 point sources on each of four lattices of uneven sizes, one batch per step
+HEAD_DIMS = [(6, 6, 6, 6), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 8)]
+HEAD_SEEDS = [1003, 1004, 1005, 1006]
+HEAD_MU, HEAD_M = 0.2, 20
+HEAD_K_GRID = list(range(400, 1001, 50))
+HEAD_K_REF = 1500
+# Krylov size of the reference arm (the driver runs it before this arm, so it cannot read this
+# arm's calibration): the k the calibration below chose on GB300 for the headline batch
+REF_K_DEFAULT = 550
+HEAD_WORKLOAD = ("12 spin-colour point sources x 4 lattices {6^4, 8^4, 12^4, 16^3x8} (48 sequences, "
+                 "58896 sites), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.2, batched two-sided Lanczos, "
+                 "20 eigenvalues of smallest |Re lambda| deflated per lattice")
+ORACLE_REFS = os.path.join(ROOT, "tests", "golden", "oracle_refs.npz")
+# the 8^4 Gaussian-source batch (an extra)
 DIMS = (8, 8, 8, 8)
 EPS, SEED_U, SEED_B = 1.0, 1001, 2001
 MU, KAPPA = 0.3, 0.2
@@ -47,12 +67,13 @@ K_GRID = list(range(300, 1001, 50))
 K_REF = 1000
 DW_DIMS = (48, 48, 48, 64)  # 7.1M sites: every stencil operand is far larger than L2
 NRHS = 12
-WORKLOAD = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3, batches of 12 Gaussian b, "
-            "two-sided Lanczos, 20 eigenvalues of smallest |Re lambda| deflated")
-MULTI_DIMS = [(6, 6, 6, 6), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 8)]
-MULTI_MU, MULTI_K, MULTI_M = 0.2, 700, 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_b_regen launch (12 x 8^4 sequences), steady-state mean
-REGEN_DRAM_BYTES_PER_LAUNCH = 30998400
+WORKLOAD8 = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3, batches of 12 Gaussian b, "
+             "two-sided Lanczos, 20 eigenvalues of smallest |Re lambda| deflated")
+# config of 16^3 x 8 with 30 deflated eigenpairs (an extra): single-source mixed precision
+C3_DIMS, C3_SEED_U, C3_SEED_B, C3_MU, C3_M = (16, 16, 16, 8), 1002, 2002, 0.3, 30
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the headline batch's dominant kernel
+# class, from one ncu capture of the current kernels (the roofline's "traffic"); None until measured
+HEAD_TRAFFIC = {}
 
 
 def peaks():
@@ -184,13 +205,6 @@ def dist_setup():
     return world, rank, local
 
 
-def make_inputs(torch, n_src, rank):
-    from paper_0810_4228_gb300 import synth
-    U = synth.gauge_field(DIMS, EPS, SEED_U)
-    srcs = synth.gaussian_source(DIMS, SEED_B + 7919 * rank, nrhs=n_src)
-    return U, srcs
-
-
 def calibrate_k(ovl, ctx, torch, b, flags_list, grid=None):
     """Smallest k on K_GRID whose solve agrees with the FP64 k=1000 solve to 1e-8; entries of
     flags_list are (name, flags) for two-sided Lanczos or (name, flags, method)."""
@@ -265,59 +279,101 @@ def dw_bandwidth(torch, ovl, reps=20, dims=DW_DIMS):
     return dims, V, res
 
 
-def cpu_baseline(k: int, budget_s: float = 30.0):
-    """The FP64 oracle's two-sided Lanczos on the same workload, single-threaded, in a child process."""
-    code = f"""
-import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
-import numpy as np
-from oracle import wilson as W, krylov as K
-from paper_0810_4228_gb300 import synth
-U = synth.gauge_field({DIMS!r}, {EPS}, {SEED_U})
-b = synth.gaussian_source({DIMS!r}, {SEED_B})
-A = W.a_operator(U, {DIMS!r}, {MU}, {KAPPA})
-Ad = A.conj().T.tocsr()
-t0 = time.perf_counter()
-K.lanczos2(A.dot, Ad.dot, b / np.linalg.norm(b), b / np.linalg.norm(b), 20)
-t20 = time.perf_counter() - t0
-k = {k}
-frac = min(1.0, {budget_s} / max(t20 * k / 20.0, 1e-9))
-ks = max(20, int(k * frac))
-t0 = time.perf_counter()
-y = K.sign_lanczos2(A.dot, Ad.dot, b, ks)
-t = time.perf_counter() - t0
-print(json.dumps({{"t": t, "ks": ks, "k": k}}))
-"""
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    per_solve = d["t"] * d["k"] / d["ks"]  # basis cost is linear in k; inner sign is small at this k
-    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one FP64 oracle two-sided Lanczos solve with {d['ks']} of k={d['k']} steps "
-                       f"(scipy CSR matvec + numpy, 1 thread) on the same 8^4 field and source, "
-                       f"{d['t']:.1f} s, scaled by k/{d['ks']}")}
+def _oracle_worker(task):
+    """One host process of the oracle sample: the oracle's two-sided Lanczos recurrence from one
+    point source of one headline lattice for a bounded number of steps (single-threaded)."""
+    j, r, budget_s, k = task
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import krylov as K
+    from oracle import wilson as W
+    from paper_0810_4228_gb300 import synth
+    dims = HEAD_DIMS[j]
+    U = synth.gauge_field(dims, EPS, HEAD_SEEDS[j])
+    A = W.a_operator(U, dims, HEAD_MU, KAPPA)
+    Ah = A.conj().T.tocsr()
+    b = synth.point_sources(dims, site=0)[r]
+    t0 = time.perf_counter()
+    K.lanczos2(A.dot, Ah.dot, b, b, 4)
+    t4 = (time.perf_counter() - t0) / 4
+    s = int(max(8, min(k, budget_s / max(t4, 1e-9))))
+    t0 = time.perf_counter()
+    _, _, a_, be, ga = K.lanczos2(A.dot, Ah.dot, b, b, s)
+    t_step = (time.perf_counter() - t0) / s
+    # the inner sign at the full size: the oracle's dense sgn(G_k) e_1 of a k x k tridiagonal
+    # (its cost does not depend on the values; the sample's coefficients, repeated)
+    t_in = None
+    if r == 0:
+        def rep(x, n):
+            return np.tile(x, -(-n // len(x)))[:n]
+        t0 = time.perf_counter()
+        K.inner_sign_e1(K.tridiag(rep(a_, k), rep(be, k - 1), rep(ga, k - 1)))
+        t_in = time.perf_counter() - t0
+    return {"j": j, "steps": s, "t_step": t_step, "t_inner": t_in}
+
+
+def oracle_batch_sample(k: int, budget_s: float = 20.0, procs: int = 0):
+    """The FP64 oracle on a bounded sample of the headline batch, on all host cores: one process
+    per core (spawned), each running the oracle's two-sided Lanczos recurrence from a point source
+    of one of the four lattices for about budget_s seconds; the per-step times measured under full
+    load, with the oracle's dense inner sign at size k, give the time of the whole batch
+    (12 sources x 4 lattices x (k steps + inner sign)) spread over the processes.  The deflation
+    set-up is excluded (as on the GPU and in the paper); the deflation split of each source
+    (a few dozen vector operations against k steps of two matvecs) is not timed."""
+    import multiprocessing as mp
+    P = max(procs or os.cpu_count() or 1, len(HEAD_DIMS))  # at least one process per lattice
+    tasks = [(w % len(HEAD_DIMS), 0 if w < len(HEAD_DIMS) else (w // len(HEAD_DIMS)) % 12, budget_s, k)
+             for w in range(P)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(P) as pool:
+        res = pool.map(_oracle_worker, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    per_lat = {}
+    for d in res:
+        per_lat.setdefault(d["j"], []).append(d["t_step"])
+    t_step = {j: statistics.median(v) for j, v in per_lat.items()}
+    t_in = {d["j"]: d["t_inner"] for d in res if d["t_inner"] is not None}
+    cpu_s = sum(NRHS * (k * t_step[j] + t_in[j]) for j in range(len(HEAD_DIMS)))
+    batch_wall = cpu_s / P
+    nseq = NRHS * len(HEAD_DIMS)
+    return {"value": nseq / batch_wall, "unit": "solves/s", "cores": P, "kind": "oracle",
+            "batch_seconds": batch_wall, "k": k, "sample_wall_s": round(wall, 1),
+            "sample": (f"{P} concurrent single-threaded processes (one per host core) each ran "
+                       f"{min(d['steps'] for d in res)}-{max(d['steps'] for d in res)} steps of the FP64 oracle's "
+                       f"two-sided Lanczos (scipy CSR matvec + numpy) from a point source of one of the four "
+                       f"lattices; per-step s under full load "
+                       + ", ".join(f"{'x'.join(map(str, HEAD_DIMS[j]))}: {t_step[j]*1e3:.1f} ms" for j in sorted(t_step))
+                       + f"; dense inner sign at k={k}: "
+                       + ", ".join(f"{t_in[j]:.2f} s" for j in sorted(t_in))
+                       + f"; batch = 12 sources x 4 lattices x (k steps + inner sign) / {P} processes")}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    k = args.k or 600
-    t_all = []
-    # each step is a bounded sample: a two-sided Lanczos run of the oracle
-    budget = max(2.0, 200.0 / max(args.steps + args.warmup, 1))
-    for i in range(args.warmup + args.steps):
-        d = cpu_baseline(k, budget_s=budget)
+    k = args.k or REF_K_DEFAULT
+    nrun = args.warmup + args.steps
+    budget = max(4.0, min(20.0, 150.0 / max(nrun, 1)))
+    t_all, last = [], None
+    for i in range(nrun):
+        last = oracle_batch_sample(k, budget_s=budget)
         if i >= args.warmup:
-            t_all.append(1.0 / d["value"])
+            t_all.append(last["batch_seconds"])
     per = sum(t_all) / len(t_all)
-    val = 1.0 / per
+    nseq = NRHS * len(HEAD_DIMS)
+    val = nseq / per
     line = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(DIMS), "mu": MU, "kappa": KAPPA, "eps": EPS, "k": k},
+            "config": {"workload": HEAD_WORKLOAD, "dims": [list(d) for d in HEAD_DIMS], "mu": HEAD_MU,
+                       "kappa": KAPPA, "eps": EPS, "k": k, "rhs_per_lattice": NRHS, "m_deflated": HEAD_M},
             "impl": "reference",
-            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": d["sample"]},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -420,156 +476,144 @@ def autograd_timing(torch, ovl, U_np, b, flush, k=800, gdims=(24, 24, 24, 24)):
     return out
 
 
-def multi_lattice_batch(torch, ovl, flush):
-    """12 point sources on each of four lattices of different sizes, 20 deflated eigenpairs each,
-    mixed vs FP64, timed once."""
+def load_oracle_refs():
+    """{case: {key: array}} from tests/golden/oracle_refs.npz (values written by the oracle), or {}."""
+    if not os.path.exists(ORACLE_REFS):
+        return {}
+    import numpy as np
+    z = np.load(ORACLE_REFS)
+    out = {}
+    for key in z.files:
+        case, field = key.split("/", 1)
+        out.setdefault(case, {})[field] = z[key]
+    return out
+
+
+_PROJ_CACHE = {}
+
+
+def oracle_error(y, ref):
+    """Distance of a full sgn(A) b vector y (torch or numpy) to the oracle's stored one: relative
+    2-norm over the sampled components, their largest difference relative to their largest
+    magnitude, and the relative error estimated from the eight stored projections
+    g_j^dag sgn(A) b (E|g^dag e|^2 = 2 |e|^2: g has N(0, 1) real and imaginary parts)."""
+    import numpy as np
+    from paper_0810_4228_gb300 import synth
+    yy = y.detach().cpu().numpy() if hasattr(y, "detach") else np.asarray(y)
+    dims = tuple(int(d) for d in ref["dims"])
+    if dims not in _PROJ_CACHE:
+        _PROJ_CACHE[dims] = np.stack([synth.gaussian_source(dims, 9000 + j) for j in range(len(ref["proj"]))])
+    G = _PROJ_CACHE[dims]
+    d = yy[ref["idx"]] - ref["val"]
+    pe = G.conj() @ yy - ref["proj"]
+    return {"sampled_rel": float(np.linalg.norm(d) / np.linalg.norm(ref["val"])),
+            "sampled_maxabs_rel": float(np.abs(d).max() / np.abs(ref["val"]).max()),
+            "proj_rel": float(np.sqrt(np.mean(np.abs(pe) ** 2) / 2.0) / float(ref["norm"]))}
+
+
+def headline_setup(torch, ovl):
+    """Contexts of the four lattices (fields drawn on the host: the oracle sees the same links),
+    their deflation eigenpairs (library eigensolver, untimed) and the 12 point sources each."""
     from paper_0810_4228_gb300 import synth
     ctxs, srcs, setup = [], [], []
-    for j, d in enumerate(MULTI_DIMS):
+    for d, seed in zip(HEAD_DIMS, HEAD_SEEDS):
         c = ovl.Context(d)
-        U = synth.gauge_field_torch(d, EPS, 1003 + j, device="cuda")
-        c.set_gauge(U)
-        del U
+        c.set_gauge(torch.from_numpy(synth.gauge_field(d, EPS, seed)).cuda())
         t0 = time.perf_counter()
-        e = c.deflation_eigs(MULTI_MU, KAPPA, MULTI_M)
-        setup.append({"m": e["m"], "seconds": round(time.perf_counter() - t0, 2), "max_residual": e["max_residual"]})
+        e = c.deflation_eigs(HEAD_MU, KAPPA, HEAD_M)
+        setup.append({"dims": list(d), "m": e["m"], "seconds": round(time.perf_counter() - t0, 2),
+                      "max_residual": e["max_residual"]})
         ctxs.append(c)
         srcs.append(torch.from_numpy(synth.point_sources(d, site=0)).cuda())
-    bt = ovl.Batch(ctxs, [NRHS] * len(ctxs))
-    res = {"lattices": [list(d) for d in MULTI_DIMS], "rhs_per_lattice": NRHS, "mu": MULTI_MU, "k": MULTI_K,
-           "deflation": f"{MULTI_M} eigenpairs per lattice (library eigensolver, untimed)", "deflation_setup": setup,
-           "sources": "12 spin-colour point sources at site 0"}
-    for name, fl in (("mixed", ovl.MIXED), ("fp64", 0)):
-        bt.solve(MULTI_K, MULTI_MU, KAPPA, srcs, flags=fl)
-        t = time_solves(torch, None, lambda _: bt.solve(MULTI_K, MULTI_MU, KAPPA, srcs, flags=fl), [0], 1, 3, flush)
-        ms = statistics.mean(t)
-        res[name] = {"ms_per_batch": round(ms, 3), "solves_per_s": round(bt.nseq * 1e3 / ms, 2)}
-    # accuracy of the mixed batch against single FP64 k = 1000 solves, one source per lattice
-    outs, _, _ = bt.solve(MULTI_K, MULTI_MU, KAPPA, srcs, flags=ovl.MIXED)
-    errs = []
-    for j, c in enumerate(ctxs):
-        ref, _ = c.sign_krylov(ovl.LANCZOS2, K_REF, MULTI_MU, KAPPA, srcs[j][5])
-        errs.append(torch.linalg.vector_norm(outs[j][5] - ref).item() / torch.linalg.vector_norm(ref).item())
-    res["mixed"]["max_rel_err_vs_k1000_fp64_sampled"] = max(errs)
-    bt.close()
-    for c in ctxs:
-        c.close()
-    torch.cuda.empty_cache()
-    return res
+    return ctxs, srcs, setup
 
 
-def run_ours(args, world, rank, local):
-    import torch
-    from paper_0810_4228_gb300 import ovl, synth
+def headline_errors(torch, outs, refs64, orefs):
+    """Largest relative error of the batch's sgn(A) b over all sources against the FP64 k = 1500
+    solves, and over the oracle's sources (6^4, 8^4) against the oracle."""
+    e64 = max(torch.linalg.vector_norm(outs[j][r] - refs64[j][r]).item() / torch.linalg.vector_norm(refs64[j][r]).item()
+              for j in range(len(HEAD_DIMS)) for r in range(NRHS))
+    eo = None
+    for name, ref in orefs.items():
+        j = [tuple(d) for d in HEAD_DIMS].index(tuple(int(x) for x in ref["dims"]))
+        r = int(ref["source_arg"])
+        e = oracle_error(outs[j][r], ref)
+        v = max(e["sampled_rel"], e["proj_rel"])
+        eo = v if eo is None else max(eo, v)
+    return e64, eo
 
-    torch.cuda.set_device(local)
-    if args.dw_only:
-        ovl.load()
-        dims = tuple(int(v) for v in args.dw_dims.split(",")) if args.dw_dims else DW_DIMS
-        ddims, dV, dres = dw_bandwidth(torch, ovl, reps=args.steps, dims=dims)
-        print(json.dumps({"dw_only": True, "dims": list(ddims), "sites": dV,
-                          **{nm: {"ms": r["ms"], "GB_s": r["GB_s"]} for nm, r in dres.items()}}))
-        return
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    ovl.load()
-    hbm_peak, peak_kind = peaks()
+
+def calibrate_headline(torch, ovl, bt, ctxs, srcs, orefs, flags, grid):
+    """Smallest k on the grid for which every source of the batch is within 1e-8 of its FP64
+    k = 1500 solve and the oracle's sources are within 1e-8 of the oracle."""
+    refs64 = [torch.stack([c.sign_krylov(ovl.LANCZOS2, HEAD_K_REF, HEAD_MU, KAPPA, srcs[j][r])[0].clone()
+                           for r in range(NRHS)]) for j, c in enumerate(ctxs)]
+    # the self-converged FP64 reference itself against the oracle
+    ref_vs_oracle = None
+    for name, ref in orefs.items():
+        j = [tuple(d) for d in HEAD_DIMS].index(tuple(int(x) for x in ref["dims"]))
+        e = oracle_error(refs64[j][int(ref["source_arg"])], ref)
+        v = max(e["sampled_rel"], e["proj_rel"])
+        ref_vs_oracle = v if ref_vs_oracle is None else max(ref_vs_oracle, v)
+    chosen, e64, eo = grid[-1], None, None
+    for k in grid:
+        outs, _, _ = bt.solve(k, HEAD_MU, KAPPA, srcs, flags=flags)
+        e64, eo = headline_errors(torch, outs, refs64, orefs)
+        print(f"[bench] calibrate headline flags={flags} k={k} err_fp64={e64:.3e} err_oracle={eo}",
+              file=sys.stderr, flush=True)
+        if e64 <= 1e-8 and (eo is None or eo <= 1e-8):
+            chosen = k
+            break
+    return chosen, e64, eo, ref_vs_oracle, refs64
+
+
+def headline_launches(k, m=HEAD_M):
+    """Kernels one headline batch launches (batch_launches with the pass-1 form the batch takes:
+    the 48 sequences' 128-site blocks exceed what one resident grid holds, so pass 1 runs stepwise)."""
+    blocks = sum(NRHS * -(-(d[0] * d[1] * d[2] * d[3]) // 128) for d in HEAD_DIMS)
+    return batch_launches(NRHS * len(HEAD_DIMS), k, m, persistent_pass1=blocks <= 3 * 152)
+
+
+def gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank):
+    """The 8^4 workload with Gaussian sources (mu = 0.3, 20 deflated): a batch of 12 sources, single
+    sources (two-sided Lanczos mixed / FP64, Arnoldi FP64 / double-float), each at its calibrated k
+    (1e-8 against the FP64 k = 1000 solve), the FP64 reference and the solves against the oracle's
+    stored sgn(A) b of the source with seed 2001."""
+    from paper_0810_4228_gb300 import synth
     U = synth.gauge_field(DIMS, EPS, SEED_U)
-    srcs_np = synth.gaussian_source(DIMS, SEED_B + 7919 * rank, nrhs=NRHS)
+    srcs = torch.from_numpy(synth.gaussian_source(DIMS, SEED_B + 7919 * rank, nrhs=NRHS)).cuda()
+    b1 = torch.from_numpy(synth.gaussian_source(DIMS, SEED_B)).cuda()  # the oracle's source
     ctx = ovl.Context(DIMS)
     ctx.set_gauge(torch.from_numpy(U).cuda())
-    srcs = torch.from_numpy(srcs_np).cuda()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
-
-    # ---- deflation set-up: the M_DEFL eigenpairs of A nearest the imaginary axis (untimed, once per field)
-    eig = None
-    if args.m > 0:
-        t0 = time.perf_counter()
-        eig = ctx.deflation_eigs(MU, KAPPA, args.m)
+    t0 = time.perf_counter()
+    eig = ctx.deflation_eigs(MU, KAPPA, args.m) if args.m > 0 else None
+    if eig:
         eig["seconds"] = round(time.perf_counter() - t0, 2)
-        print(f"[bench] deflation {eig}", file=sys.stderr, flush=True)
-
     bt = ovl.Batch([ctx], [NRHS])
-    fl_mix = ovl.MIXED | ovl.OVERLAP
-    fl_64 = ovl.OVERLAP
-    # ---- accuracy calibration (untimed): every source against the FP64 k = 1000 solve
-    if args.k:
-        k_mix = k_64 = k_s = k_s64 = k_arn = k_adf = args.k
-        err_mix = err_64 = err_s = err_s64 = err_arn = err_adf = None
-    else:
-        refs = torch.stack([ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, srcs[r])[0].clone() for r in range(NRHS)])
-        k_mix, err_mix = calibrate_batch(torch, bt, srcs, refs, ovl.MIXED, K_GRID)
-        k_64, err_64 = calibrate_batch(torch, bt, srcs, refs, 0, K_GRID)
-        cal = calibrate_k(ovl, ctx, torch, srcs[0], [("mixed", ovl.MIXED), ("fp64", 0)])
-        (k_s, err_s), (k_s64, err_s64) = cal["mixed"], cal["fp64"]
-        # Arnoldi on its own k grid (step 25: it needs a smaller subspace, Sec. 5)
-        cal_a = calibrate_k(ovl, ctx, torch, srcs[0], [("arnoldi", 0, ovl.ARNOLDI),
-                                                       ("arnoldi_df", ovl.MIXED, ovl.ARNOLDI)],
-                            grid=list(range(250, 801, 25)))
-        (k_arn, err_arn), (k_adf, err_adf) = cal_a["arnoldi"], cal_a["arnoldi_df"]
-    print(f"[bench] batch k mixed={k_mix} ({err_mix}), fp64={k_64} ({err_64}); single k mixed={k_s}, fp64={k_s64}",
-          file=sys.stderr, flush=True)
-
-    if args.solves_only:
-        if not args.k:
-            raise SystemExit("--solves-only needs --k")
-        one_method = ovl.ARNOLDI if args.arnoldi else ovl.LANCZOS2
-        one_flags = (ovl.OVERLAP | ovl.MIXED) if args.arnoldi else fl_mix
-        if args.single or args.arnoldi:
-            out1 = torch.empty_like(srcs[0])
-            t = time_solves(torch, ctx, lambda b: ctx.sign_krylov(one_method, k_s, MU, KAPPA, b, out1, flags=one_flags),
-                            [srcs[r] for r in range(NRHS)], args.warmup, args.steps, flush)
-        else:
-            t = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix),
-                            [0], args.warmup, args.steps, flush)
-        if args.profile_one:
-            # one more solve between cudaProfilerStart/Stop: `ncu --profile-from-start off` captures
-            # exactly the launches of one solve (no effect without a profiler)
-            torch.cuda.synchronize()
-            torch.cuda.cudart().cudaProfilerStart()
-            if args.single or args.arnoldi:
-                ctx.sign_krylov(one_method, k_s, MU, KAPPA, srcs[0], out1, flags=one_flags)
-            else:
-                bt.solve(k_mix, MU, KAPPA, [srcs], [srcs.clone()], flags=fl_mix)
-            torch.cuda.synchronize()
-            torch.cuda.cudart().cudaProfilerStop()
-        print(json.dumps({"solves_only": True, "single": args.single, "arnoldi_doublefloat": args.arnoldi, "k": k_mix,
-                          "ms_per_step": statistics.mean(t)}))
-        return
-
-    outb = torch.empty_like(srcs)
-    # ---- per-phase profile of the batched solve (CUDA events around each phase, eager launches)
-    nprof = 3
-    bt.profile(reset=True)
-    for _ in range(nprof):
-        _, pinfo, _ = bt.solve(k_mix, MU, KAPPA, [srcs], [outb], flags=fl_mix | ovl.PROFILE)
-    prof, _ = bt.profile(reset=True)
-    prof = {kk: v / nprof for kk, v in prof.items()}
-    tuned = bt.tuning()
-    kused = max(i["k_used"] for i in pinfo)
-    print(f"[bench] batch profile {prof}", file=sys.stderr, flush=True)
-
-    # ---- timed region: the mixed batched solve (headline), device-resident inputs
-    clocks = Clocks(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    t_mix = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [outb], flags=fl_mix), [0],
-                        args.warmup, args.steps, flush)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    tot = max_over_ranks(sum(t_mix), world, "cuda")
-    if world > 1:
-        torch.distributed.barrier()
-    value = whole_job_rate(tot, world, NRHS, args.steps)
-    print(f"[bench] batched mixed solves/s {value:.2f}, ms/step {statistics.mean(t_mix):.3f}, steps "
-          f"{[round(t, 3) for t in t_mix]}", file=sys.stderr, flush=True)
-
-    # ---- FP64 batched, single-source forms and Arnoldi (context, fewer steps)
+    fl_mix, fl_64 = ovl.MIXED | ovl.OVERLAP, ovl.OVERLAP
+    oref = orefs.get("gauss8_mu0.3")
+    refs = torch.stack([ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, srcs[r])[0].clone() for r in range(NRHS)])
+    k_mix, err_mix = calibrate_batch(torch, bt, srcs, refs, ovl.MIXED, K_GRID)
+    k_64, err_64 = calibrate_batch(torch, bt, srcs, refs, 0, K_GRID)
+    cal = calibrate_k(ovl, ctx, torch, b1, [("mixed", ovl.MIXED), ("fp64", 0)])
+    (k_s, err_s), (k_s64, err_s64) = cal["mixed"], cal["fp64"]
+    cal_a = calibrate_k(ovl, ctx, torch, b1, [("arnoldi", 0, ovl.ARNOLDI), ("arnoldi_df", ovl.MIXED, ovl.ARNOLDI)],
+                        grid=list(range(250, 801, 25)))
+    (k_arn, err_arn), (k_adf, err_adf) = cal_a["arnoldi"], cal_a["arnoldi_df"]
+    vs_oracle = None
+    if oref is not None:
+        vs_oracle = {}
+        for name, meth, k, fl in (("fp64_k1000_reference", ovl.LANCZOS2, K_REF, 0),
+                                  ("lanczos2_mixed", ovl.LANCZOS2, k_s, ovl.MIXED),
+                                  ("lanczos2_fp64", ovl.LANCZOS2, k_s64, 0),
+                                  ("arnoldi_fp64", ovl.ARNOLDI, k_arn, 0),
+                                  ("arnoldi_doublefloat", ovl.ARNOLDI, k_adf, ovl.MIXED)):
+            y = ctx.sign_krylov(meth, k, MU, KAPPA, b1, flags=fl)[0]
+            vs_oracle[name] = dict(k=k, **oracle_error(y, oref))
     nctx = max(3, min(args.steps, 5))
+    outb = torch.empty_like(srcs)
+    t_b = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [srcs], [outb], flags=fl_mix), [0], 2, nctx,
+                      flush)
     t_b64 = time_solves(torch, ctx, lambda _: bt.solve(k_64, MU, KAPPA, [srcs], [outb], flags=fl_64), [0], 2, nctx,
                         flush)
     out1 = torch.empty_like(srcs[0])
@@ -578,8 +622,6 @@ def run_ours(args, world, rank, local):
                       bsingle, 2, nctx, flush)
     t_s64 = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s64, MU, KAPPA, b, out1, flags=fl_64),
                         bsingle, 2, nctx, flush)
-    # the single-source mixed solve by kernel class (rows a1-a8; CUDA events around each class,
-    # eager launches), and the optional re-projection of the deflated directions in pass 1 (row a4)
     single_profile, reproj = None, None
     try:
         ctx.profile(reset=True)
@@ -591,12 +633,11 @@ def run_ours(args, world, rank, local):
     try:
         t_rp = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, b, out1,
                                                                  flags=fl_mix | ovl.REPROJ), bsingle, 2, nctx, flush)
-        reproj = {"k": k_s, "ms": round(statistics.mean(t_rp), 3),
-                  "ms_without": round(statistics.mean(t_s), 3), "m": args.m}
-        if not args.k:
-            yr = ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, srcs[0], flags=ovl.MIXED | ovl.REPROJ)[0]
-            reproj["rel_err_vs_k1000_fp64"] = (torch.linalg.vector_norm(yr - refs[0]) /
-                                               torch.linalg.vector_norm(refs[0])).item()
+        reproj = {"k": k_s, "ms": round(statistics.mean(t_rp), 3), "ms_without": round(statistics.mean(t_s), 3),
+                  "m": args.m}
+        yr = ctx.sign_krylov(ovl.LANCZOS2, k_s, MU, KAPPA, srcs[0], flags=ovl.MIXED | ovl.REPROJ)[0]
+        reproj["rel_err_vs_k1000_fp64"] = (torch.linalg.vector_norm(yr - refs[0]) /
+                                           torch.linalg.vector_norm(refs[0])).item()
     except Exception as exc:  # report, keep the rest of the line
         reproj = {"error": repr(exc)[:200]}
     t_arn = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_arn, MU, KAPPA, b, out1,
@@ -616,59 +657,233 @@ def run_ours(args, world, rank, local):
                   "frac_hbm": round(sweep_bytes / (sweep_ms * 1e6) / hbm_peak, 3) if sweep_ms else None,
                   "inner_sign_ms": round(aprof.get("inner_sign", {}).get("ms", 0.0), 3),
                   "stencil_ms": round(aprof.get("dslash", {}).get("ms", 0.0), 3)}
+    res = {
+        "workload": WORKLOAD8, "deflation_setup": eig,
+        "batch_mixed": {"solves_per_s": NRHS * 1e3 / statistics.mean(t_b), "ms_per_batch": statistics.mean(t_b),
+                        "k": k_mix, "max_rel_err_vs_k1000_fp64": err_mix,
+                        "method": "batched two-sided Lanczos, FP32 pass 1 (persistent), double-float pass 2"},
+        "batch_fp64": {"solves_per_s": NRHS * 1e3 / statistics.mean(t_b64), "ms_per_batch": statistics.mean(t_b64),
+                       "k": k_64, "max_rel_err_vs_k1000_fp64": err_64},
+        "single_mixed": {"solves_per_s": 1e3 / statistics.mean(t_s), "ms": statistics.mean(t_s), "k": k_s,
+                         "rel_err_vs_k1000_fp64": err_s, "kernels": "persistent passes (FP32 pass 1, FP64 pass 2)",
+                         "profile_ms_by_kernel_class": single_profile, "with_reprojection": reproj},
+        "single_fp64": {"solves_per_s": 1e3 / statistics.mean(t_s64), "ms": statistics.mean(t_s64), "k": k_s64,
+                        "rel_err_vs_k1000_fp64": err_s64},
+        "arnoldi_fp64": {"solves_per_s": 1e3 / statistics.mean(t_arn), "ms": statistics.mean(t_arn), "k": k_arn,
+                         "rel_err_vs_k1000_fp64": err_arn,
+                         "k_ratio_2sl_over_arnoldi": (k_s64 / k_arn) if k_arn else None},
+        "arnoldi_doublefloat": {"solves_per_s": 1e3 / statistics.mean(t_adf), "ms": statistics.mean(t_adf),
+                                "k": k_adf, "rel_err_vs_k1000_fp64": err_adf, "gram_schmidt_sweeps": adf_sweeps},
+        "vs_oracle_source_seed_2001": vs_oracle,
+    }
+    bt.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+    return res, U
+
+
+def config3_extra(torch, ovl, flush, steps):
+    """16^3 x 8, mu = 0.3, 30 deflated eigenpairs: single-source mixed precision at the smallest k
+    on a grid (step 50, at most 800) within 1e-8 of the FP64 k = 1200 solve, against FP64 at its own
+    calibrated k; the error of each stated against the FP64 reference."""
+    from paper_0810_4228_gb300 import synth
+    ctx = ovl.Context(C3_DIMS)
+    ctx.set_gauge(torch.from_numpy(synth.gauge_field(C3_DIMS, EPS, C3_SEED_U)).cuda())
+    t0 = time.perf_counter()
+    eig = ctx.deflation_eigs(C3_MU, KAPPA, C3_M)
+    eig["seconds"] = round(time.perf_counter() - t0, 2)
+    b = torch.from_numpy(synth.gaussian_source(C3_DIMS, C3_SEED_B)).cuda()
+    ref = ctx.sign_krylov(ovl.LANCZOS2, 1200, C3_MU, KAPPA, b)[0].clone()
+    nrm = torch.linalg.vector_norm(ref).item()
+    out = {"dims": list(C3_DIMS), "mu": C3_MU, "m": C3_M, "deflation_setup": eig,
+           "reference": "FP64 two-sided Lanczos, k = 1200"}
+    for name, fl in (("mixed", ovl.MIXED), ("fp64", 0)):
+        chosen, err = 800, None
+        for k in range(400, 801, 50):
+            y = ctx.sign_krylov(ovl.LANCZOS2, k, C3_MU, KAPPA, b, flags=fl)[0]
+            err = torch.linalg.vector_norm(y - ref).item() / nrm
+            if err <= 1e-8:
+                chosen = k
+                break
+        y1 = torch.empty_like(b)
+        t = time_solves(torch, ctx, lambda bb: ctx.sign_krylov(ovl.LANCZOS2, chosen, C3_MU, KAPPA, bb, y1,
+                                                               flags=fl | ovl.OVERLAP), [b], 2, max(3, steps), flush)
+        out[name] = {"k": chosen, "rel_err_vs_fp64_k1200": err, "ms": statistics.mean(t),
+                     "solves_per_s": 1e3 / statistics.mean(t)}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_0810_4228_gb300 import ovl, synth
+
+    torch.cuda.set_device(local)
+    if args.dw_only:
+        ovl.load()
+        dims = tuple(int(v) for v in args.dw_dims.split(",")) if args.dw_dims else DW_DIMS
+        ddims, dV, dres = dw_bandwidth(torch, ovl, reps=args.steps, dims=dims)
+        print(json.dumps({"dw_only": True, "dims": list(ddims), "sites": dV,
+                          **{nm: {"ms": r["ms"], "GB_s": r["GB_s"]} for nm, r in dres.items()}}))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ovl.load()
+    hbm_peak, peak_kind = peaks()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    orefs = load_oracle_refs()
+    orefs_head = {n: r for n, r in orefs.items() if n.startswith("batch")} if rank == 0 else {}
+
+    # ---- headline: deflation set-up (untimed), the batch of 48 sequences
+    ctxs, srcs, setup = headline_setup(torch, ovl)
+    if rank > 0:  # replicas: each rank its own point sources (site = rank)
+        srcs = [torch.from_numpy(synth.point_sources(d, site=rank % (d[0] * d[1] * d[2] * d[3]))).cuda()
+                for d in HEAD_DIMS]
+    print(f"[bench] headline deflation {setup}", file=sys.stderr, flush=True)
+    bt = ovl.Batch(ctxs, [NRHS] * len(ctxs))
+    nseq = NRHS * len(ctxs)
+    sites = [d[0] * d[1] * d[2] * d[3] for d in HEAD_DIMS]
+    seq_sites = NRHS * sum(sites)
+    fl_mix, fl_64 = ovl.MIXED | ovl.OVERLAP, ovl.OVERLAP
+
+    if args.solves_only:
+        if not args.k:
+            raise SystemExit("--solves-only needs --k")
+        outs = [s.clone() for s in srcs]
+        t = time_solves(torch, None, lambda _: bt.solve(args.k, HEAD_MU, KAPPA, srcs, outs, flags=fl_mix), [0],
+                        args.warmup, args.steps, flush)
+        if args.profile_one:
+            # one more solve between cudaProfilerStart/Stop: `ncu --profile-from-start off` captures
+            # exactly the launches of one solve (no effect without a profiler)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
+            bt.solve(args.k, HEAD_MU, KAPPA, srcs, outs, flags=fl_mix)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"solves_only": True, "k": args.k, "ms_per_step": statistics.mean(t),
+                          "solves_per_s": nseq * 1e3 / statistics.mean(t)}))
+        return
+
+    # ---- accuracy calibration (untimed)
+    refs64 = None
+    if args.k:
+        k_mix, err64_mix, erro_mix, ref_vs_oracle = args.k, None, None, None
+    else:
+        k_mix, err64_mix, erro_mix, ref_vs_oracle, refs64 = calibrate_headline(
+            torch, ovl, bt, ctxs, srcs, orefs_head, ovl.MIXED, HEAD_K_GRID)
+    print(f"[bench] headline k={k_mix} err_fp64={err64_mix} err_oracle={erro_mix}", file=sys.stderr, flush=True)
+
+    # ---- per-phase profile of the batched solve (CUDA events around each phase, eager launches)
+    outs = [torch.empty_like(s) for s in srcs]
+    nprof = 3
+    bt.profile(reset=True)
+    for _ in range(nprof):
+        _, pinfo, _ = bt.solve(k_mix, HEAD_MU, KAPPA, srcs, outs, flags=fl_mix | ovl.PROFILE)
+    prof, _ = bt.profile(reset=True)
+    prof = {kk: v / nprof for kk, v in prof.items()}
+    tuned = bt.tuning()
+    kused = max(i["k_used"] for i in pinfo)
+    print(f"[bench] batch profile {prof}", file=sys.stderr, flush=True)
+
+    # ---- timed region: the mixed batched solve (headline), device-resident inputs
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_mix = time_solves(torch, None, lambda _: bt.solve(k_mix, HEAD_MU, KAPPA, srcs, outs, flags=fl_mix), [0],
+                        args.warmup, args.steps, flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot = max_over_ranks(sum(t_mix), world, "cuda")
+    if world > 1:
+        torch.distributed.barrier()
+    value = whole_job_rate(tot, world, nseq, args.steps)
+    print(f"[bench] headline mixed solves/s {value:.2f}, ms/step {statistics.mean(t_mix):.3f}, steps "
+          f"{[round(t, 3) for t in t_mix]}", file=sys.stderr, flush=True)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
-    hsrc = srcs.cpu().pin_memory()
-    hout = torch.empty_like(hsrc).pin_memory()
-    t_e2e = time_solves(torch, ctx, lambda _: bt.solve(k_mix, MU, KAPPA, [hsrc], [hout], flags=fl_mix), [0],
+    hsrc = [s.cpu().pin_memory() for s in srcs]
+    hout = [torch.empty_like(h).pin_memory() for h in hsrc]
+    t_e2e = time_solves(torch, None, lambda _: bt.solve(k_mix, HEAD_MU, KAPPA, hsrc, hout, flags=fl_mix), [0],
                         args.warmup, args.steps, flush)
-    e2e_val = whole_job_rate(max_over_ranks(sum(t_e2e), world, "cuda"), world, NRHS, args.steps)
-    nbytes = srcs.numel() * srcs.element_size()
+    e2e_val = whole_job_rate(max_over_ranks(sum(t_e2e), world, "cuda"), world, nseq, args.steps)
+    nbytes = sum(s.numel() * s.element_size() for s in srcs)
 
-    # ---- roofline of the dominant phase of the batched solve
+    # ---- the same batch in FP64 at equal accuracy (smallest k on the grid from k_mix - 100 up)
+    fp64 = None
+    try:
+        if refs64 is not None:
+            k64, e64 = HEAD_K_GRID[-1], None
+            for k in [kk for kk in HEAD_K_GRID if kk >= k_mix - 100]:
+                o64, _, _ = bt.solve(k, HEAD_MU, KAPPA, srcs, flags=0)
+                e64, eo64 = headline_errors(torch, o64, refs64, orefs_head)
+                if e64 <= 1e-8 and (eo64 is None or eo64 <= 1e-8):
+                    k64 = k
+                    break
+            del o64
+        else:
+            k64, e64 = k_mix, None
+        t64 = time_solves(torch, None, lambda _: bt.solve(k64, HEAD_MU, KAPPA, srcs, outs, flags=fl_64), [0], 1,
+                          max(2, min(args.steps, 3)), flush)
+        fp64 = {"k": k64, "max_rel_err_vs_k1500_fp64": e64, "ms_per_batch": statistics.mean(t64),
+                "solves_per_s": nseq * 1e3 / statistics.mean(t64),
+                "method": "batched two-sided Lanczos in FP64, two passes (the stored basis would exceed 32 GiB)"}
+    except Exception as exc:  # report, keep the headline measurement
+        fp64 = {"error": repr(exc)[:200]}
+    del refs64
+    torch.cuda.empty_cache()
+
+    # ---- roofline of the dominant phase (algorithmic bytes of the method, Sec. 4-5)
     steps2 = max(kused - 1, 1)
     roof_all = {
-        "pass1_batched_fp32": {"bound": "hbm", "achieved": PASS1_BYTES_SITE * V * NRHS * kused / prof["pass1"] / 1e6,
+        "pass1_batched_fp32": {"bound": "hbm", "achieved": PASS1_BYTES_SITE * seq_sites * kused / prof["pass1"] / 1e6,
                                "peak": hbm_peak, "unit": "GB/s",
-                               "algorithmic": f"{PASS1_BYTES_SITE} B/site/step x {V} sites x {NRHS} rhs x {kused} steps",
-                               "ms_per_launch_sequence": prof["pass1"]},
-        "pass2_batched_doublefloat": {"bound": "alu",
-                               "achieved": REGEN_DF_OPS_SITE * V * NRHS * steps2 / prof["pass2_or_combine"] / 1e9,
-                               "peak": FP32_OPS_PEAK_T, "unit": "Top/s (FP32 operations)",
-                               "algorithmic": f"{REGEN_DF_OPS_SITE} FP32 operations/site/step of the double-float arithmetic "
-                                              f"x {V} sites x {NRHS} rhs x {steps2} steps",
-                               "fp64_equivalent": {"achieved_tflops": REGEN_FLOP_SITE * V * NRHS * steps2 / prof["pass2_or_combine"] / 1e9,
-                                                   "fp64_roof_tflops": FP64_PEAK_TFLOPS,
-                                                   "note": f"{REGEN_FLOP_SITE} FP64 flop/site/step: the same step in native FP64"},
-                               "ms_per_launch_sequence": prof["pass2_or_combine"]},
+                               "algorithmic": f"{PASS1_BYTES_SITE} B/site/step x {seq_sites} site-sequences x {kused} steps",
+                               "ms_per_launch_sequence": prof["pass1"],
+                               "kernels": "k_b_pair + k_b_lstep per step"},
+        "pass2_batched_doublefloat": {
+            "bound": "hbm", "achieved": PASS2_BYTES_SITE * seq_sites * steps2 / prof["pass2_or_combine"] / 1e6,
+            "peak": hbm_peak, "unit": "GB/s",
+            "algorithmic": f"{PASS2_BYTES_SITE} B/site/step x {seq_sites} site-sequences x {steps2} steps",
+            "ms_per_launch_sequence": prof["pass2_or_combine"], "kernels": "k_b_regen per step",
+            "alu_view": {
+                "fp32_ops_achieved_T": REGEN_DF_OPS_SITE * seq_sites * steps2 / prof["pass2_or_combine"] / 1e9,
+                "fp32_issue_peak_T": FP32_OPS_PEAK_T,
+                "note": f"{REGEN_DF_OPS_SITE} FP32 operations/site/step of the double-float arithmetic",
+                "fp64_equivalent_tflops": REGEN_FLOP_SITE * seq_sites * steps2 / prof["pass2_or_combine"] / 1e9,
+                "fp64_roof_tflops": FP64_PEAK_TFLOPS}},
     }
     for r_ in roof_all.values():
         r_["frac"] = r_["achieved"] / r_["peak"]
+        if "alu_view" in r_:
+            av = r_["alu_view"]
+            av["frac_fp32_issue"] = av["fp32_ops_achieved_T"] / av["fp32_issue_peak_T"]
     dname = "pass2_batched_doublefloat" if prof["pass2_or_combine"] >= prof["pass1"] else "pass1_batched_fp32"
     roof = dict(roof_all[dname])
-    # DRAM bytes per launch of the dominant kernel from one ncu capture of the same kernel
-    # (profiles/regen_dram_8x4_batch12.md); not measured for the pass-1 kernels
-    traffic = REGEN_DRAM_BYTES_PER_LAUNCH if dname == "pass2_batched_doublefloat" and NRHS == 12 else None
-    roof.update({"kernel": dname, "traffic": traffic,
-                 "peak_kind": ("derived FP32 issue rate 152 SM x 128 lanes x 2.07 GHz" if roof["bound"] == "alu"
-                               else f"{peak_kind} hbm_gbs")})
+    roof.update({"kernel": dname, "traffic": HEAD_TRAFFIC.get(dname),
+                 "peak_kind": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"})
 
-    multi = None
-    if rank == 0 and not args.no_multi:
-        try:
-            multi = multi_lattice_batch(torch, ovl, flush)
-        except Exception as exc:  # report, keep the headline measurement
-            multi = {"error": repr(exc)[:200]}
-
-    # ---- row a10: the gradients (sign function and stencil adjoint)
-    grads = None
-    if rank == 0 and not args.no_grad:
-        try:
-            grads = autograd_timing(torch, ovl, U, srcs[0], flush)
-        except Exception as exc:  # report, keep the headline measurement
-            grads = {"error": repr(exc)[:200]}
-
-    # ---- stencil bandwidth on a lattice far larger than L2
+    # ---- extras (rank 0)
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        for key, fn in (("config_16x3x8_m30", lambda: config3_extra(torch, ovl, flush, args.steps)),
+                        ("gauss8", lambda: gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank))):
+            try:
+                extras[key] = fn()
+            except Exception as exc:  # report, keep the headline measurement
+                extras[key] = {"error": repr(exc)[:200]}
+        U8 = None
+        if isinstance(extras.get("gauss8"), tuple):
+            extras["gauss8"], U8 = extras["gauss8"]
+        if not args.no_grad and U8 is not None:
+            try:
+                extras["autograd"] = autograd_timing(
+                    torch, ovl, U8, torch.from_numpy(synth.gaussian_source(DIMS, SEED_B)).cuda(), flush)
+            except Exception as exc:  # report, keep the headline measurement
+                extras["autograd"] = {"error": repr(exc)[:200]}
     dw = None
     if rank == 0 and not args.no_dw:
         try:
@@ -686,7 +901,10 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(k_mix)
+        try:
+            cpu = oracle_batch_sample(k_mix, budget_s=15.0)
+        except Exception as exc:  # report, keep the headline measurement
+            cpu = {"error": repr(exc)[:200]}
 
     if rank == 0:
         line = {
@@ -694,44 +912,34 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": statistics.mean(t_mix),
             "ms_per_step_median": statistics.median(t_mix), "ms_per_step_min": min(t_mix), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(DIMS), "mu": MU, "kappa": KAPPA, "eps": EPS,
-                       "rhs_per_step": NRHS,
+            "config": {"workload": HEAD_WORKLOAD, "dims": [list(d) for d in HEAD_DIMS], "mu": HEAD_MU,
+                       "kappa": KAPPA, "eps": EPS, "rhs_per_lattice": NRHS, "sequences_per_step": nseq,
                        "autotuned_shapes": {"pass1_sites_per_block": tuned[0], "regen_blocks_per_sm": tuned[1],
-                                            "regen_sequences_per_block": tuned[2]}
-                       if tuned else None,
-                       "method": "batched two-sided Lanczos, two-pass mixed (FP32 pass 1, FP64 pass 2)",
-                       "k": k_mix, "m_deflated": args.m, "deflation_setup": eig,
-                       "max_rel_err_vs_k1000_fp64": err_mix,
+                                            "regen_sequences_per_block": tuned[2]} if tuned else None,
+                       "method": ("batched two-sided Lanczos, two-pass mixed: FP32 pass 1 (12-real links), "
+                                  "double-float pass 2 (about 48 significant bits), FP64 coefficients"),
+                       "k": k_mix, "m_deflated": HEAD_M, "deflation_setup": setup,
+                       "max_rel_err_vs_k1500_fp64": err64_mix,
+                       "max_rel_err_vs_oracle": erro_mix,
+                       "oracle_sources": sorted(orefs_head),
+                       "k1500_fp64_reference_vs_oracle": ref_vs_oracle,
                        "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "roofline_phases": roof_all,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
-            "gpu_launches": batch_launches(NRHS, k_mix, args.m) * args.steps,
+            "gpu_launches": headline_launches(k_mix) * args.steps,
             "clocks": clk,
-            "fp64_batched": {"solves_per_s": NRHS * 1e3 / statistics.mean(t_b64), "ms_per_batch": statistics.mean(t_b64),
-                             "k": k_64, "max_rel_err_vs_k1000_fp64": err_64},
-            "mixed_single_source": {"solves_per_s": 1e3 / statistics.mean(t_s), "ms": statistics.mean(t_s), "k": k_s,
-                                    "rel_err_vs_k1000_fp64": err_s, "kernels": "persistent passes",
-                                    "profile_ms_by_kernel_class": single_profile,
-                                    "with_reprojection": reproj},
-            "fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_s64), "ms": statistics.mean(t_s64),
-                                   "k": k_s64, "rel_err_vs_k1000_fp64": err_s64},
-            "arnoldi_fp64_single_source": {"solves_per_s": 1e3 / statistics.mean(t_arn), "ms": statistics.mean(t_arn),
-                                           "k": k_arn, "rel_err_vs_k1000_fp64": err_arn,
-                                           "k_ratio_2sl_over_arnoldi": (k_s64 / k_arn) if k_arn else None},
-            "arnoldi_doublefloat_single_source": {"solves_per_s": 1e3 / statistics.mean(t_adf),
-                                                  "ms": statistics.mean(t_adf), "k": k_adf,
-                                                  "rel_err_vs_k1000_fp64": err_adf,
-                                                  "gram_schmidt_sweeps": adf_sweeps},
             "profile_ms_per_batch": {kk: round(v, 4) for kk, v in prof.items()},
-            "multi_lattice_batch": multi,
+            "fp64_batched": fp64,
+            **extras,
             "dw": dw,
-            "autograd": grads,
         }
         print(json.dumps(line))
     bt.close()
+    for c in ctxs:
+        c.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -743,21 +951,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=0, help="fix the Krylov size (skip the accuracy calibration)")
-    ap.add_argument("--m", type=int, default=M_DEFL, help="deflated eigenpairs (0: none)")
+    ap.add_argument("--m", type=int, default=M_DEFL, help="deflated eigenpairs of the 8^4 extras (0: none)")
     ap.add_argument("--no-dw", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-multi", action="store_true", help="skip the four-lattice point-source batch")
+    ap.add_argument("--no-extras", action="store_true", help="only the headline batch (and the stencil bandwidth)")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient timings")
-    ap.add_argument("--single", action="store_true", help="with --solves-only: single-source solves instead of batches")
     ap.add_argument("--dw-only", action="store_true", help="only the stencil bandwidth measurement (--steps repetitions)")
     ap.add_argument("--dw-dims", default="", help="lattice of the stencil bandwidth measurement, e.g. 32,32,32,32")
-    ap.add_argument("--arnoldi", action="store_true",
-                    help="with --solves-only: single-source double-float Arnoldi solves (D_ov b) instead")
     ap.add_argument("--profile-one", action="store_true",
                     help="with --solves-only: one extra solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--solves-only", action="store_true",
-                    help="only the timed solves (for profiler captures): needs --k, skips calibration, "
-                         "profile, FP64/Arnoldi/e2e legs, the bandwidth lattice and the CPU baseline")
+                    help="only the timed headline solves (for profiler captures): needs --k, skips calibration, "
+                         "profile, e2e, extras, the bandwidth lattice and the CPU baseline")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

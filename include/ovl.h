@@ -91,6 +91,11 @@ typedef struct ovl_ctx ovl_ctx;
                                     persistent cooperative kernels (default on small lattices)   */
 #define OVL_PASS2_F64    0x80000 /* MIXED: regeneration pass in native FP64                       */
 #define OVL_NO_TUNE      0x200000 /* batch_solve: keep the current launch shapes, no autotuning     */
+#define OVL_ARNOLDI_CGS2 0x400000 /* sign_krylov ARNOLDI with MIXED: classical Gram-Schmidt applied
+                                     twice, four sweeps over the basis per step.  The default is the
+                                     delayed form (the second Gram-Schmidt pass of step j fused with
+                                     the first of step j + 1): two sweeps per step, the same Arnoldi
+                                     process (Sec. 2, Eq. 2.2-2.3) in exact arithmetic             */
 #define OVL_PASS2_DF     0x100000 /* MIXED: regeneration pass in double-float arithmetic (FP32 pairs,
                                     about 48 significant bits, on the FP32 pipe).  Default: double-
                                     float in batched solves, FP64 in single solves (one source per

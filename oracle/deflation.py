@@ -57,8 +57,13 @@ def eigenpairs_dense(A: np.ndarray, m: int, select: str = "re") -> Deflation:
 
 
 def eigenpairs_arpack(A, m: int, select: str = "re", extra: int | None = None,
-                      tol: float = 1e-12, seed: int = 0) -> Deflation:
-    """Right and left eigenpairs of the sparse A near 0 by ARPACK shift-invert."""
+                      tol: float = 1e-12, seed: int = 0, permc_spec: str = "MMD_AT_PLUS_A") -> Deflation:
+    """Right and left eigenpairs of the sparse A near 0 by ARPACK shift-invert.
+
+    The inverse is applied through a sparse LU factorisation of A; ``permc_spec`` is its column
+    ordering (the same factors up to rounding for any ordering; a minimum-degree ordering of
+    A^T + A suits the structurally symmetric stencil and keeps the fill several times smaller
+    than the unsymmetric COLAMD default on 4D lattices)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as sla
 
@@ -66,7 +71,7 @@ def eigenpairs_arpack(A, m: int, select: str = "re", extra: int | None = None,
     n_ev = m + (extra if extra is not None else max(4, m // 2))
     rng = np.random.default_rng(seed)
     v0 = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
-    lu = sla.splu(A)
+    lu = sla.splu(A, permc_spec=permc_spec)
     op = sla.LinearOperator(A.shape, matvec=lu.solve, dtype=np.complex128)
     opH = sla.LinearOperator(A.shape, matvec=lambda x: lu.solve(x, trans="H"),
                              dtype=np.complex128)

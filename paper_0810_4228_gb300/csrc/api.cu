@@ -422,6 +422,27 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
         double2* x64 = c->s64;  // FP64 value of v_j, the stencil's input
         prof(c, KC_ANORM, [&] { ovl::launch_adf_start(c->bR, Vd, x64, ks, n, st); });
         const int ldH = c->kcap + 1;
+        // default: delayed CGS2 (two basis sweeps per step); OVL_ARNOLDI_CGS2: the classical form below
+        if (!(flags & OVL_ARNOLDI_CGS2)) {
+            for (int j = 0; j < k; ++j) {
+                float4* uj = Vd + (size_t)j * n;
+                float4* un = Vd + (size_t)(j + 1) * n;
+                prof(c, KC_ADSLASH, [&] { ovl::launch_dslash(c->U64, 0, x64, c->t64, mu, kappa, 1, g, st, ks); });
+                prof(c, KC_ADOT, [&] {
+                    ovl::launch_adf_dot2(Vd, n, j + 1, uj, c->t64, c->h1, c->h2, part, n, c->num_sms, ks, st);
+                }, 2);
+                prof(c, KC_ANORM, [&] { ovl::launch_adf_dcgs(c->H, ldH, c->h1, c->h2, h1d, h2d, ks, j, 0, st); });
+                prof(c, KC_AAXPY, [&] {
+                    ovl::launch_adf_update2(Vd, n, j, h1d, h2d, uj, un, c->t64, x64, c->H, ldH, c->h1, c->h2, n, ks,
+                                            st);
+                });
+            }
+            // re-orthogonalise u_k against V_0..V_{k-1}: finishes column k - 1 of H
+            prof(c, KC_ADOT, [&] {
+                ovl::launch_adf_dot(Vd, n, k + 1, Vd + (size_t)k * n, c->h1, h1d, part, n, c->num_sms, ks, st);
+            }, 2);
+            prof(c, KC_ANORM, [&] { ovl::launch_adf_dcgs(c->H, ldH, c->h1, c->h2, h1d, h2d, ks, k, 1, st); });
+        } else
         for (int j = 0; j < k; ++j) {
             float4* t = Vd + (size_t)(j + 1) * n;
             prof(c, KC_ADSLASH, [&] {

@@ -304,6 +304,268 @@ __global__ void __launch_bounds__(AD_T) k_adf_combine(const float4* __restrict__
     }
 }
 
+// ================================================== low-synch Arnoldi: delayed CGS2 ==
+// Classical Gram-Schmidt applied twice with the second pass delayed by one step (the "DCGS2" of the
+// low-synchronisation Gram-Schmidt literature: Swirydowicz, Langou, Ananthan, Yang and Thomas,
+// Numer. Linear Algebra Appl. 28 (2021); Bielich, Langou, Thomas, Swirydowicz, Yamazaki and Boman,
+// Parallel Comput. 112 (2022)), on the double-float basis.  At step j the slots V_0..V_{j-1} hold
+// final orthonormal vectors and slot j holds u_j, A v_{j-1} projected once and neither
+// re-orthogonalised nor normalised; the stencil has produced w = A u_j (FP64) from its FP64 value.
+//  (1) one sweep over V_0..V_j:  c = V_{<j}^dag u_j, rho^2 = u_j^dag u_j, d = V_{<j}^dag w,
+//      e = u_j^dag w                                           (k_adf_dot2, k_adf_dot2_reduce)
+//  (2) nu^2 = rho^2 - |c|^2 (V_{<j} orthonormal); column j-1 of H becomes final,
+//      H[<j, j-1] += c, H[j, j-1] = nu; v_j = (u_j - V_{<j} c) / nu             (k_adf_dcgs)
+//  (3) one sweep over V_0..V_{j-1}:  v_j, and u_{j+1} = A v_j - V_{<=j} h = w / nu - V_{<j} d / nu
+//      - r v_j with r = (e - c^dag d) / nu^2; the tentative column j of H is
+//      h = (d / nu - g, r - c_{j-1}), g = H[<=j, <j] c / nu                      (k_adf_update2)
+// because A v_j = (w - A V_{<j} c) / nu = (w - V_{<=j} H[<=j, <j] c) / nu by the Arnoldi relation
+// of the final columns: the projection coefficients of A v_j come from the sums of (1) without
+// another pass, and the basis is read twice per step instead of four times.  After the last step
+// one more dot sweep re-orthogonalises u_k and finishes column k-1.  In exact arithmetic this is
+// the Arnoldi process of Sec. 2 (Eq. 2.2-2.3).
+
+static size_t adf_dot2_smem() { return sizeof(float4) * (2 * (size_t)AD_CH + (size_t)AD_W * 2 * AD_SUB); }
+
+// stage 1 of the two-vector dot, grid (chunks, vector groups): V_l^dag x1 and V_l^dag x2 for every
+// l < nvec over the block's chunk; x1 is a double-float vector, x2 an FP64 one (split on staging).
+// Partials: part[(2 l + q) * gridDim.x + chunk], q = 0 for x1, 1 for x2.
+__global__ void __launch_bounds__(AD_T) k_adf_dot2(const float4* __restrict__ V, size_t ld, int nvec, int vpb,
+                                                   const float4* __restrict__ x1, const double2* __restrict__ x2,
+                                                   double2* __restrict__ part, size_t n, const KState* ks) {
+    extern __shared__ float4 adf_sm[];
+    float4* xs1 = adf_sm;
+    float4* xs2 = adf_sm + AD_CH;
+    if (ks->done || ks->status) return;
+    const size_t base = (size_t)blockIdx.x * AD_CH;
+    const int lim = (int)(n - base < (size_t)AD_CH ? n - base : (size_t)AD_CH);
+    for (int q = threadIdx.x; q < lim; q += AD_T) {
+        xs1[q] = x1[base + q];
+        xs2[q] = to_f4(d2df(x2[base + q]));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4* wb = adf_sm + 2 * AD_CH + (size_t)wid * 2 * AD_SUB;
+    const int l0 = blockIdx.y * vpb + wid;
+    const int l1 = min(nvec, blockIdx.y * vpb + vpb);
+    const int nv = l0 < l1 ? (l1 - l0 + AD_W - 1) / AD_W : 0;
+    const int ntile = (lim + AD_SUB - 1) / AD_SUB;
+    const int total = nv * ntile;
+    auto issue = [&](int it) {
+        const int a = it / ntile, si = it - a * ntile;
+        const float4* src = V + (size_t)(l0 + a * AD_W) * ld + base + (size_t)si * AD_SUB;
+        float4* dst = wb + (it & 1) * AD_SUB;
+        const int cnt = min(AD_SUB, lim - si * AD_SUB);
+        for (int u = lane; u < cnt; u += 32) cp_async16(dst + u, src + u);
+        cp_async_commit();
+    };
+    if (total > 0) issue(0);
+    dfacc re1 = {0.f, 0.f}, im1 = {0.f, 0.f}, re2 = {0.f, 0.f}, im2 = {0.f, 0.f};
+    for (int it = 0; it < total; ++it) {
+        if (it + 1 < total) {
+            issue(it + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const int a = it / ntile, si = it - a * ntile;
+        const float4* cur = wb + (it & 1) * AD_SUB;
+        const int cnt = min(AD_SUB, lim - si * AD_SUB);
+        if (si == 0) {
+            re1 = {0.f, 0.f};
+            im1 = {0.f, 0.f};
+            re2 = {0.f, 0.f};
+            im2 = {0.f, 0.f};
+        }
+#pragma unroll 4
+        for (int u = lane; u < cnt; u += 32) {
+            const cx<df> v = from_f4(cur[u]);
+            adf_dot_term(re1, im1, v, from_f4(xs1[si * AD_SUB + u]));
+            adf_dot_term(re2, im2, v, from_f4(xs2[si * AD_SUB + u]));
+        }
+        if (si == ntile - 1) {
+            const df s1r = warp_sum_df(dfacc_value(re1)), s1i = warp_sum_df(dfacc_value(im1));
+            const df s2r = warp_sum_df(dfacc_value(re2)), s2i = warp_sum_df(dfacc_value(im2));
+            if (lane == 0) {
+                const size_t l = (size_t)(l0 + a * AD_W);
+                part[(2 * l) * gridDim.x + blockIdx.x] = make_double2(s1r.to_double(), s1i.to_double());
+                part[(2 * l + 1) * gridDim.x + blockIdx.x] = make_double2(s2r.to_double(), s2i.to_double());
+            }
+        }
+        __syncwarp();  // this tile's buffer receives the copy issued two iterations on
+    }
+}
+
+// stage 2: one warp per (vector, operand) sums its chunk partials in FP64 (fixed order):
+// h1[l] = V_l^dag x1, h2[l] = V_l^dag x2
+__global__ void k_adf_dot2_reduce(const double2* __restrict__ part, int nblk, int nvec, double2* __restrict__ h1,
+                                  double2* __restrict__ h2, const KState* ks) {
+    if (ks->done || ks->status) return;
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= 2 * nvec) return;
+    double re = 0.0, im = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
+        const double2 v = part[(size_t)p * nblk + b];
+        re += v.x;
+        im += v.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) ((p & 1) ? h2 : h1)[p >> 1] = make_double2(re, im);
+}
+
+// (2): one block.  h1 = (c, rho^2) and h2 = (d, e) of step j (h2 unused when fin).  Finishes
+// column j-1 of H (j >= 1), decides a lucky breakdown (nu <= bdtol |H|), and for the update writes
+// cdf = c, qdf = d / nu (double-float), ks->red[1] = (1 / nu, nu), ks->red[2] = r.  fin = 1 after
+// the last step (j = k): only column k-1 is finished and the solve is marked done.
+__global__ void __launch_bounds__(1024) k_adf_dcgs(double2* __restrict__ H, int ldH, const double2* __restrict__ h1,
+                                                   const double2* __restrict__ h2, float4* __restrict__ cdf,
+                                                   float4* __restrict__ qdf, KState* ks, int j, int fin,
+                                                   double bdtol) {
+    __shared__ double red[4 * 32];  // block_sum<4>: 32 doubles per value
+    __shared__ double s_nu;
+    __shared__ int s_stop;
+    if (ks->done || ks->status) return;
+    // |c|^2, c^dag d, |H[<j, j-1] + c|^2
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = threadIdx.x; l < j; l += blockDim.x) {
+        const double2 c = h1[l];
+        acc[0] += c.x * c.x + c.y * c.y;
+        if (!fin) {
+            const double2 d = h2[l];
+            acc[1] += c.x * d.x + c.y * d.y;
+            acc[2] += c.x * d.y - c.y * d.x;
+        }
+        const double2 hv = H[l + (size_t)(j - 1) * ldH];
+        const double hr = hv.x + c.x, hi = hv.y + c.y;
+        acc[3] += hr * hr + hi * hi;
+    }
+    block_sum<4>(acc, red);
+    if (threadIdx.x == 0) {
+        const double rho2 = h1[j].x;
+        const double nu2 = rho2 - acc[0];
+        const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+        int stop = 0;
+        if (j >= 1) {
+            H[j + (size_t)(j - 1) * ldH] = make_double2(nu, 0.0);
+            const double colnorm = sqrt(acc[3] + nu * nu);
+            if (colnorm > ks->anorm) ks->anorm = colnorm;
+            ks->kused = j;
+            if (fin || nu <= bdtol * fmax(ks->anorm, 1e-300)) stop = 1;  // last column, or K_j invariant
+        } else if (!(nu > 0.0)) {
+            stop = 1;  // zero start vector (cannot happen after the deflation split's check)
+        }
+        if (stop) {
+            ks->done = 1;
+        } else {
+            const double inu = 1.0 / nu;
+            ks->red[1] = make_double2(inu, nu);
+            // r = (e - c^dag d) / nu^2
+            const double2 e = h2[j];
+            ks->red[2] = make_double2((e.x - acc[1]) * inu * inu, (e.y - acc[2]) * inu * inu);
+        }
+        s_nu = nu;
+        s_stop = stop;
+    }
+    __syncthreads();
+    const double inu = s_stop ? 0.0 : 1.0 / s_nu;
+    for (int l = threadIdx.x; l < j; l += blockDim.x) {
+        const double2 c = h1[l];
+        const double2 hv = H[l + (size_t)(j - 1) * ldH];
+        H[l + (size_t)(j - 1) * ldH] = make_double2(hv.x + c.x, hv.y + c.y);
+        if (!s_stop) {
+            cdf[l] = to_f4(d2df(c));
+            const double2 d = h2[l];
+            qdf[l] = to_f4(d2df(make_double2(d.x * inu, d.y * inu)));
+        }
+    }
+}
+
+// (3): per element e, over the final vectors V_0..V_{j-1}: s1 = sum_l c_l V_l[e], s2 = sum_l
+// (d_l / nu) V_l[e]; then v_j = (u_j - s1) / nu into slot j (in place of u_j) and u_{j+1} =
+// w / nu - s2 - r v_j into slot j + 1 and, as FP64, into x64 (the next stencil's input).  Blocks
+// 0..j also write the tentative column j of H: H[i, j] = d_i / nu - g_i (i < j), r - c_{j-1}
+// (i = j), g_i = sum_{l >= i-1} H[i, l] c_l / nu (upper Hessenberg rows of the final columns).
+__global__ void __launch_bounds__(AD_T) k_adf_update2(const float4* __restrict__ V, size_t ld, int j,
+                                                      const float4* __restrict__ cdf, const float4* __restrict__ qdf,
+                                                      float4* __restrict__ uj, float4* __restrict__ unext,
+                                                      const double2* __restrict__ w, double2* __restrict__ x64,
+                                                      double2* __restrict__ H, int ldH, const double2* __restrict__ h1,
+                                                      const double2* __restrict__ h2, size_t n, KState* ks) {
+    __shared__ float4 red1[AD_W][32];
+    __shared__ float4 red2[AD_W][32];
+    if (ks->done || ks->status) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double2 sc = ks->red[1];
+    const double inu = sc.x;
+    const double2 r = ks->red[2];
+    if ((int)blockIdx.x <= j && wid == 0) {
+        const int i = blockIdx.x;
+        double gr = 0.0, gi = 0.0;
+        for (int l = max(i - 1, 0) + lane; l < j; l += 32) {
+            const double2 hv = H[i + (size_t)l * ldH], c = h1[l];
+            gr += hv.x * c.x - hv.y * c.y;
+            gi += hv.x * c.y + hv.y * c.x;
+        }
+        gr = warp_sum(gr) * inu;
+        gi = warp_sum(gi) * inu;
+        if (lane == 0) {
+            double2 hv;
+            if (i < j) {
+                const double2 d = h2[i];
+                hv = make_double2(d.x * inu - gr, d.y * inu - gi);
+            } else {
+                const double2 cl = j > 0 ? h1[j - 1] : make_double2(0.0, 0.0);
+                hv = make_double2(r.x - cl.x, r.y - cl.y);
+            }
+            H[i + (size_t)j * ldH] = hv;
+        }
+    }
+    const df dinu(inu);
+    const cx<df> rr = d2df(r);
+    const size_t ntile = (n + 31) / 32;
+    for (size_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const size_t e = tile * 32 + lane;
+        const bool in = e < n;
+        dfacc a1r = {0.f, 0.f}, a1i = {0.f, 0.f}, a2r = {0.f, 0.f}, a2i = {0.f, 0.f};
+        if (in) {
+#pragma unroll 4
+            for (int l = wid; l < j; l += AD_W) {
+                if ((lane & 7) == 0 && l + AD_PFV * AD_W < j)  // one lane per 128-byte line
+                    prefetch_l2(V + (size_t)(l + AD_PFV * AD_W) * ld + e);
+                const cx<df> v = from_f4(__ldg(V + (size_t)l * ld + e));
+                adf_axpy_term(a1r, a1i, from_f4(__ldg(cdf + l)), v);
+                adf_axpy_term(a2r, a2i, from_f4(__ldg(qdf + l)), v);
+            }
+        }
+        red1[wid][lane] = make_float4(a1r.s, a1r.e, a1i.s, a1i.e);
+        red2[wid][lane] = make_float4(a2r.s, a2r.e, a2i.s, a2i.e);
+        __syncthreads();
+        if (wid == 0 && in) {
+            df s1r = df_fast2sum(red1[0][lane].x, red1[0][lane].y), s1i = df_fast2sum(red1[0][lane].z, red1[0][lane].w);
+            df s2r = df_fast2sum(red2[0][lane].x, red2[0][lane].y), s2i = df_fast2sum(red2[0][lane].z, red2[0][lane].w);
+#pragma unroll
+            for (int q = 1; q < AD_W; ++q) {
+                const float4 p1 = red1[q][lane], p2 = red2[q][lane];
+                s1r = s1r + df_fast2sum(p1.x, p1.y);
+                s1i = s1i + df_fast2sum(p1.z, p1.w);
+                s2r = s2r + df_fast2sum(p2.x, p2.y);
+                s2i = s2i + df_fast2sum(p2.z, p2.w);
+            }
+            const cx<df> u = from_f4(uj[e]);
+            const cx<df> vj = mk((u.r - s1r) * dinu, (u.i - s1i) * dinu);
+            const cx<df> ww = d2df(w[e]);
+            const cx<df> rv = rr * vj;
+            const cx<df> un = mk(ww.r * dinu - s2r - rv.r, ww.i * dinu - s2i - rv.i);
+            uj[e] = to_f4(vj);
+            unext[e] = to_f4(un);
+            x64[e] = df2d(un);
+        }
+        __syncthreads();  // red1, red2 are reused by the next tile
+    }
+}
+
 // ---------------------------------------------------------------- launchers --
 // the update kernel's grid: one block per 32 elements up to AD_MAXB blocks (its norm partials,
 // one double per block, must fit the solve's partials buffer of at least 2^16 doubles)
@@ -365,6 +627,37 @@ void launch_adf_update_fin(const float4* V, size_t ld, int nvec, const float4* h
 
 void launch_adf_normalize(float4* t, double2* x64, const KState* ks, size_t n, cudaStream_t st) {
     k_adf_normalize<<<adf_grid(n), 256, 0, st>>>(t, x64, ks, n);
+}
+
+void launch_adf_dot2(const float4* V, size_t ld, int nvec, const float4* x1, const double2* x2, double2* h1,
+                     double2* h2, double* partials, size_t n, int num_sms, const KState* ks, cudaStream_t st) {
+    if (nvec <= 0) return;
+    const int nchunk = adf_dot_blocks(n);
+    const long long target = 8ll * (num_sms > 0 ? num_sms : 1);
+    long long vpw = ((long long)nvec * nchunk + (long long)AD_W * target - 1) / ((long long)AD_W * target);
+    if (vpw < 1) vpw = 1;
+    const int vpb = (int)(vpw * AD_W);
+    const int ngroup = (nvec + vpb - 1) / vpb;
+    double2* part = reinterpret_cast<double2*>(partials);
+    static unsigned long long attr_dev = 0;
+    if (first_use_on_device(attr_dev))
+        cudaFuncSetAttribute(k_adf_dot2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adf_dot2_smem());
+    k_adf_dot2<<<dim3(nchunk, ngroup), AD_T, adf_dot2_smem(), st>>>(V, ld, nvec, vpb, x1, x2, part, n, ks);
+    k_adf_dot2_reduce<<<(2 * nvec + 7) / 8, 256, 0, st>>>(part, nchunk, nvec, h1, h2, ks);
+}
+
+void launch_adf_dcgs(double2* H, int ldH, const double2* h1, const double2* h2, float4* cdf, float4* qdf, KState* ks,
+                     int j, int fin, cudaStream_t st) {
+    // double-float sweeps: the lucky-breakdown threshold of the double-float CGS2 path (1e-11)
+    k_adf_dcgs<<<1, 1024, 0, st>>>(H, ldH, h1, h2, cdf, qdf, ks, j, fin, 1e-11);
+}
+
+void launch_adf_update2(const float4* V, size_t ld, int j, const float4* cdf, const float4* qdf, float4* uj,
+                        float4* unext, const double2* w, double2* x64, double2* H, int ldH, const double2* h1,
+                        const double2* h2, size_t n, KState* ks, cudaStream_t st) {
+    unsigned grid = adf_update_grid(n);
+    if (grid < (unsigned)j + 1) grid = (unsigned)j + 1;  // blocks 0..j each write one row of column j
+    k_adf_update2<<<grid, AD_T, 0, st>>>(V, ld, j, cdf, qdf, uj, unext, w, x64, H, ldH, h1, h2, n, ks);
 }
 
 void launch_adf_combine(const float4* V, size_t ld, const double2* c, float4* cdf, const KState* ks, int kmax,

@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256) k_newton_coop(const double2* alpha, const
                                                      int fallback) {
     extern __shared__ double2 prow[];
     __shared__ unsigned long long best;
-    __shared__ double red[32];
+    __shared__ double red[2 * 32];  // block_sum<2>: 32 doubles per value
     const long long max_spins = 20000000;
     int* err = &ks->timeout;
     // uniform entry decision (all blocks read the same state before anyone writes it)

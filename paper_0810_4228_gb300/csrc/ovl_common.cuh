@@ -301,7 +301,8 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum NV doubles over the block; result valid in thread 0.  smem: 32*NV doubles.
+// Sum NV doubles over the block; result valid in thread 0.  smem: 32*NV doubles (value j of warp w
+// goes to smem[j * 32 + w]), whatever the block size.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;

@@ -125,6 +125,15 @@ void launch_adf_update_fin(const float4* V, size_t ld, int nvec, const float4* h
 // t <- t / |t| (|t| from the last update) and its FP64 value into x64
 void launch_adf_normalize(float4* t, double2* x64, const KState* ks, size_t n, cudaStream_t st);
 // y += sum_{l < kused} c_l V_l; cdf: kmax float4 scratch
+// delayed CGS2 (low-synch Arnoldi, csrc/arnoldi_df.cu): h1[l] = V_l^dag x1, h2[l] = V_l^dag x2 for l < nvec in
+// one sweep (x1 double-float, x2 FP64); the step's scalar work; the fused update of v_j and u_{j+1}
+void launch_adf_dot2(const float4* V, size_t ld, int nvec, const float4* x1, const double2* x2, double2* h1,
+                     double2* h2, double* partials, size_t n, int num_sms, const KState* ks, cudaStream_t st);
+void launch_adf_dcgs(double2* H, int ldH, const double2* h1, const double2* h2, float4* cdf, float4* qdf, KState* ks,
+                     int j, int fin, cudaStream_t st);
+void launch_adf_update2(const float4* V, size_t ld, int j, const float4* cdf, const float4* qdf, float4* uj,
+                        float4* unext, const double2* w, double2* x64, double2* H, int ldH, const double2* h1,
+                        const double2* h2, size_t n, KState* ks, cudaStream_t st);
 void launch_adf_combine(const float4* V, size_t ld, const double2* c, float4* cdf, const KState* ks, int kmax,
                         double2* y, size_t n, cudaStream_t st);
 

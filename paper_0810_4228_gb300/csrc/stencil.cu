@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
                                                      double2* alpha, int step, int klast, double* partials,
                                                      unsigned int* counter, Geom g) {
     using R = typename LinkReal<LF>::R;
-    __shared__ double red[64];
+    __shared__ double red[3 * 32];  // grid_sum_last<3>: 32 doubles per value
     if (ks->done || ks->status) return;
     const double2 sv = ks->sv, sw = ks->sw;
     const int i = site_of_thread(g);

@@ -26,7 +26,7 @@ ARNOLDI, LANCZOS2 = 0, 1
 GAMMA5, DAGGER, NATIVE, HOST, F32, F32_FULL = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 OVERLAP, MIXED, TWO_PASS, INNER_NEWTON, NO_GRAPH, PROFILE = 0x100, 0x200, 0x400, 0x1000, 0x2000, 0x4000
 STENCIL_SITE, STENCIL_SPLIT, REPROJ, STEPWISE, PASS2_F64, PASS2_DF = 0x10000, 0x20000, 0x8000, 0x40000, 0x80000, 0x100000
-NO_TUNE = 0x200000
+NO_TUNE, ARNOLDI_CGS2 = 0x200000, 0x400000
 
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EBREAKDOWN",
              ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}

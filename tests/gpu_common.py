@@ -42,3 +42,52 @@ def config4(eps=0.5, seed=1000, mu=0.3):
 def torch_c128(x):
     import torch
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+REFS_PATH = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
+                                       "golden", "oracle_refs.npz")
+
+
+@functools.lru_cache(maxsize=1)
+def oracle_refs():
+    """The FP64 oracle's sgn(A) b on the full-size workloads, as written by
+    tests/golden/make_oracle_refs.py: {case: {field: array}}."""
+    z = np.load(REFS_PATH)
+    out = {}
+    for key in z.files:
+        case, field = key.split("/", 1)
+        out.setdefault(case, {})[field] = z[key]
+    return out
+
+
+@functools.lru_cache(maxsize=4)
+def _proj_vectors(dims, n):
+    return np.stack([synth.gaussian_source(dims, 9000 + j) for j in range(n)])
+
+
+def oracle_distance(y, ref):
+    """(relative 2-norm over the sampled components, largest sampled difference relative to the
+    largest sampled magnitude, relative error estimated from the stored projections
+    g_j^dag sgn(A) b) of a full vector y against the oracle's stored sgn(A) b.  The g_j have
+    i.i.d. N(0, 1) real and imaginary parts, so E|g^dag e|^2 = 2 |e|^2."""
+    y = np.asarray(y).ravel()
+    G = _proj_vectors(tuple(int(d) for d in ref["dims"]), len(ref["proj"]))
+    d = y[ref["idx"]] - ref["val"]
+    pe = G.conj() @ y - ref["proj"]
+    return (float(np.linalg.norm(d) / np.linalg.norm(ref["val"])),
+            float(np.abs(d).max() / np.abs(ref["val"]).max()),
+            float(np.sqrt(np.mean(np.abs(pe) ** 2) / 2.0) / float(ref["norm"])))
+
+
+def assert_oracle_close(y, ref, tol, what=""):
+    """Element by element on the sampled components and on the whole vector through the
+    projections (which estimate the relative 2-norm error to within a factor of about two with
+    eight projections; the bound below allows three)."""
+    rel_s, max_s, rel_p = oracle_distance(y, ref)
+    assert rel_s <= tol and max_s <= tol and rel_p <= 3 * tol, (what, rel_s, max_s, rel_p)
+    return rel_s, max_s, rel_p
+
+
+def gamma5_diag(V):
+    """Chiral gamma5 = diag(1, 1, -1, -1) in spin, on the flattened index 12 s + 3 spin + colour."""
+    return np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V)

@@ -53,7 +53,8 @@ def test_flags_match_header():
         src = f.read()
     for name in ("ARNOLDI", "LANCZOS2", "GAMMA5", "DAGGER", "NATIVE", "HOST", "F32", "F32_FULL",
                  "OVERLAP", "MIXED", "TWO_PASS", "INNER_NEWTON", "NO_GRAPH", "PROFILE",
-                 "STENCIL_SITE", "STENCIL_SPLIT", "REPROJ", "STEPWISE", "PASS2_F64", "PASS2_DF", "NO_TUNE"):
+                 "STENCIL_SITE", "STENCIL_SPLIT", "REPROJ", "STEPWISE", "PASS2_F64", "PASS2_DF", "NO_TUNE",
+                 "ARNOLDI_CGS2"):
         m = re.search(r"#define\s+OVL_%s\s+(0x[0-9a-fA-F]+|\d+)" % name, src)
         assert m, name
         assert int(m.group(1), 0) == getattr(ovl, name), name

@@ -196,6 +196,29 @@ def test_arnoldi_lucky_breakdown(ovl):
         assert rel(y, ref) < 1e-10
 
 
+@pytest.mark.parametrize("k", [1, 2, 7, 60, 300])
+def test_arnoldi_delayed_cgs2_matches_classical(ovl, c4, k):
+    """The double-float Arnoldi's default delayed Gram-Schmidt (two basis sweeps per step, the
+    second pass of step j fused with the first of step j + 1) and the classical form (four sweeps,
+    OVL_ARNOLDI_CGS2) build the same Arnoldi process (Sec. 2, Eq. 2.2-2.3): equal results to
+    1e-12 from k = 1 on, and the oracle's Arnoldi (CGS2) result at small k; with 20 deflated
+    eigenpairs as well."""
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    yd, infod = _solve(ovl, ctx, ovl.ARNOLDI, k, c4["mu"], c4["b"], flags=ovl.MIXED)
+    yc, infoc = _solve(ovl, ctx, ovl.ARNOLDI, k, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.ARNOLDI_CGS2)
+    assert infod["status"] == 0 and infod["k_used"] == infoc["k_used"] == k
+    assert rel(yd, yc) < 1e-12
+    if k <= 60:
+        assert rel(yd, K.sign_arnoldi(c4["A"].dot, c4["b"], k)) < 1e-10
+    if k == 300:
+        assert rel(yd, c4["ref"]) < 1e-10
+        d = Dm.eigenpairs_dense(c4["A"].toarray(), 20)
+        ctx.set_deflation(c4["mu"], KAPPA, d.lam, torch_c128(d.R.T.copy()), torch_c128(d.L.T.copy()))
+        yd, _ = _solve(ovl, ctx, ovl.ARNOLDI, 200, c4["mu"], c4["b"], flags=ovl.MIXED)
+        yc, _ = _solve(ovl, ctx, ovl.ARNOLDI, 200, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.ARNOLDI_CGS2)
+        assert rel(yd, yc) < 1e-12 and rel(yd, c4["ref"]) < 1e-10
+
+
 @pytest.mark.parametrize("flags,tol", [("TWO_PASS", 1e-10), ("MIXED", 1e-8), ("MIXED|STEPWISE", 1e-8)])
 def test_two_pass(ovl, c4, flags, tol):
     """Two-pass 2sL (Sec. 5): FP64 or FP32 pass 1 for the coefficients, FP64
