@@ -314,6 +314,31 @@ int ovl_get_deflation(ovl_ctx* ctx, int* m_out, double* lambda, void* R, void* L
 int ovl_sign_krylov(ovl_ctx* ctx, int method, int k, double mu, double kappa,
                     const void* b, void* out, int flags, ovl_info* info);
 
+/* --- eigenvalues of the overlap operator ------------------------------------------------------ */
+typedef struct {
+    int       nconv;          /* eigenpairs returned (nev on success)                        */
+    int       restarts;       /* Arnoldi cycles                                              */
+    long long sign_solves;    /* applications of D_ov (each one sign solve of k steps)       */
+    double    ritz_residual;  /* largest |h| |e^T z| of the returned Ritz pairs              */
+    double    max_residual;   /* largest |D_ov x - lambda x| of the unit eigenvectors        */
+} ovl_ovinfo;
+
+/* The nev eigenvalues of D_ov(mu) = 1 + gamma5 sgn(gamma5 D_w(mu)) (Eq. 1.1) nearest 0, the
+ * application Sec. 5 names as the next use of the sign function (the paper gives no method for
+ * it): thick-restart Arnoldi with a basis of nkrylov vectors (0 = automatic, max(2 nev + 20, 40))
+ * in which every application of D_ov is one ovl_sign_krylov solve by `method` (OVL_ARNOLDI or
+ * OVL_LANCZOS2) with Krylov size k, the installed deflation and `flags` (OVL_MIXED, OVL_TWO_PASS,
+ * OVL_INNER_NEWTON, OVL_ARNOLDI_CGS2; OVL_OVERLAP is implied; OVL_HOST and OVL_PROFILE are
+ * rejected).  The eigenvalues are accurate to about the sign solves' relative error.
+ *   - converged when every returned Ritz pair has |h| |e^T z| <= tol (|D_ov| <= 2 at mu = 0);
+ *   - lambda: HOST array of 2 nev doubles (re, im), sorted by modulus, nearest 0 first;
+ *   - vecs: DEVICE array of nev canonical complex128 unit eigenvectors (12V each), or NULL;
+ *   - at most maxit restart cycles, else OVL_ENOCONV (info tells how far it got);
+ *   - a failing sign solve ends the run with its status (OVL_EBREAKDOWN included);
+ *   - allocates its own workspace ((2 nkrylov + 2) vectors) and frees it before returning. */
+int ovl_overlap_eigs(ovl_ctx* ctx, int method, int k, double mu, double kappa, int flags, int nev,
+                     int nkrylov, double tol, int maxit, double* lambda, void* vecs, ovl_ovinfo* info);
+
 /* --- per-kernel profile -------------------------------------------------------------------- */
 
 /* One kernel class of a profiled solve: its name, how many times it was queued, how many

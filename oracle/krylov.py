@@ -18,6 +18,17 @@
                          b_perp^R = (1 - R L^dag) b, b_perp^L = (1 - L R^dag) b (Eq. 4.5).
                          Deflated start vectors: v_1 = b_perp^R/|b_perp^R| and
                          w_1 = b_perp^L / conj(b_perp^L^dag v_1), so that w_1^dag v_1 = 1.
+* ``sign_arnoldi_restarted`` -- the Arnoldi approximation restarted every m steps with a
+                         basis of m + 1 vectors (the restart the paper's discussion of the
+                         N k^2 basis cost in Sec. 5 calls for; the paper gives no scheme).  The
+                         restart follows Eiermann and Ernst (SIAM J. Numer. Anal. 44, 2006):
+                         cycle c continues from the last basis vector of cycle c - 1, its
+                         Hessenberg block joins the accumulated matrix H_c (block lower
+                         bidiagonal, upper Hessenberg), and y gains |b| V_c [f(H_c) e_1] over
+                         the rows of cycle c (the earlier rows of f(H_c) e_1 equal those of
+                         f(H_{c-1}) e_1 because H_c is block lower triangular).  The inner sign
+                         of H_c is Roberts' iteration: H_c is far from normal and its spectral
+                         evaluation loses all accuracy after a few cycles.
 * ``sign_lanczos2_twopass`` -- the two-pass procedure mentioned in Sec. 5:
                          pass 1 keeps only alpha, beta, gamma; pass 2 regenerates
                          v_i from them and accumulates y.
@@ -41,6 +52,7 @@ __all__ = [
     "tridiag",
     "inner_sign_e1",
     "sign_arnoldi",
+    "sign_arnoldi_restarted",
     "sign_lanczos2",
     "sign_lanczos2_twopass",
     "overlap_from_sign",
@@ -188,6 +200,34 @@ def sign_arnoldi(matvec, b, k: int, defl: Deflation | None = None,
     y = exact + nb * (V[:, :j] @ c)
     if return_info:
         return y, {"k_used": j, "H": H[:j, :j], "V": V[:, :j], "c": nb * c}
+    return y
+
+
+def sign_arnoldi_restarted(matvec, b, m: int, cycles: int, defl: Deflation | None = None,
+                           inner: str = "newton", return_info: bool = False):
+    """sgn(A) b by Arnoldi restarted every m steps (at most cycles cycles, cycles * m steps in all);
+    with LR deflation the restarted process runs on b_perp (Sec. 3, Eq. 3.4)."""
+    b = np.asarray(b, dtype=np.complex128)
+    exact, bperp, _ = _split(b, defl)
+    nb = np.linalg.norm(bperp)
+    y = exact.copy()
+    if nb == 0 or m == 0 or cycles == 0:
+        return (y, {"k_used": 0, "H": np.zeros((0, 0), complex)}) if return_info else y
+    Ht = np.zeros((cycles * m + 1, cycles * m), dtype=np.complex128)
+    v = bperp / nb
+    K = 0
+    for _ in range(cycles):
+        V, H, _ = arnoldi(matvec, v, m)
+        j = H.shape[1]                       # steps of this cycle (< m on a lucky breakdown)
+        Ht[K:K + j + 1, K:K + j] = H         # includes the coupling entry H[j, j-1] below the block
+        f = inner_sign_e1(Ht[:K + j, :K + j], inner)
+        y = y + nb * (V[:, :j] @ f[K:K + j])
+        K += j
+        if j < m or H[j, j - 1] == 0:        # invariant Krylov space: the approximation is final
+            break
+        v = V[:, j]
+    if return_info:
+        return y, {"k_used": K, "H": Ht[:K, :K]}
     return y
 
 

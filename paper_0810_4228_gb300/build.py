@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libovl.so")
-SOURCES = ["stencil.cu", "krylov.cu", "arnoldi_df.cu", "inner_sign.cu", "api.cu", "eigs.cu", "noalloc.cu", "persistent.cu", "grad.cu", "grad_krylov.cu", "batch.cu", "host_eig.cpp"]
+SOURCES = ["stencil.cu", "krylov.cu", "arnoldi_df.cu", "inner_sign.cu", "api.cu", "eigs.cu", "noalloc.cu", "persistent.cu", "grad.cu", "grad_krylov.cu", "batch.cu", "overlap_eigs.cu", "host_eig.cpp"]
 HEADERS = ["ovl_common.cuh", "ovl_kernels.h", "ctx.h", "stencil_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--extended-lambda"]

@@ -732,7 +732,8 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
     ovl::launch_pack_spinor(bin, c->b64, 0, c->g, c->st);
     CUDA_TRY(c, cudaGetLastError());
 
-    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_STEPWISE | OVL_PASS2_F64 | OVL_PASS2_DF);
+    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_STEPWISE | OVL_PASS2_F64 |
+                                OVL_PASS2_DF | OVL_ARNOLDI_CGS2);
     bool ran = false;
     c->prof_on = (flags & OVL_PROFILE) != 0;
     if (!(flags & (OVL_NO_GRAPH | OVL_PROFILE))) {

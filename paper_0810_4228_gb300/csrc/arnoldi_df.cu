@@ -371,12 +371,7 @@ __global__ void __launch_bounds__(AD_T) k_adf_dot2(const float4* __restrict__ V,
         const int a = it / ntile, si = it - a * ntile;
         const float4* cur = wb + (it & 1) * AD_SUB;
         const int cnt = min(AD_SUB, lim - si * AD_SUB);
-        if (si == 0) {
-            re1 = {0.f, 0.f};
-            im1 = {0.f, 0.f};
-            re2 = {0.f, 0.f};
-            im2 = {0.f, 0.f};
-        }
+        if (si == 0) re1 = im1 = re2 = im2 = {0.f, 0.f};
 #pragma unroll 4
         for (int u = lane; u < cnt; u += 32) {
             const cx<df> v = from_f4(cur[u]);

@@ -38,7 +38,7 @@ EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl
            "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad", "ovl_batch_create",
            "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_batch_profile", "ovl_batch_tuning",
            "ovl_batch_set_tuning",
-           "ovl_sign_krylov_batched"]
+           "ovl_sign_krylov_batched", "ovl_overlap_eigs"]
 
 
 class OvlError(RuntimeError):
@@ -55,6 +55,14 @@ class KStat(ctypes.Structure):
 class EigInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("iterations", ctypes.c_int), ("matvecs", ctypes.c_longlong),
                 ("max_residual", ctypes.c_double), ("lambda_cut", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class OvInfo(ctypes.Structure):
+    _fields_ = [("nconv", ctypes.c_int), ("restarts", ctypes.c_int), ("sign_solves", ctypes.c_longlong),
+                ("ritz_residual", ctypes.c_double), ("max_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -109,6 +117,7 @@ def load(path: str = LIB_PATH):
         "ovl_batch_profile": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "ovl_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ovl_batch_set_tuning": (I, [P, I, I, I]),
+        "ovl_overlap_eigs": (I, [P, I, I, D, D, I, I, I, D, I, ctypes.POINTER(D), P, ctypes.POINTER(OvInfo)]),
         "ovl_sign_krylov_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, D, D, ctypes.POINTER(P),
                                         ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
     }
@@ -307,6 +316,20 @@ class Context:
         self._check(self._lib.ovl_get_deflation(self._h, None, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                 _ptr(R) if m else None, _ptr(L) if m else None, flags))
         return lam[0:2 * m:2] + 1j * lam[1:2 * m:2], R, L
+
+    def overlap_eigs(self, method: int, k: int, mu: float, kappa: float, nev: int, flags: int = 0,
+                     nkrylov: int = 0, tol: float = 1e-10, maxit: int = 200, vecs=None):
+        """The nev eigenvalues of D_ov(mu) nearest 0 (thick-restart Arnoldi, D_ov applied by sign solves
+        of `method` with Krylov size k); returns (eigenvalues as a complex numpy array, nearest 0 first,
+        info dict).  vecs: optional device tensor (nev, 12V) complex128 receiving the eigenvectors."""
+        lam = (ctypes.c_double * (2 * nev))()
+        info = OvInfo()
+        r = self._lib.ovl_overlap_eigs(self._h, int(method), int(k), mu, kappa, int(flags), int(nev), int(nkrylov),
+                                       float(tol), int(maxit), lam, _ptr(vecs) if vecs is not None else None,
+                                       ctypes.byref(info))
+        if r:
+            raise OvlError(r, f"{self._lib.ovl_last_error(self._h).decode()} {info.as_dict()}")
+        return np.array(lam[0::2]) + 1j * np.array(lam[1::2]), info.as_dict()
 
     def profile(self, reset: bool = True):
         """Per-kernel-class totals of the OVL_PROFILE solves since the last reset."""

@@ -5,8 +5,11 @@ Only ``oracle/`` computes here; the inputs come from the seeded generators of
 ``paper_0810_4228_gb300.synth``.  For each case the oracle builds A = gamma5 D_w(mu) (Sec. 1,
 Eq. 1.2), finds its own critical eigenpairs with ARPACK in shift-invert mode (Sec. 3 and Sec. 5:
 the m eigenvalues of smallest |Re lambda| and their left/right eigenvectors), and runs the deflated
-two-sided Lanczos approximation (Sec. 4, Eq. 4.5) at two Krylov sizes; the difference of the two
-is stored as the oracle's own error estimate.
+Arnoldi approximation (Sec. 3, Eq. 3.4) at two Krylov sizes; the difference of the two is stored
+as the oracle's own error estimate.  Arnoldi rather than two-sided Lanczos: both converge to the
+same sgn(A) b, but the oracle's two-sided Lanczos at k of about 1000 carries a rounding floor near
+1e-10 (loss of bi-orthogonality amplifies rounding), while Arnoldi with Gram-Schmidt applied twice
+keeps its basis orthonormal and reaches 1e-12.
 
 Stored per case (a vector of N = 12 V complex entries is too large to keep whole):
   * ``idx``: 4096 sampled component indices (seeded), ``val``: sgn(A) b at those indices;
@@ -21,7 +24,8 @@ Workloads (fields U = exp(i eps H), seeds as named; kappa = 0.2, antiperiodic ti
     the point sources of spin-colour index r at site 0, m = 20 (two of the four lattices of the
     batched workload; the oracle's LU-based eigensolver does not reach 12^4 and 16^3 x 8).
 
-Usage: ``python tests/golden/make_oracle_refs.py [--jobs J]`` (about an hour on 8 cores).
+Usage: ``python tests/golden/make_oracle_refs.py [--jobs J] [--cache DIR]`` (about an hour on 8
+cores; ``--cache`` keeps each field's eigenpairs in DIR and reuses them on a later run).
 """
 from __future__ import annotations
 
@@ -38,7 +42,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 OUT = os.path.join(HERE, "oracle_refs.npz")
 
 KAPPA, EPS, M = 0.2, 1.0, 20
-K_LO, K_HI = 900, 1100
+K_LO, K_HI = 800, 1000
 NSAMPLE, NPROJ, PROJ_SEED = 4096, 8, 9000
 
 # one field + chemical potential per group; its sources share the oracle's eigenpairs
@@ -53,7 +57,8 @@ GROUPS = [
 ]
 
 
-def _run_group(gr):
+def _run_group(args):
+    gr, cache = args
     sys.path.insert(0, ROOT)
     from oracle import deflation as D
     from oracle import krylov as K
@@ -65,7 +70,15 @@ def _run_group(gr):
     U = synth.gauge_field(dims, EPS, gr["seed"])
     A = W.a_operator(U, dims, mu, KAPPA)
     Ah = A.conj().T.tocsr()
-    defl = D.eigenpairs_arpack(A, M)
+    cfile = (os.path.join(cache, f"defl_{'x'.join(map(str, dims))}_s{gr['seed']}_mu{mu}_m{M}.npz")
+             if cache else None)
+    if cfile and os.path.exists(cfile):
+        z = np.load(cfile)
+        defl = K.Deflation(lam=z["lam"], R=z["R"], L=z["L"])
+    else:
+        defl = D.eigenpairs_arpack(A, M)
+        if cfile:
+            np.savez(cfile, lam=defl.lam, R=defl.R, L=defl.L)
     res = max(np.linalg.norm(A @ defl.R - defl.R * defl.lam, axis=0).max(),
               np.linalg.norm(Ah @ defl.L - defl.L * np.conj(defl.lam), axis=0).max())
     t_eig = time.time() - t0
@@ -75,12 +88,12 @@ def _run_group(gr):
     out = {}
     for name, kind, arg in gr["sources"]:
         b = synth.gaussian_source(dims, arg) if kind == "gauss" else synth.point_sources(dims, site=0)[arg]
-        y_lo = K.sign_lanczos2(A.dot, Ah.dot, b, K_LO, defl=defl)
-        y_hi = K.sign_lanczos2(A.dot, Ah.dot, b, K_HI, defl=defl)
+        y_lo = K.sign_arnoldi(A.dot, b, K_LO, defl=defl)
+        y_hi = K.sign_arnoldi(A.dot, b, K_HI, defl=defl)
         nrm = np.linalg.norm(y_hi)
         out[name] = {
             "dims": np.array(dims), "seed": gr["seed"], "eps": EPS, "mu": mu, "kappa": KAPPA, "m": defl.m,
-            "source_kind": kind, "source_arg": arg, "k_lo": K_LO, "k_hi": K_HI,
+            "source_kind": kind, "source_arg": arg, "k_lo": K_LO, "k_hi": K_HI, "method": "arnoldi",
             "idx": idx, "val": y_hi[idx], "norm": nrm, "proj": G.conj() @ y_hi,
             "selfdiff": np.linalg.norm(y_hi - y_lo) / nrm, "eig_residual": res,
             "lam": defl.lam,
@@ -93,13 +106,16 @@ def _run_group(gr):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=3)
+    ap.add_argument("--cache", default="", help="directory for the fields' eigenpairs (reused when present)")
     args = ap.parse_args()
+    if args.cache:
+        os.makedirs(args.cache, exist_ok=True)
     threads = max(1, (os.cpu_count() or 1) // args.jobs)
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = str(threads)
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.jobs) as pool:
-        parts = pool.map(_run_group, GROUPS, chunksize=1)
+        parts = pool.map(_run_group, [(g, args.cache) for g in GROUPS], chunksize=1)
     flat = {}
     for part in parts:
         for name, d in part.items():

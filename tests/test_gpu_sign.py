@@ -214,8 +214,8 @@ def test_arnoldi_delayed_cgs2_matches_classical(ovl, c4, k):
         assert rel(yd, c4["ref"]) < 1e-10
         d = Dm.eigenpairs_dense(c4["A"].toarray(), 20)
         ctx.set_deflation(c4["mu"], KAPPA, d.lam, torch_c128(d.R.T.copy()), torch_c128(d.L.T.copy()))
-        yd, _ = _solve(ovl, ctx, ovl.ARNOLDI, 200, c4["mu"], c4["b"], flags=ovl.MIXED)
-        yc, _ = _solve(ovl, ctx, ovl.ARNOLDI, 200, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.ARNOLDI_CGS2)
+        yd, _ = _solve(ovl, ctx, ovl.ARNOLDI, 300, c4["mu"], c4["b"], flags=ovl.MIXED)
+        yc, _ = _solve(ovl, ctx, ovl.ARNOLDI, 300, c4["mu"], c4["b"], flags=ovl.MIXED | ovl.ARNOLDI_CGS2)
         assert rel(yd, yc) < 1e-12 and rel(yd, c4["ref"]) < 1e-10
 
 
