@@ -339,6 +339,30 @@ typedef struct {
 int ovl_overlap_eigs(ovl_ctx* ctx, int method, int k, double mu, double kappa, int flags, int nev,
                      int nkrylov, double tol, int maxit, double* lambda, void* vecs, ovl_ovinfo* info);
 
+/* out = sgn(A) b (or D_ov b with OVL_OVERLAP) by the Arnoldi approximation restarted every m steps,
+ * at most `cycles` cycles: the basis holds m + 1 vectors instead of k + 1 (Sec. 5 names the N k^2
+ * cost of Arnoldi's basis; the paper gives no restart).  Cycle c continues from the last basis
+ * vector of cycle c - 1; its Hessenberg block joins the accumulated matrix H (block lower
+ * bidiagonal, upper Hessenberg, m cycles x m columns at most), and y gains |b_perp| V_c times the
+ * rows of cycle c of sgn(H) e_1 (the restart of Eiermann and Ernst, SIAM J. Numer. Anal. 44, 2006),
+ * with the installed LR deflation (Sec. 3, Eq. 3.4).  The basis and its Gram-Schmidt sweeps are
+ * double-float (as with OVL_MIXED for OVL_ARNOLDI, delayed CGS2 within a cycle), the inner sign
+ * the resolvent quadrature of H (Roberts' iteration with OVL_INNER_NEWTON or as the fallback).
+ * A lucky breakdown ends the process after that cycle.  info->k_used = columns of H used.
+ * flags: OVL_OVERLAP, OVL_HOST, OVL_NO_GRAPH, OVL_PROFILE, OVL_INNER_NEWTON; OVL_EINVAL for
+ * m < 1, cycles < 1, m x cycles > 8192 or the two-sided Lanczos options. */
+int ovl_sign_arnoldi_restarted(ovl_ctx* ctx, int m, int cycles, double mu, double kappa,
+                               const void* b, void* out, int flags, ovl_info* info);
+
+/* Limits of the bounded device waits of the persistent FP32 pass 1 (the grid barriers of
+ * OVL_MIXED two-sided Lanczos solves on lattices that fit the GPU): a wait gives up after
+ * `polls` polls (0 restores the default, 2e7), sets the solve's timeout flag and every block
+ * leaves, so the call returns OVL_ETIMEOUT and the context stays usable.  unreachable != 0 adds
+ * one arrival to every barrier's target, so every wait runs out: a test of the timeout path
+ * without a fault (use a small `polls`).  Drops the captured solve graph.  The paper has no
+ * counterpart. */
+int ovl_set_wait_limit(ovl_ctx* ctx, long long polls, int unreachable);
+
 /* --- per-kernel profile -------------------------------------------------------------------- */
 
 /* One kernel class of a profiled solve: its name, how many times it was queued, how many

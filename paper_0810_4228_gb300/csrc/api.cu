@@ -128,6 +128,22 @@ int ensure_solve(ovl_ctx* c, int k) {
     return OVL_OK;
 }
 
+// restarted Arnoldi: the accumulated Hessenberg matrix of K columns and its inner-sign workspace
+int ensure_restart(ovl_ctx* c, int K) {
+    if (K <= c->krs_cap) return OVL_OK;
+    drop_graph(c);
+    dfree(&c->Hrs), dfree(&c->cvrs), dfree(&c->innrs);
+    c->krs_cap = 0;
+    const size_t ie = std::max(ovl::inner_work_elems(K, 1), ovl::inner_work_elems(K, 2));
+    int r;
+    if ((r = dalloc(c, &c->Hrs, sizeof(double2) * (size_t)(K + 1) * (K + 1))) ||
+        (r = dalloc(c, &c->cvrs, sizeof(double2) * (size_t)(K + 1))) || (r = dalloc(c, &c->innrs, sizeof(double2) * ie)))
+        return r;
+    c->krs_cap = K;
+    c->innrs_elems = ie;
+    return OVL_OK;
+}
+
 // small dense complex inverse (Gauss-Jordan, partial pivoting) on the host; returns false if singular
 bool host_inverse(std::vector<std::complex<double>>& A, int m) {
     std::vector<int> piv(m);
@@ -326,7 +342,8 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
                 float4* vv[3] = {(float4*)c->v32[0], (float4*)c->v32[1], (float4*)c->v32[2]};
                 float4* ww[3] = {(float4*)c->w32[0], (float4*)c->w32[1], (float4*)c->w32[2]};
                 lr = ovl::launch_pass1_persistent(c->U12, vv, ww, ks, c->alpha, c->beta, c->gamma, c->R32, c->L32,
-                                                  mproj, mu, kappa, k, part, c->bar, g, c->num_sms, st);
+                                                  mproj, mu, kappa, k, part, c->bar, g, c->num_sms, st,
+                                                  c->wait_polls, c->wait_unreachable);
             });
             if (lr) return fail(c, OVL_ECUDA, std::string("persistent pass 1 launch: ") +
                                                    cudaGetErrorString((cudaError_t)lr));
@@ -490,6 +507,79 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
     return OVL_OK;
 }
 
+int enqueue_restarted(ovl_ctx* c, int rs, int cycles, double mu, double kappa, int flags) {
+    cudaStream_t st = c->st;
+    const size_t n = c->n;
+    const Geom& g = c->g;
+    KState* ks = c->ks;
+    double* part = c->partials;
+    unsigned int* cnt = c->counter;
+    const int m = c->m;
+    const int K = rs * cycles, ldH = c->krs_cap + 1;
+    prof(c, KC_SETUP, [&] { ovl::launch_state_init(ks, st); });
+    if (m > 0) {
+        prof(c, KC_DEFLATE, [&] {
+            ovl::launch_multidot(c->L, n, m, c->b64, c->pq, 0, part, n, st);
+            ovl::launch_multidot(c->R, n, m, c->b64, c->pq + m, 0, part, n, st);
+        }, 4);
+    }
+    prof(c, KC_DEFLATE, [&] {
+        ovl::launch_deflate_split(c->b64, c->R, c->L, c->lam, m, c->pq, c->bR, nullptr, c->y64, ks, nullptr, part, cnt,
+                                  n, st);
+    });
+    // double-float basis in V64's slots 0..rs; the two-sided Lanczos coefficient arrays hold the
+    // double-float coefficient copies (see the unrestarted double-float Arnoldi)
+    float4* Vd = reinterpret_cast<float4*>(c->V64);
+    float4* h1d = reinterpret_cast<float4*>(c->alpha);
+    float4* h2d = reinterpret_cast<float4*>(c->beta);
+    float4* cdf = reinterpret_cast<float4*>(c->gamma);
+    double2* x64 = c->s64;
+    // the accumulated matrix is block lower bidiagonal: everything outside the blocks and their
+    // coupling entries is zero
+    CUDA_TRY(c, cudaMemsetAsync(c->Hrs, 0, sizeof(double2) * (size_t)ldH * K, st));
+    prof(c, KC_ANORM, [&] { ovl::launch_adf_start(c->bR, Vd, x64, ks, n, st); });
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+        double2* Hc = c->Hrs + (size_t)cyc * rs * (1 + (size_t)ldH);
+        prof(c, KC_SETUP, [&] { ovl::launch_rs_begin(ks, cyc, st); });
+        for (int j = 0; j < rs; ++j) {
+            float4* uj = Vd + (size_t)j * n;
+            float4* un = Vd + (size_t)(j + 1) * n;
+            prof(c, KC_ADSLASH, [&] { ovl::launch_dslash(c->U64, 0, x64, c->t64, mu, kappa, 1, g, st, ks); });
+            prof(c, KC_ADOT, [&] {
+                ovl::launch_adf_dot2(Vd, n, j + 1, uj, c->t64, c->h1, c->h2, part, n, c->num_sms, ks, st);
+            }, 2);
+            prof(c, KC_ANORM, [&] { ovl::launch_adf_dcgs(Hc, ldH, c->h1, c->h2, h1d, h2d, ks, j, 0, st); });
+            prof(c, KC_AAXPY, [&] {
+                ovl::launch_adf_update2(Vd, n, j, h1d, h2d, uj, un, c->t64, x64, Hc, ldH, c->h1, c->h2, n, ks, st);
+            });
+        }
+        // re-orthogonalise u_rs: finishes the cycle's last column and its coupling entry
+        prof(c, KC_ADOT, [&] {
+            ovl::launch_adf_dot(Vd, n, rs + 1, Vd + (size_t)rs * n, c->h1, h2d, part, n, c->num_sms, ks, st);
+        }, 2);
+        prof(c, KC_ANORM, [&] { ovl::launch_adf_dcgs(Hc, ldH, c->h1, c->h2, h1d, h2d, ks, rs, 2, st); });
+        prof(c, KC_SETUP, [&] { ovl::launch_rs_mid(ks, st); });
+        // inner sign of the accumulated matrix, then this cycle's share of the combination
+        int r = 0;
+        prof(c, KC_INNER, [&] {
+            if (!(flags & OVL_INNER_NEWTON)) {
+                const int q = ovl::launch_inner_quadrature_hess(c->Hrs, ldH, ks, c->cvrs, c->innrs, c->innrs_elems,
+                                                                c->krs_cap, part, cnt, st);
+                r = q ? q
+                      : ovl::launch_inner_newton(nullptr, nullptr, nullptr, c->Hrs, ldH, 0, ks, c->cvrs, c->innrs,
+                                                 c->innrs_elems, c->krs_cap, c->num_sms, st, 1);
+            } else {
+                r = ovl::launch_inner_newton(nullptr, nullptr, nullptr, c->Hrs, ldH, 0, ks, c->cvrs, c->innrs,
+                                             c->innrs_elems, c->krs_cap, c->num_sms, st);
+            }
+        }, (flags & OVL_INNER_NEWTON) ? 2 : 15);
+        if (r) return fail(c, OVL_ECUDA, "inner sign launch failed");
+        prof(c, KC_COMBINE, [&] { ovl::launch_rs_combine(Vd, n, c->cvrs, cyc * rs, cdf, ks, rs, c->y64, n, st); }, 2);
+        prof(c, KC_ANORM, [&] { ovl::launch_rs_restart(Vd, n, rs, h1d, x64, ks, n, cyc + 1 == cycles, st); });
+    }
+    return OVL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -535,6 +625,7 @@ int ovl_destroy(ovl_ctx* c) {
         dfree(&c->stage_out);
     dfree(&c->nat_a), dfree(&c->nat_b), dfree(&c->pq);
     dfree(&c->gwork), dfree(&c->tadj);
+    dfree(&c->Hrs), dfree(&c->cvrs), dfree(&c->innrs);
     for (int i = 0; i < 3; ++i) dfree(&c->W64[i]), dfree(&c->R64[i]), dfree(&c->v32[i]), dfree(&c->w32[i]);
     delete c;
     return OVL_OK;
@@ -710,18 +801,16 @@ int ovl_get_deflation(ovl_ctx* c, int* m_out, double* lambda, void* R, void* L, 
     return OVL_OK;
 }
 
-int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, const void* b, void* out, int flags,
-                    ovl_info* info) {
-    if (!c || !b || !out) return fail(c, OVL_EINVAL, "null argument");
-    if (method != OVL_ARNOLDI && method != OVL_LANCZOS2) return fail(c, OVL_EINVAL, "unknown method");
-    if (k < 1 || k > 8192) return fail(c, OVL_EINVAL, "k out of range [1, 8192]");
-    if (!c->have_gauge) return fail(c, OVL_ESTATE, "gauge field not set");
-    if (b == out) return fail(c, OVL_EINVAL, "b and out must not overlap");
-    if (c->m > 0 && (mu != c->dmu || kappa != c->dkappa))
-        return fail(c, OVL_EINVAL, "mu/kappa differ from those of the installed deflation");
-    if (method == OVL_ARNOLDI && (flags & OVL_TWO_PASS))
-        return fail(c, OVL_EINVAL, "two-pass is defined for two-sided Lanczos only");
-    int r = ensure_solve(c, k);
+}  // extern "C"
+
+namespace {
+
+// the common body of ovl_sign_krylov (rs = 0) and ovl_sign_arnoldi_restarted (rs = cycle length,
+// k = rs x cycles): pack, queue (or replay the captured graph), unpack, read the status
+int sign_solve(ovl_ctx* c, int method, int k, int rs, double mu, double kappa, const void* b, void* out, int flags,
+               ovl_info* info) {
+    int r = rs > 0 ? ensure_solve(c, rs) : ensure_solve(c, k);
+    if (!r && rs > 0) r = ensure_restart(c, k);
     if (r) return r;
     const size_t cb = c->n * sizeof(double2);
     const double2* bin = (const double2*)b;
@@ -738,8 +827,8 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
     c->prof_on = (flags & OVL_PROFILE) != 0;
     if (!(flags & (OVL_NO_GRAPH | OVL_PROFILE))) {
         GraphEntry& ge = c->graph;
-        if (!(ge.valid && ge.method == method && ge.k == k && ge.flags == gflags && ge.m == c->m && ge.mu == mu &&
-              ge.kappa == kappa)) {
+        if (!(ge.valid && ge.method == method && ge.k == k && ge.rs == rs && ge.flags == gflags && ge.m == c->m &&
+              ge.mu == mu && ge.kappa == kappa)) {
             drop_graph(c);
             cudaGraph_t graph = nullptr;
             // capture on a private stream (the caller's may be the legacy default stream, which
@@ -748,14 +837,16 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
             cudaStream_t user_st = c->st;
             if (c->cap_st && cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 c->st = c->cap_st;
-                const int er = enqueue_solve(c, method, k, mu, kappa, gflags);
+                const int er = rs > 0 ? enqueue_restarted(c, rs, k / rs, mu, kappa, gflags)
+                                      : enqueue_solve(c, method, k, mu, kappa, gflags);
                 const cudaError_t ec = cudaStreamEndCapture(c->cap_st, &graph);
                 c->st = user_st;
                 if (er == OVL_OK && ec == cudaSuccess && graph) {
                     cudaGraphExec_t exec = nullptr;
                     if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
                         ge.valid = true;
-                        ge.method = method, ge.k = k, ge.flags = gflags, ge.m = c->m, ge.mu = mu, ge.kappa = kappa;
+                        ge.method = method, ge.k = k, ge.rs = rs, ge.flags = gflags, ge.m = c->m, ge.mu = mu,
+                        ge.kappa = kappa;
                         ge.exec = exec;
                     }
                 }
@@ -769,7 +860,7 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
         }
     }
     if (!ran) {
-        r = enqueue_solve(c, method, k, mu, kappa, gflags);
+        r = rs > 0 ? enqueue_restarted(c, rs, k / rs, mu, kappa, gflags) : enqueue_solve(c, method, k, mu, kappa, gflags);
         c->prof_on = false;
         if (r) return r;
     }
@@ -798,6 +889,38 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
     return OVL_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, const void* b, void* out, int flags,
+                    ovl_info* info) {
+    if (!c || !b || !out) return fail(c, OVL_EINVAL, "null argument");
+    if (method != OVL_ARNOLDI && method != OVL_LANCZOS2) return fail(c, OVL_EINVAL, "unknown method");
+    if (k < 1 || k > 8192) return fail(c, OVL_EINVAL, "k out of range [1, 8192]");
+    if (!c->have_gauge) return fail(c, OVL_ESTATE, "gauge field not set");
+    if (b == out) return fail(c, OVL_EINVAL, "b and out must not overlap");
+    if (c->m > 0 && (mu != c->dmu || kappa != c->dkappa))
+        return fail(c, OVL_EINVAL, "mu/kappa differ from those of the installed deflation");
+    if (method == OVL_ARNOLDI && (flags & OVL_TWO_PASS))
+        return fail(c, OVL_EINVAL, "two-pass is defined for two-sided Lanczos only");
+    return sign_solve(c, method, k, 0, mu, kappa, b, out, flags, info);
+}
+
+int ovl_sign_arnoldi_restarted(ovl_ctx* c, int m, int cycles, double mu, double kappa, const void* b, void* out,
+                               int flags, ovl_info* info) {
+    if (!c || !b || !out) return fail(c, OVL_EINVAL, "null argument");
+    if (m < 1 || cycles < 1 || (long long)m * cycles > 8192)
+        return fail(c, OVL_EINVAL, "m >= 1, cycles >= 1 and m x cycles <= 8192 required");
+    if (!c->have_gauge) return fail(c, OVL_ESTATE, "gauge field not set");
+    if (b == out) return fail(c, OVL_EINVAL, "b and out must not overlap");
+    if (c->m > 0 && (mu != c->dmu || kappa != c->dkappa))
+        return fail(c, OVL_EINVAL, "mu/kappa differ from those of the installed deflation");
+    if (flags & (OVL_TWO_PASS | OVL_REPROJ | OVL_STEPWISE))
+        return fail(c, OVL_EINVAL, "flags: two-pass, re-projection and stepwise are two-sided Lanczos options");
+    return sign_solve(c, OVL_ARNOLDI, m * cycles, m, mu, kappa, b, out, flags | OVL_MIXED, info);
+}
+
 int ovl_profile_get(ovl_ctx* c, ovl_kstat* out, int max, int* count) {
     if (!c || !count || (max > 0 && !out)) return fail(c, OVL_EINVAL, "bad argument");
     int q = 0;
@@ -813,6 +936,14 @@ int ovl_profile_get(ovl_ctx* c, ovl_kstat* out, int max, int* count) {
         ++q;
     }
     *count = q;
+    return OVL_OK;
+}
+
+int ovl_set_wait_limit(ovl_ctx* c, long long polls, int unreachable) {
+    if (!c || polls < 0) return fail(c, OVL_EINVAL, "bad argument");
+    c->wait_polls = polls;
+    c->wait_unreachable = unreachable ? 1 : 0;
+    drop_graph(c);  // a captured solve holds the old limits
     return OVL_OK;
 }
 

@@ -413,7 +413,9 @@ __global__ void k_adf_dot2_reduce(const double2* __restrict__ part, int nblk, in
 // (2): one block.  h1 = (c, rho^2) and h2 = (d, e) of step j (h2 unused when fin).  Finishes
 // column j-1 of H (j >= 1), decides a lucky breakdown (nu <= bdtol |H|), and for the update writes
 // cdf = c, qdf = d / nu (double-float), ks->red[1] = (1 / nu, nu), ks->red[2] = r.  fin = 1 after
-// the last step (j = k): only column k-1 is finished and the solve is marked done.
+// the last step (j = k): only column k-1 is finished and the solve is marked done.  fin = 2 at the
+// end of a restart cycle: column k-1 is finished, cdf = c and ks->red[1] are written for the next
+// cycle's start vector (u_k - V c) / nu, and the solve goes on unless the Krylov space is invariant.
 __global__ void __launch_bounds__(1024) k_adf_dcgs(double2* __restrict__ H, int ldH, const double2* __restrict__ h1,
                                                    const double2* __restrict__ h2, float4* __restrict__ cdf,
                                                    float4* __restrict__ qdf, KState* ks, int j, int fin,
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(1024) k_adf_dcgs(double2* __restrict__ H, int 
             const double colnorm = sqrt(acc[3] + nu * nu);
             if (colnorm > ks->anorm) ks->anorm = colnorm;
             ks->kused = j;
-            if (fin || nu <= bdtol * fmax(ks->anorm, 1e-300)) stop = 1;  // last column, or K_j invariant
+            if (fin == 1 || nu <= bdtol * fmax(ks->anorm, 1e-300)) stop = 1;  // last column, or K_j invariant
         } else if (!(nu > 0.0)) {
             stop = 1;  // zero start vector (cannot happen after the deflation split's check)
         }
@@ -456,9 +458,10 @@ __global__ void __launch_bounds__(1024) k_adf_dcgs(double2* __restrict__ H, int 
         } else {
             const double inu = 1.0 / nu;
             ks->red[1] = make_double2(inu, nu);
-            // r = (e - c^dag d) / nu^2
-            const double2 e = h2[j];
-            ks->red[2] = make_double2((e.x - acc[1]) * inu * inu, (e.y - acc[2]) * inu * inu);
+            if (!fin) {  // r = (e - c^dag d) / nu^2
+                const double2 e = h2[j];
+                ks->red[2] = make_double2((e.x - acc[1]) * inu * inu, (e.y - acc[2]) * inu * inu);
+            }
         }
         s_nu = nu;
         s_stop = stop;
@@ -471,8 +474,10 @@ __global__ void __launch_bounds__(1024) k_adf_dcgs(double2* __restrict__ H, int 
         H[l + (size_t)(j - 1) * ldH] = make_double2(hv.x + c.x, hv.y + c.y);
         if (!s_stop) {
             cdf[l] = to_f4(d2df(c));
-            const double2 d = h2[l];
-            qdf[l] = to_f4(d2df(make_double2(d.x * inu, d.y * inu)));
+            if (!fin) {
+                const double2 d = h2[l];
+                qdf[l] = to_f4(d2df(make_double2(d.x * inu, d.y * inu)));
+            }
         }
     }
 }
@@ -558,6 +563,95 @@ __global__ void __launch_bounds__(AD_T) k_adf_update2(const float4* __restrict__
             x64[e] = df2d(un);
         }
         __syncthreads();  // red1, red2 are reused by the next tile
+    }
+}
+
+// ======================================================== restarted Arnoldi ==
+// Arnoldi restarted every m steps (Eiermann and Ernst, SIAM J. Numer. Anal. 44 (2006)): cycle c
+// runs m delayed-CGS2 steps on the double-float basis slots 0..m from the start vector in slot 0,
+// writing its Hessenberg block into the accumulated matrix at rows and columns c m ..; the block's
+// subdiagonal entry H[m, m-1] is the coupling to the next cycle.  After the cycle the inner sign of
+// the accumulated K x K matrix gives c_K = |b_perp| sgn(H_K) e_1, of which the rows of cycle c
+// multiply its basis: y += V_c c_K[c m ..].  The next cycle starts from v_m = (u_m - V c) / nu.
+// Cycle bookkeeping in the state record: red[4].x = K (columns finished so far), red[5] = (steps of
+// this cycle, stopped); a lucky breakdown stops the process after that cycle's combination.
+__global__ void k_rs_begin(KState* ks, int cyc) {
+    if (ks->status) return;
+    if (cyc == 0) {  // a source the deflation split left empty (done already) stops the process
+        ks->red[4] = make_double2(0.0, 0.0);
+        ks->red[5] = make_double2(0.0, ks->done ? 1.0 : 0.0);
+    }
+    ks->done = ks->red[5].y != 0.0 ? 1 : 0;
+    ks->kused = 0;
+}
+
+// after the cycle's last Gram-Schmidt: K += steps of this cycle; kused = K for the inner sign
+__global__ void k_rs_mid(KState* ks) {
+    if (ks->status) return;
+    const int local = ks->red[5].y != 0.0 ? 0 : ks->kused;
+    const int K = (int)ks->red[4].x + local;
+    ks->red[4] = make_double2((double)K, 0.0);
+    ks->red[5].x = (double)local;
+    ks->kused = K;
+}
+
+// double-float combination coefficients of this cycle: cdf[l] = c[off + l], l < steps
+__global__ void k_rs_coef(const double2* __restrict__ c, float4* __restrict__ cdf, const KState* ks, int off) {
+    if (ks->status) return;
+    const int local = (int)ks->red[5].x;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < local; l += gridDim.x * blockDim.x)
+        cdf[l] = to_f4(d2df(c[off + l]));
+}
+
+// y += sum_{l < steps} cdf_l V_l (y FP64)
+__global__ void __launch_bounds__(AD_T) k_rs_combine(const float4* __restrict__ V, size_t ld,
+                                                     const float4* __restrict__ cdf, const KState* ks,
+                                                     double2* __restrict__ y, size_t n) {
+    __shared__ float4 red[AD_W][32];
+    if (ks->status) return;
+    const int local = (int)ks->red[5].x;
+    if (local <= 0) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t e = (size_t)blockIdx.x * 32 + lane;
+    const bool in = e < n;
+    cx<df> s;
+    adf_lincomb(V, ld, local, cdf, e, in, wid, lane, red, s);
+    if (wid == 0 && in) {
+        const double2 a = y[e], d = df2d(s);
+        y[e] = make_double2(a.x + d.x, a.y + d.y);
+    }
+}
+
+// the next cycle's start vector v_0 = (u_m - V_{<m} c) / nu into slot 0 (each element is read and
+// written by its own block) and its FP64 value into x64; after the last cycle, a lucky breakdown
+// or an earlier stop, the process is marked stopped and done instead
+__global__ void __launch_bounds__(AD_T) k_rs_restart(float4* __restrict__ V, size_t ld, int m,
+                                                     const float4* __restrict__ cdf, double2* __restrict__ x64,
+                                                     KState* ks, size_t n, int last) {
+    __shared__ float4 red[AD_W][32];
+    if (ks->status) return;
+    if (ks->done || ks->red[5].y != 0.0 || last) {  // the same decision in every block
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ks->red[5].y = 1.0;
+            ks->done = 1;
+        }
+        return;
+    }
+    const df inu(ks->red[1].x);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t ntile = (n + 31) / 32;
+    for (size_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const size_t e = tile * 32 + lane;
+        const bool in = e < n;
+        cx<df> s;
+        adf_lincomb(V, ld, m, cdf, e, in, wid, lane, red, s);
+        if (wid == 0 && in) {
+            const cx<df> u = from_f4(V[(size_t)m * ld + e]);
+            const cx<df> v = mk((u.r - s.r) * inu, (u.i - s.i) * inu);
+            V[e] = to_f4(v);
+            x64[e] = df2d(v);
+        }
+        __syncthreads();  // red is reused by the next tile
     }
 }
 
@@ -653,6 +747,18 @@ void launch_adf_update2(const float4* V, size_t ld, int j, const float4* cdf, co
     unsigned grid = adf_update_grid(n);
     if (grid < (unsigned)j + 1) grid = (unsigned)j + 1;  // blocks 0..j each write one row of column j
     k_adf_update2<<<grid, AD_T, 0, st>>>(V, ld, j, cdf, qdf, uj, unext, w, x64, H, ldH, h1, h2, n, ks);
+}
+
+void launch_rs_begin(KState* ks, int cyc, cudaStream_t st) { k_rs_begin<<<1, 1, 0, st>>>(ks, cyc); }
+void launch_rs_mid(KState* ks, cudaStream_t st) { k_rs_mid<<<1, 1, 0, st>>>(ks); }
+void launch_rs_combine(const float4* V, size_t ld, const double2* c, int off, float4* cdf, const KState* ks, int m,
+                       double2* y, size_t n, cudaStream_t st) {
+    k_rs_coef<<<(m + 255) / 256 > 0 ? (m + 255) / 256 : 1, 256, 0, st>>>(c, cdf, ks, off);
+    k_rs_combine<<<(unsigned)((n + 31) / 32), AD_T, 0, st>>>(V, ld, cdf, ks, y, n);
+}
+void launch_rs_restart(float4* V, size_t ld, int m, const float4* cdf, double2* x64, KState* ks, size_t n, int last,
+                       cudaStream_t st) {
+    k_rs_restart<<<adf_update_grid(n), AD_T, 0, st>>>(V, ld, m, cdf, x64, ks, n, last);
 }
 
 void launch_adf_combine(const float4* V, size_t ld, const double2* c, float4* cdf, const KState* ks, int kmax,

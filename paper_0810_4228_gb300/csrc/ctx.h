@@ -27,7 +27,7 @@ struct ProfRec {
 
 struct GraphEntry {
     bool valid = false;
-    int method = -1, k = -1, flags = 0, m = -1;
+    int method = -1, k = -1, flags = 0, m = -1, rs = 0;
     double mu = 0, kappa = 0;
     cudaGraphExec_t exec = nullptr;
 };
@@ -84,6 +84,18 @@ struct ovl_ctx {
 
     ovl_priv::GraphEntry graph;
 
+    // bounded device waits of the persistent pass 1 (ovl_set_wait_limit; 0 = the default limit)
+    long long wait_polls = 0;
+    int wait_unreachable = 0;
+
+    // restarted Arnoldi: the accumulated Hessenberg matrix ((krs + 1) x krs), its combination
+    // coefficients and inner-sign workspace (the basis is V64's first m + 1 slots)
+    int krs_cap = 0;
+    double2* Hrs = nullptr;
+    double2* cvrs = nullptr;
+    double2* innrs = nullptr;
+    size_t innrs_elems = 0;
+
     // gradient of the Krylov sign (grad_krylov.cu): basis checkpoints and adjoint vectors, and the
     // scratch of the small-problem adjoint
     void* gwork = nullptr;
@@ -110,6 +122,9 @@ void drop_graph(ovl_ctx* c);
 bool host_inverse(std::vector<std::complex<double>>& A, int m);
 // queue one solve of the C ABI's sign_krylov (b already packed into c->b64)
 int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int flags);
+// queue one restarted Arnoldi solve: k / rs cycles of rs steps (b already packed into c->b64)
+int enqueue_restarted(ovl_ctx* c, int rs, int cycles, double mu, double kappa, int flags);
+int ensure_restart(ovl_ctx* c, int K);
 // install m eigenpairs already in the device layout (R, L: m device vectors each, lam: host)
 int install_deflation(ovl_ctx* c, double mu, double kappa, int m, const double* lambda, const double2* Rdev,
                       const double2* Ldev);

@@ -134,6 +134,14 @@ void launch_adf_dcgs(double2* H, int ldH, const double2* h1, const double2* h2, 
 void launch_adf_update2(const float4* V, size_t ld, int j, const float4* cdf, const float4* qdf, float4* uj,
                         float4* unext, const double2* w, double2* x64, double2* H, int ldH, const double2* h1,
                         const double2* h2, size_t n, KState* ks, cudaStream_t st);
+// restarted Arnoldi (csrc/arnoldi_df.cu): cycle bookkeeping, the cycle's combination y += V c[off ..] and the next
+// cycle's start vector
+void launch_rs_begin(KState* ks, int cyc, cudaStream_t st);
+void launch_rs_mid(KState* ks, cudaStream_t st);
+void launch_rs_combine(const float4* V, size_t ld, const double2* c, int off, float4* cdf, const KState* ks, int m,
+                       double2* y, size_t n, cudaStream_t st);
+void launch_rs_restart(float4* V, size_t ld, int m, const float4* cdf, double2* x64, KState* ks, size_t n, int last,
+                       cudaStream_t st);
 void launch_adf_combine(const float4* V, size_t ld, const double2* c, float4* cdf, const KState* ks, int kmax,
                         double2* y, size_t n, cudaStream_t st);
 
@@ -142,7 +150,7 @@ bool persistent_ok(const Geom& g, int num_sms);
 int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const w[3], KState* ks, double2* alpha,
                             double2* beta, double2* gamma, const float2* R32, const float2* L32, int m, double mu,
                             double kappa, int k, double* partials, unsigned int* bar, const Geom& g, int num_sms,
-                            cudaStream_t st);
+                            cudaStream_t st, long long spin = 0, int unreachable = 0);
 // coef_work: 4 (kmax + 1) double2 of scratch for the per-step regeneration coefficients.
 // Udf non-null: double-float arithmetic (links Udf; v[] are converted to double-float in place, so
 // v[0] must hold the FP64 start vector and all three are left in double-float); else FP64 (links U64).

@@ -178,6 +178,8 @@ struct P1Args {
     int k;
     int ntiles;
     int tpb;
+    long long spin;          // polls before a barrier wait gives up (sets ks->timeout)
+    unsigned int unreach;    // added to every barrier target: 1 makes every wait run out (timeout tests)
 };
 
 // pass-1 scalars shared by the block (written by warp 0)
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(32 * PW1) k_pass1_persistent(P1Args a) {
             // p_j at 4 + 2j, q_j at 4 + 2m + 2j: reduce into the block's slots 4 + 4j.. and move
             block_reduce_ff<4, PW1>(pr, redf, a.partA + (size_t)blockIdx.x * NA + 4 + 4 * j);
         }
-        grid_barrier_mono(a.bar, (unsigned)G * (++nbar), err, 1, PSPIN);
+        grid_barrier_mono(a.bar, (unsigned)G * (++nbar) + a.unreach, err, 1, a.spin);
         if (*(volatile int*)err) return;
         // ---- scalars (warp 0): alpha_i, the recurrence coefficients of phase C
         if (wid == 0) {
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(32 * PW1) k_pass1_persistent(P1Args a) {
             }
         }
         block_reduce_ff<4, PW1>(pc, redf, a.partC + (size_t)blockIdx.x * 4);
-        grid_barrier_mono(a.bar, (unsigned)G * (++nbar), err, 1, PSPIN);
+        grid_barrier_mono(a.bar, (unsigned)G * (++nbar) + a.unreach, err, 1, a.spin);
         if (*(volatile int*)err) return;
         if (wid == 0) {
             warp_sum_partials(a.partC, 4, 4, G, oc);
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(32 * PW2) k_pass2_persistent(P2Args<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R>* dirpart = reinterpret_cast<cx<R>*>(smraw);  // [PW2][PT][12]
     cx<R>* st = dirpart + PW2 * PT * 12;               // [tpb][3][PT][12]
-    if (a.ks->status) return;
+    if (a.ks->status || a.ks->timeout) return;  // (pass 1 gave up: the same decision in every block)
     const int kused = a.ks->kused;
     const Geom g = a.g;
     const int G = gridDim.x;
@@ -579,9 +581,11 @@ bool persistent_ok(const Geom& g, int num_sms) {
 int launch_pass1_persistent(const float4* U12, float4* const v[3], float4* const w[3], KState* ks, double2* alpha,
                             double2* beta, double2* gamma, const float2* R32, const float2* L32, int m, double mu,
                             double kappa, int k, double* partials, unsigned int* bar, const Geom& g, int num_sms,
-                            cudaStream_t st) {
+                            cudaStream_t st, long long spin, int unreachable) {
     if (m > PMAX_M) return -1;
     P1Args a;
+    a.spin = spin > 0 ? spin : PSPIN;
+    a.unreach = unreachable ? 1u : 0u;
     a.U = U12;
     for (int q = 0; q < 3; ++q) a.v[q] = v[q], a.w[q] = w[q];
     a.ks = ks;

@@ -38,7 +38,8 @@ EXPORTS = ["ovl_create", "ovl_destroy", "ovl_last_error", "ovl_set_stream", "ovl
            "ovl_profile_get", "ovl_profile_reset", "ovl_dw_grad", "ovl_sign_grad", "ovl_batch_create",
            "ovl_batch_destroy", "ovl_batch_last_error", "ovl_batch_solve", "ovl_batch_profile", "ovl_batch_tuning",
            "ovl_batch_set_tuning",
-           "ovl_sign_krylov_batched", "ovl_overlap_eigs"]
+           "ovl_sign_krylov_batched", "ovl_overlap_eigs", "ovl_sign_arnoldi_restarted",
+           "ovl_set_wait_limit"]
 
 
 class OvlError(RuntimeError):
@@ -117,6 +118,8 @@ def load(path: str = LIB_PATH):
         "ovl_batch_profile": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I), I]),
         "ovl_batch_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ovl_batch_set_tuning": (I, [P, I, I, I]),
+        "ovl_set_wait_limit": (I, [P, ctypes.c_longlong, I]),
+        "ovl_sign_arnoldi_restarted": (I, [P, I, I, D, D, P, P, I, ctypes.POINTER(Info)]),
         "ovl_overlap_eigs": (I, [P, I, I, D, D, I, I, I, D, I, ctypes.POINTER(D), P, ctypes.POINTER(OvInfo)]),
         "ovl_sign_krylov_batched": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), I, D, D, ctypes.POINTER(P),
                                         ctypes.POINTER(P), I, ctypes.POINTER(Info)]),
@@ -316,6 +319,27 @@ class Context:
         self._check(self._lib.ovl_get_deflation(self._h, None, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                 _ptr(R) if m else None, _ptr(L) if m else None, flags))
         return lam[0:2 * m:2] + 1j * lam[1:2 * m:2], R, L
+
+    def set_wait_limit(self, polls: int = 0, unreachable: bool = False):
+        """Bounded device waits of the persistent pass 1 give up after `polls` polls (0: default);
+        unreachable=True makes every such wait run out (tests of the OVL_ETIMEOUT path)."""
+        self._check(self._lib.ovl_set_wait_limit(self._h, int(polls), 1 if unreachable else 0))
+
+    def sign_arnoldi_restarted(self, m: int, cycles: int, mu: float, kappa: float, b, out=None, flags: int = 0):
+        """out = sgn(A) b (D_ov b with OVERLAP) by Arnoldi restarted every m steps, at most `cycles`
+        cycles (a basis of m + 1 double-float vectors).  Returns (out, info dict)."""
+        import torch
+        if out is None:
+            out = (np.empty_like(b) if isinstance(b, np.ndarray) else torch.empty_like(b))
+        if _is_host(b):
+            flags |= HOST
+        info = Info()
+        r = self._lib.ovl_sign_arnoldi_restarted(self._h, int(m), int(cycles), mu, kappa, _ptr(b), _ptr(out),
+                                                 int(flags), ctypes.byref(info))
+        self._check(r)
+        d = info.as_dict()
+        d["status"] = r
+        return out, d
 
     def overlap_eigs(self, method: int, k: int, mu: float, kappa: float, nev: int, flags: int = 0,
                      nkrylov: int = 0, tol: float = 1e-10, maxit: int = 200, vecs=None):
