@@ -189,7 +189,8 @@ int ovl_apply_pair_noalloc_blocks(const int dims[4], int* blocks, int* max_block
  *   grad_U[x][nu] = g_{U_{x,nu}}     (canonical complex128 [V][4][3][3], device; may be NULL)
  *   *grad_mu      = dl/dmu = Re <g, (dA/dmu) x>, dA/dmu = -kappa gamma5 (e^mu T_4^+ - e^-mu T_4^-)
  * (host double; may be NULL).  x, g: canonical complex128 device vectors.  grad_x = A^dag g is
- * ovl_apply_Dw with OVL_DAGGER.  Uses the installed gauge field U. */
+ * ovl_apply_Dw with OVL_DAGGER.  Uses the installed gauge field U.  flags: 0 (FP64) or OVL_F32
+ * (the link force in FP32 arithmetic, relative error about 1e-7; d/dmu stays FP64). */
 int ovl_dw_grad(ovl_ctx* ctx, double mu, double kappa, const void* x, const void* g, void* grad_U,
                 double* grad_mu, int flags);
 
@@ -252,8 +253,12 @@ int ovl_sign_krylov_batched(ovl_ctx* const* ctxs, int nctx, const int* nrhs, int
  * b, g: canonical complex128 device vectors.  The two Krylov bases (k + 1 vectors each) and
  * k more vectors stay in device memory for the call.  Errors as ovl_sign_krylov;
  * OVL_EBREAKDOWN also if g^dag b = 0 (the process cannot start); OVL_ENOCONV if the
- * quadrature of the k x k part does not settle.  flags: 0 (reserved).  info: as
- * ovl_sign_krylov (may be NULL).  Synchronises the context's stream. */
+ * quadrature of the k x k part does not settle.  flags: 0 = FP64 process (the N k^2 combination
+ * Z = W conj(M) in double-float arithmetic, about 48 bits, on the FP32 pipe); OVL_MIXED = the
+ * two-sided Lanczos process in FP32 with 12-real links (FP64 reductions, coefficients and the
+ * k x k quadrature), the combination and the link force in FP32: relative error about 1e-6
+ * against the FP64 path.  info: as ovl_sign_krylov (may be NULL).  Synchronises the context's
+ * stream. */
 int ovl_sign_grad(ovl_ctx* ctx, int k, double mu, double kappa, const void* b, const void* g, void* y,
                   void* grad_U, double* grad_mu, void* grad_b, int flags, ovl_info* info);
 

@@ -618,7 +618,7 @@ int ovl_destroy(ovl_ctx* c) {
     free_solve(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
-    dfree(&c->U64), dfree(&c->U12), dfree(&c->U18), dfree(&c->Udf);
+    dfree(&c->U64), dfree(&c->U12), dfree(&c->U18), dfree(&c->Udf), dfree(&c->nbr);
     dfree(&c->R), dfree(&c->L), dfree(&c->lam), dfree(&c->R32), dfree(&c->L32);
     dfree(&c->b64), dfree(&c->y64), dfree(&c->bR), dfree(&c->bL), dfree(&c->t64), dfree(&c->s64);
     dfree(&c->t32), dfree(&c->s32), dfree(&c->ks), dfree(&c->counter), dfree(&c->bar), dfree(&c->stage_in),
@@ -650,7 +650,8 @@ int ovl_set_gauge(ovl_ctx* c, const void* U, int flags) {
     const size_t V = c->g.V;
     int r;
     if ((r = dalloc(c, &c->U64, V * 36 * sizeof(double2))) || (r = dalloc(c, &c->U12, V * 12 * sizeof(float4))) ||
-        (r = dalloc(c, &c->U18, V * 36 * sizeof(float2))) || (r = dalloc(c, &c->Udf, V * 36 * sizeof(float4))))
+        (r = dalloc(c, &c->U18, V * 36 * sizeof(float2))) || (r = dalloc(c, &c->Udf, V * 36 * sizeof(float4))) ||
+        (r = dalloc(c, &c->nbr, V * 8 * sizeof(int))))
         return r;
     const double2* src = (const double2*)U;
     double2* tmp = nullptr;
@@ -660,6 +661,7 @@ int ovl_set_gauge(ovl_ctx* c, const void* U, int flags) {
         src = tmp;
     }
     ovl::launch_pack_gauge(src, c->U64, c->U12, c->U18, c->Udf, c->g, c->st);
+    ovl::launch_build_nbr(c->nbr, c->g, c->st);
     CUDA_TRY(c, cudaGetLastError());
     if (tmp) {
         CUDA_TRY(c, cudaStreamSynchronize(c->st));

@@ -35,6 +35,7 @@ struct BSeq {
     const void* U;            // pass-1 links: FP32-12 (float4) or FP64 (double2)
     const double2* U64;       // FP64 links (regeneration)
     const void* Udf;          // double-float links (regeneration of mixed solves)
+    const int* nbr;           // [8][V] neighbour table of the lattice (regeneration)
     void* v[3];               // pass-1 ring (FP32 float4 pairs or FP64); unused with a stored basis
     void* w[3];
     void* t;
@@ -208,7 +209,11 @@ __device__ __forceinline__ void* vslot(const BSeq& q, int j, bool wvec) {
     return wvec ? q.w[j % 3] : q.v[j % 3];
 }
 
-// t = sv A v~_i, s = sw A^dag w~_i at every site of every running sequence; alpha_i = w_i^dag t
+// t = sv A v~_i, s = sw A^dag w~_i at every site of every running sequence; alpha_i = w_i^dag t.
+// The grid's y index splits the two stencils (y = 0: t and the alpha partials; y = 1: s), so a
+// thread carries one accumulator spinor instead of two (fewer registers: more warps per SM).
+// The last step's s (i = klast) is not used, so the y = 1 blocks may skip it once the sequence
+// is marked done.
 template <int LF, class R, int SH>
 __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
                                                int klast, HopCoef<R> hv, HopCoef<R> hw) {
@@ -220,30 +225,44 @@ __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restri
     constexpr int BT = SHAPE_SITES[SH];
     const int local = blockIdx.x - q.blk0[SH];
     const int site = local * BT + threadIdx.x;
-    const cx<R> sv = mk((R)ks->sv.x, (R)ks->sv.y), sw = mk((R)ks->sw.x, (R)ks->sw.y);
     const VT* vi = (const VT*)vslot<R>(q, i, false);
     const VT* wi = (const VT*)vslot<R>(q, i, true);
+    if (blockIdx.y == 1) {  // s = sw A^dag w~
+        if (site < q.g.V) {
+            const cx<R> sw = mk((R)ks->sw.x, (R)ks->sw.y);
+            const VT* const xs[1] = {wi};
+            const HopCoef<R> hcs[1] = {hw};
+            Spinor<R> acc[1], self;
+            apply_site<LF, R, 1>(q.g, site, q.U, xs, acc, hcs);
+            load_spinor(wi, q.g.V, site, self);
+            finish_site(acc[0], self, true);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[0].s[sp][c] = sw * acc[0].s[sp][c];
+            store_spinor((VT*)q.s, q.g.V, site, acc[0]);
+        }
+        return;
+    }
     typename AccOf<R>::T a[3];
     if (site < q.g.V) {
-        const VT* const xs[2] = {vi, wi};
-        const HopCoef<R> hcs[2] = {hv, hw};
-        Spinor<R> acc[2], self[2];
-        apply_site<LF, R, 2>(q.g, site, q.U, xs, acc, hcs);
-        load_spinor(vi, q.g.V, site, self[0]);
-        load_spinor(wi, q.g.V, site, self[1]);
-        finish_site(acc[0], self[0], true);
-        finish_site(acc[1], self[1], true);
+        const cx<R> sv = mk((R)ks->sv.x, (R)ks->sv.y);
+        const VT* const xs[1] = {vi};
+        const HopCoef<R> hcs[1] = {hv};
+        Spinor<R> acc[1], self;
+        apply_site<LF, R, 1>(q.g, site, q.U, xs, acc, hcs);
+        load_spinor(vi, q.g.V, site, self);
+        finish_site(acc[0], self, true);
+        load_spinor(wi, q.g.V, site, self);  // w~ at the own site: alpha = conj(sw) w~^dag t
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 acc[0].s[sp][c] = sv * acc[0].s[sp][c];
-                acc[1].s[sp][c] = sw * acc[1].s[sp][c];
-                acc_cdot(a, self[1].s[sp][c], acc[0].s[sp][c]);
+                acc_cdot(a, self.s[sp][c], acc[0].s[sp][c]);
                 acc_norm2(a[2], acc[0].s[sp][c]);
             }
         store_spinor((VT*)q.t, q.g.V, site, acc[0]);
-        store_spinor((VT*)q.s, q.g.V, site, acc[1]);
     }
     double o[3];
     if (seq_reduce<3, BT / 32>(a, q.part, q.cnt, local, q.nblk[SH], o) && threadIdx.x == 0) {
@@ -255,11 +274,32 @@ __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restri
     }
 }
 
+// 16-byte chunks of a device-layout vector: FP32 float4 = two complex, FP64 double2 = one
+template <class R> struct Chunk;
+template <> struct Chunk<float> {
+    static constexpr int N = 6, P = 2;
+    static __device__ __forceinline__ void split(const float4 v, cx<float> (&z)[2]) {
+        z[0] = mk(v.x, v.y);
+        z[1] = mk(v.z, v.w);
+    }
+    static __device__ __forceinline__ float4 join(const cx<float> (&z)[2]) {
+        return make_float4(z[0].r, z[0].i, z[1].r, z[1].i);
+    }
+};
+template <> struct Chunk<double> {
+    static constexpr int N = 12, P = 1;
+    static __device__ __forceinline__ void split(const double2 v, cx<double> (&z)[1]) { z[0] = mk(v.x, v.y); }
+    static __device__ __forceinline__ double2 join(const cx<double> (&z)[1]) { return make_double2(z[0].r, z[0].i); }
+};
+
 // v^ = t - alpha v_i - gamma_{i-1} v_{i-1}, w^ = s - conj(alpha) w_i - conj(beta_{i-1}) w_{i-1};
-// w^^dag v^, |v^|^2, |w^|^2 -> beta_i, gamma_i, the scales, breakdown checks (Eq. 4.2)
+// w^^dag v^, |v^|^2, |w^|^2 -> beta_i, gamma_i, the scales, breakdown checks (Eq. 4.2).  Element by
+// element: one 16-byte chunk of each operand at a time (few registers, many warps per SM).
 template <class R, int SH>
 __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_lstep(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i) {
     using VT = typename BVec<R>::T;
+    using CH = Chunk<R>;
+    constexpr int P = CH::P;
     const BSeq& q = S[bseq[blockIdx.x]];  // set-up data, not written by the solve
     KState* ks = q.ks;
     pdl_wait_and_release();
@@ -281,33 +321,45 @@ __global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_lstep(const BSeq* __restr
     const int site = local * BT + threadIdx.x;
     typename AccOf<R>::T a[4];
     if (site < q.g.V) {
-        Spinor<R> t, s, vi, wi, vm, wm;
-        load_spinor((const VT*)q.t, q.g.V, site, t);
-        load_spinor((const VT*)q.s, q.g.V, site, s);
-        load_spinor((const VT*)vslot<R>(q, i, false), q.g.V, site, vi);
-        load_spinor((const VT*)vslot<R>(q, i, true), q.g.V, site, wi);
-        if (i > 0) {
-            load_spinor((const VT*)vslot<R>(q, i - 1, false), q.g.V, site, vm);
-            load_spinor((const VT*)vslot<R>(q, i - 1, true), q.g.V, site, wm);
-        }
+        const size_t V = (size_t)q.g.V;
+        const VT* tp = (const VT*)q.t;
+        const VT* sp_ = (const VT*)q.s;
+        const VT* vp = (const VT*)vslot<R>(q, i, false);
+        const VT* wp = (const VT*)vslot<R>(q, i, true);
+        const VT* vmp = (const VT*)vslot<R>(q, i > 0 ? i - 1 : i, false);
+        const VT* wmp = (const VT*)vslot<R>(q, i > 0 ? i - 1 : i, true);
+        VT* vn = (VT*)vslot<R>(q, i + 1, false);
+        VT* wn = (VT*)vslot<R>(q, i + 1, true);
+        const cx<R> c0 = cf[0], c1 = cf[1], c2 = cf[2], c3 = cf[3];
+#pragma unroll 2
+        for (int ch = 0; ch < CH::N; ++ch) {
+            const size_t e = (size_t)ch * V + site;
+            cx<R> t[P], s[P], vv[P], ww[P], vm[P], wm[P];
+            CH::split(__ldg(tp + e), t);
+            CH::split(__ldg(sp_ + e), s);
+            CH::split(__ldg(vp + e), vv);
+            CH::split(__ldg(wp + e), ww);
+            if (i > 0) {
+                CH::split(__ldg(vmp + e), vm);
+                CH::split(__ldg(wmp + e), wm);
+            }
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                cx<R> x = t.s[sp][c] - cf[0] * vi.s[sp][c];
-                cx<R> y = s.s[sp][c] - cf[1] * wi.s[sp][c];
+            for (int p = 0; p < P; ++p) {
+                cx<R> x = t[p] - c0 * vv[p];
+                cx<R> y = s[p] - c1 * ww[p];
                 if (i > 0) {
-                    x = x - cf[2] * vm.s[sp][c];
-                    y = y - cf[3] * wm.s[sp][c];
+                    x = x - c2 * vm[p];
+                    y = y - c3 * wm[p];
                 }
-                t.s[sp][c] = x;
-                s.s[sp][c] = y;
+                t[p] = x;
+                s[p] = y;
                 acc_cdot(a, y, x);
                 acc_norm2(a[2], x);
                 acc_norm2(a[3], y);
             }
-        store_spinor((VT*)vslot<R>(q, i + 1, false), q.g.V, site, t);
-        store_spinor((VT*)vslot<R>(q, i + 1, true), q.g.V, site, s);
+            vn[e] = CH::join(t);
+            wn[e] = CH::join(s);
+        }
     }
     double o[4];
     if (seq_reduce<4, BT / 32>(a, q.part, q.cnt, local, q.nblk[SH], o) && threadIdx.x == 0) {
@@ -564,25 +616,15 @@ template <> __device__ __forceinline__ cx<df> cvt_coef<df>(cx<double> z) { retur
 // that only the projected half spinor, one link row and two accumulators are live at a time (few
 // registers: more blocks per SM).  The operations and their order are those of hop_half_uniform
 // with mul_link / mul_link_dag, so the results are the same.
-__device__ __forceinline__ void hop_half_rows_df(int h, const Geom& g, const Coord& c, int i, const dfc* __restrict__ U,
-                                                 const dfc* __restrict__ x, const HopCoef<df>& hc,
-                                                 cx<df>* __restrict__ out) {
+__device__ __forceinline__ void hop_half_rows_df(int h, const Geom& g, const int* __restrict__ nbr, int i,
+                                                 const dfc* __restrict__ U, const dfc* __restrict__ x,
+                                                 const HopCoef<df>& hc, cx<df>* __restrict__ out) {
     const int nu = h & 3;
     const bool fwd = h < 4;
-    int y[4];
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        int v = c.x[d];
-        if (d == nu) {
-            v += fwd ? 1 : -1;
-            if (v == g.L[d]) v = 0;
-            if (v < 0) v = g.L[d] - 1;
-        }
-        y[d] = v;
-    }
-    const int nb = internal_index(g, y);
-    const bool edge = fwd ? (c.x[3] == g.L[3] - 1) : (c.x[3] == 0);
-    const df ph = (nu == 3 && edge) ? df(g.bc_t) : df(1);
+    // neighbour and boundary phase from the lattice's table (no coordinate arithmetic per hop)
+    const int ne = __ldg(nbr + (size_t)h * g.V + i);
+    const int nb = ne < 0 ? ~ne : ne;
+    const df ph = ne < 0 ? df(-1) : df(1);
     const bool hi2 = nu >= 2, im = (nu & 1) == 0;
     const bool n0 = (nu == 3) ? !fwd : fwd;
     const bool n1 = (nu == 0) ? fwd : !fwd;
@@ -668,10 +710,10 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen(const BSeq* __restrict
         // warp wid: hop wid of the tile's 32 sites, kept as its half spinor
         const int i0 = tile * TT + lane;
         if (i0 < q.g.V) {
-            const Coord c = site_coord(q.g, i0);
             if constexpr (LF == LINK_DF) {
-                hop_half_rows_df(wid, q.g, c, i0, (const dfc*)U, (const dfc*)ri, hc, dirpart[wid][lane]);
+                hop_half_rows_df(wid, q.g, q.nbr, i0, (const dfc*)U, (const dfc*)ri, hc, dirpart[wid][lane]);
             } else {
+                const Coord c = site_coord(q.g, i0);
                 const VT* const xs[1] = {ri};
                 const HopCoef<R> hcs[1] = {hc};
                 Half<R> hp[1];
@@ -743,11 +785,11 @@ __global__ void __launch_bounds__(8 * TT, MINB) k_b_regen2(const BSeq* __restric
     {
         const int i0 = tile * TT + lane;
         if (i0 < g.V) {
-            const Coord c = site_coord(g, i0);
             if constexpr (LF == LINK_DF) {
-                hop_half_rows_df(wid, g, c, i0, (const dfc*)U, (const dfc*)ra, hc, dirpart[0][wid][lane]);
-                hop_half_rows_df(wid, g, c, i0, (const dfc*)U, (const dfc*)rb, hc, dirpart[1][wid][lane]);
+                hop_half_rows_df(wid, g, qa.nbr, i0, (const dfc*)U, (const dfc*)ra, hc, dirpart[0][wid][lane]);
+                hop_half_rows_df(wid, g, qa.nbr, i0, (const dfc*)U, (const dfc*)rb, hc, dirpart[1][wid][lane]);
             } else {
+                const Coord c = site_coord(g, i0);
                 const VT* const xs[2] = {ra, rb};
                 const HopCoef<R> hcs[2] = {hc, hc};
                 Half<R> hp[2];
@@ -970,6 +1012,7 @@ int balloc(ovl_batch* b, int mode, int kmax) {
         q.U = mode == 1 ? (const void*)c->U12 : (const void*)c->U64;
         q.U64 = c->U64;
         q.Udf = c->Udf;
+        q.nbr = c->nbr;
         b->b64[s] = (double2*)take(n * sizeof(double2));
         b->bR[s] = (double2*)take(n * sizeof(double2));
         b->bL[s] = (double2*)take(n * sizeof(double2));
@@ -1031,9 +1074,9 @@ int balloc(ovl_batch* b, int mode, int kmax) {
 
 // Launch with programmatic stream serialisation (see pdl_wait_and_release).
 template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = grid;
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -1086,11 +1129,11 @@ void pass1_step(ovl_batch* b, int i, int k, double mu, double kappa, bool mixed,
     const ovl::BSeq* S = b->dseq;
     const int* tab = b->dbseq[SH];
     if (mixed) {
-        launch_pdl(ovl::k_b_pair<ovl::LINK_F32_12, float, SH>, nb, T, 0, st, S, tab, i, k - 1,
+        launch_pdl(ovl::k_b_pair<ovl::LINK_F32_12, float, SH>, dim3(nb, 2), T, 0, st, S, tab, i, k - 1,
                    ovl::make_coef<float>(mu, kappa), ovl::make_coef<float>(-mu, kappa));
         if (i + 1 < k) launch_pdl(ovl::k_b_lstep<float, SH>, nb, T, 0, st, S, tab, i);
     } else {
-        launch_pdl(ovl::k_b_pair<ovl::LINK_F64, double, SH>, nb, T, 0, st, S, tab, i, k - 1,
+        launch_pdl(ovl::k_b_pair<ovl::LINK_F64, double, SH>, dim3(nb, 2), T, 0, st, S, tab, i, k - 1,
                    ovl::make_coef<double>(mu, kappa), ovl::make_coef<double>(-mu, kappa));
         if (i + 1 < k) launch_pdl(ovl::k_b_lstep<double, SH>, nb, T, 0, st, S, tab, i);
     }

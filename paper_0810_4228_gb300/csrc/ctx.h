@@ -47,6 +47,7 @@ struct ovl_ctx {
     float4* U12 = nullptr;
     float2* U18 = nullptr;
     float4* Udf = nullptr;  // double-float links (regeneration pass of mixed solves)
+    int* nbr = nullptr;     // [8][V] neighbour table of the regeneration kernel (ovl::launch_build_nbr)
     bool have_gauge = false;
 
     // deflation

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "df32.cuh"
 #include "stencil_impl.cuh"
 
 namespace ovl {
@@ -340,6 +341,23 @@ __device__ __forceinline__ void proj_g5_full(const Spinor<double>& x, Spinor<dou
     recon_acc<NU, S>(o, h, 1.0);
 }
 
+template <int NU, int S, class R>
+__device__ __forceinline__ void proj_g5_full_r(const Spinor<R>& x, Spinor<R>& o) {
+    Spinor<R> g5 = x;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        g5.s[2][a] = -x.s[2][a];
+        g5.s[3][a] = -x.s[3][a];
+    }
+    Half<R> h;
+    project<NU, S>(g5, h);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o.s[sp][a] = mk(R(0), R(0));
+    recon_acc<NU, S>(o, h, R(1));
+}
+
 // link force of y = gamma5 D_w(m) x for the adjoint gr of y, added into gU (device link layout):
 // gU[x, nu] += -kappa ph (cf g~ (x) conj(x(x+nu)) + cb x(x) (x) conj(g^)),
 // g~ = (1 + gamma_nu) gamma5 gr(x), g^ = (1 - gamma_nu) gamma5 gr(x + nu)
@@ -408,6 +426,187 @@ __device__ __forceinline__ double dmu_site(const Geom& g, const Coord& c, int s,
 
 // gU = sum_q force(v~_q, Z_q) (the link adjoint of Re <Z_q, A v~_q>), gmu = sum_q Re <Z_q, dA/dmu v~_q>;
 // one thread per site and direction block, the q sum inside (fixed order)
+// The same product in double-float arithmetic (products exact through the FMA split, sums
+// compensated; about 48 significant bits, on the FP32 pipe), FP64 in and out.
+__global__ void __launch_bounds__(256) k_gq_combine_df(const double2* __restrict__ W, const double2* __restrict__ M,
+                                                       double2* __restrict__ Z, int k, size_t n) {
+    __shared__ float4 ws[ZT_P][ZT_E];
+    __shared__ float4 ms[ZT_P][ZT_Q];
+    const size_t e0 = (size_t)blockIdx.x * ZT_E;
+    const int q0 = blockIdx.y * ZT_Q;
+    const int te = threadIdx.x & 63, tq = threadIdx.x >> 6;  // 4 groups of 4 columns
+    dfacc ar[4], ai[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ar[j] = ai[j] = {0.f, 0.f};
+    for (int p0 = 0; p0 < k; p0 += ZT_P) {
+        for (int x = threadIdx.x; x < ZT_P * ZT_E; x += blockDim.x) {
+            const int pp = x / ZT_E, ee = x % ZT_E;
+            const size_t e = e0 + ee;
+            const double2 w = (p0 + pp < k && e < n) ? W[(size_t)(p0 + pp) * n + e] : make_double2(0.0, 0.0);
+            const dfc d = c2dfc(d2df(w));
+            ws[pp][ee] = make_float4(d.rh, d.rl, d.ih, d.il);
+        }
+        for (int x = threadIdx.x; x < ZT_P * ZT_Q; x += blockDim.x) {
+            const int pp = x / ZT_Q, qq = x % ZT_Q;
+            const double2 m = (p0 + pp < k && q0 + qq < k) ? M[(size_t)(p0 + pp) * k + q0 + qq] : make_double2(0.0, 0.0);
+            const dfc d = c2dfc(d2df(make_double2(m.x, -m.y)));
+            ms[pp][qq] = make_float4(d.rh, d.rl, d.ih, d.il);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int pp = 0; pp < ZT_P; ++pp) {
+            const float4 wv = ws[pp][te];
+            const df wr(wv.x, wv.y), wi(wv.z, wv.w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 mv = ms[pp][tq * 4 + j];
+                const df mr(mv.x, mv.y), mi(mv.z, mv.w);
+                dfacc_add(ar[j], mr, wr, false);
+                dfacc_add(ar[j], mi, wi, true);
+                dfacc_add(ai[j], mr, wi, false);
+                dfacc_add(ai[j], mi, wr, false);
+            }
+        }
+        __syncthreads();
+    }
+    const size_t e = e0 + te;
+    if (e < n)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = q0 + tq * 4 + j;
+            if (q < k) Z[(size_t)q * n + e] = df2d(mk(dfacc_value(ar[j]), dfacc_value(ai[j])));
+        }
+}
+
+// The same product in FP32 (the mixed-precision gradient), FP64 in and out.
+__global__ void __launch_bounds__(256) k_gq_combine_f32(const double2* __restrict__ W, const double2* __restrict__ M,
+                                                        double2* __restrict__ Z, int k, size_t n) {
+    __shared__ float2 ws[ZT_P][ZT_E];
+    __shared__ float2 ms[ZT_P][ZT_Q];
+    const size_t e0 = (size_t)blockIdx.x * ZT_E;
+    const int q0 = blockIdx.y * ZT_Q;
+    const int te = threadIdx.x & 63, tq = threadIdx.x >> 6;
+    cx<float> acc[4] = {mk(0.f, 0.f), mk(0.f, 0.f), mk(0.f, 0.f), mk(0.f, 0.f)};
+    for (int p0 = 0; p0 < k; p0 += ZT_P) {
+        for (int x = threadIdx.x; x < ZT_P * ZT_E; x += blockDim.x) {
+            const int pp = x / ZT_E, ee = x % ZT_E;
+            const size_t e = e0 + ee;
+            const double2 w = (p0 + pp < k && e < n) ? W[(size_t)(p0 + pp) * n + e] : make_double2(0.0, 0.0);
+            ws[pp][ee] = make_float2((float)w.x, (float)w.y);
+        }
+        for (int x = threadIdx.x; x < ZT_P * ZT_Q; x += blockDim.x) {
+            const int pp = x / ZT_Q, qq = x % ZT_Q;
+            const double2 m = (p0 + pp < k && q0 + qq < k) ? M[(size_t)(p0 + pp) * k + q0 + qq] : make_double2(0.0, 0.0);
+            ms[pp][qq] = make_float2((float)m.x, (float)-m.y);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int pp = 0; pp < ZT_P; ++pp) {
+            const float2 wv = ws[pp][te];
+            const cx<float> w = mk(wv.x, wv.y);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 mv = ms[pp][tq * 4 + j];
+                cfma(acc[j], mk(mv.x, mv.y), w);
+            }
+        }
+        __syncthreads();
+    }
+    const size_t e = e0 + te;
+    if (e < n)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = q0 + tq * 4 + j;
+            if (q < k) Z[(size_t)q * n + e] = make_double2((double)acc[j].r, (double)acc[j].i);
+        }
+}
+
+// FP32 form of the link force and mu derivative over the pairs (v_q, Z_q) for the mixed-precision
+// gradient: every pair's contribution in FP32 from the FP64 vectors, the sum over pairs compensated
+// (Kahan) in FP32 for the links and in FP64 for d/dmu.
+template <int NU>
+__device__ __forceinline__ void link_force_f32(const Geom& g, const Coord& c, int s, const double2* x,
+                                               const double2* gr, float cf, float cb, cx<float> (&z)[9],
+                                               cx<float> (&zc)[9]) {
+    const int f = neighbour(g, c, NU, +1);
+    const float ph = (NU == 3 && c.x[3] == g.L[3] - 1) ? (float)g.bc_t : 1.f;
+    Spinor<double> dgx, dgy, dpx, dpy;
+    load_spinor(gr, g.V, s, dgx);
+    load_spinor(gr, g.V, f, dgy);
+    load_spinor(x, g.V, s, dpx);
+    load_spinor(x, g.V, f, dpy);
+    Spinor<float> gx, gy, px, py, gt, gh;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gx.s[sp][a] = mk((float)dgx.s[sp][a].r, (float)dgx.s[sp][a].i);
+            gy.s[sp][a] = mk((float)dgy.s[sp][a].r, (float)dgy.s[sp][a].i);
+            px.s[sp][a] = mk((float)dpx.s[sp][a].r, (float)dpx.s[sp][a].i);
+            py.s[sp][a] = mk((float)dpy.s[sp][a].r, (float)dpy.s[sp][a].i);
+        }
+    proj_g5_full_r<NU, +1, float>(gx, gt);
+    proj_g5_full_r<NU, -1, float>(gy, gh);
+    const float af = -cf * ph, ab = -cb * ph;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cx<float> w = mk(0.f, 0.f);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp) {
+                w = w + af * cdot(py.s[sp][j], gt.s[sp][i]);
+                w = w + ab * cdot(gh.s[sp][j], px.s[sp][i]);
+            }
+            // Kahan: z + w with the lost low part carried in zc
+            const cx<float> yv = w - zc[3 * i + j];
+            const cx<float> t = z[3 * i + j] + yv;
+            zc[3 * i + j] = (t - z[3 * i + j]) - yv;
+            z[3 * i + j] = t;
+        }
+}
+
+__global__ void __launch_bounds__(GT) k_force_sum_f32(const double2* __restrict__ U, const double2* __restrict__ V,
+                                                      const double2* __restrict__ Z, int k, double2* __restrict__ gU,
+                                                      double kappa, double mu, Geom g, double* partials,
+                                                      unsigned int* counter, double* gmu) {
+    __shared__ double red[32];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nu = blockIdx.y;  // 0..3 links, 4: the mu derivative
+    const size_t n = (size_t)12 * g.V;
+    double part[1] = {0.0};
+    if (s < g.V) {
+        const Coord c = site_coord(g, s);
+        if (nu < 4) {
+            cx<float> z[9], zc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) z[q] = zc[q] = mk(0.f, 0.f);
+            const float cf = nu == 3 ? (float)(kappa * exp(mu)) : (float)kappa;
+            const float cb = nu == 3 ? (float)(kappa * exp(-mu)) : (float)kappa;
+            for (int q = 0; q < k; ++q) {
+                const double2* x = V + (size_t)q * n;
+                const double2* gr = Z + (size_t)q * n;
+                switch (nu) {
+                    case 0: link_force_f32<0>(g, c, s, x, gr, cf, cb, z, zc); break;
+                    case 1: link_force_f32<1>(g, c, s, x, gr, cf, cb, z, zc); break;
+                    case 2: link_force_f32<2>(g, c, s, x, gr, cf, cb, z, zc); break;
+                    default: link_force_f32<3>(g, c, s, x, gr, cf, cb, z, zc); break;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                gU[((size_t)nu * 9 + q) * g.V + s] = make_double2((double)z[q].r - (double)zc[q].r,
+                                                                  (double)z[q].i - (double)zc[q].i);
+        } else {
+            for (int q = 0; q < k; ++q) part[0] += dmu_site(g, c, s, U, V + (size_t)q * n, Z + (size_t)q * n, kappa, mu);
+        }
+    }
+    if (nu == 4) {
+        double out[1];
+        if (grid_sum_last<1>(part, partials, counter, out, red) && threadIdx.x == 0) *gmu = out[0];
+    }
+}
+
 __global__ void __launch_bounds__(GT) k_force_sum(const double2* __restrict__ U, const double2* __restrict__ V,
                                                   const double2* __restrict__ Z, int k, double2* __restrict__ gU,
                                                   double kappa, double mu, Geom g, double* partials,
@@ -471,6 +670,8 @@ extern "C" int ovl_sign_grad(ovl_ctx* c, int k, double mu, double kappa, const v
     if (!c->have_gauge) return fail(c, OVL_ESTATE, "gauge field not set");
     if (k < 1) return fail(c, OVL_EINVAL, "k must be positive");
     if (flags & OVL_HOST) return fail(c, OVL_EINVAL, "device pointers only");
+    if (flags & ~OVL_MIXED) return fail(c, OVL_EINVAL, "flags: 0 or OVL_MIXED");
+    const bool mixed = (flags & OVL_MIXED) != 0;
     int r = ensure_solve(c, k);
     if (r) return r;
     cudaStream_t st = c->st;
@@ -482,7 +683,9 @@ extern "C" int ovl_sign_grad(ovl_ctx* c, int k, double mu, double kappa, const v
     unsigned int* cnt = c->counter;
     // ---- workspace: W (k + 1 vectors), Z (k vectors), g_y packed, link gradient, scalars
     const size_t kk1 = (size_t)k + 1;
-    const size_t need = ((2 * kk1 + 1 + 3 + 1) * n + 4 * kk1 + (size_t)k * k + 64) * sizeof(double2);
+    // (mixed: the FP32 bases, (k + 1) vectors of n complex64 each, after the FP64 ones)
+    const size_t need = ((2 * kk1 + 1 + 3 + 1) * n + 4 * kk1 + (size_t)k * k + 64) * sizeof(double2) +
+                        (mixed ? 2 * kk1 * n * sizeof(float2) : 0);
     if (c->gwork_bytes < need) {
         if (c->gwork) cudaFree(c->gwork);
         c->gwork = nullptr;
@@ -507,19 +710,40 @@ extern "C" int ovl_sign_grad(ovl_ctx* c, int k, double mu, double kappa, const v
     OVL_CUDA_TRY(c, cudaMemsetAsync(misc, 0, 32 * sizeof(double2), st));
     ovl::launch_pack_spinor((const double2*)b, c->b64, 0, g, st);
     ovl::launch_pack_spinor((const double2*)gy, gyd, 0, g, st);
-    // ---- two-sided Lanczos from (b, g), bases kept (Sec. 4, Eq. 4.2)
+    // ---- two-sided Lanczos from (b, g), bases kept (Sec. 4, Eq. 4.2); mixed: in FP32 with 12-real
+    // links and FP64 reductions and coefficients, the FP32 bases then widened to FP64
     double2* V = c->V64;
     ovl::launch_state_init(ks, st);
     ovl::k_bilinear_start<<<ovl::grid_n(n), 256, 0, st>>>(c->b64, gyd, V, W, c->y64, ks, c->vscale, wscale, zeta,
                                                           part, cnt, n);
-    for (int i = 0; i < k; ++i) {
-        const double2* vi = V + (size_t)i * n;
-        const double2* wi = W + (size_t)i * n;
-        ovl::launch_dslash_pair(c->U64, 0, vi, wi, c->t64, c->s64, mu, kappa, ks, c->alpha, i, k - 1, part, cnt, g, st);
-        if (i + 1 < k)
-            ovl::launch_lanczos_step(0, c->t64, c->s64, vi, wi, i > 0 ? vi - n : vi, i > 0 ? wi - n : wi,
-                                     V + (size_t)(i + 1) * n, W + (size_t)(i + 1) * n, ks, c->alpha, c->beta,
-                                     c->gamma, c->vscale, i, k, part, cnt, n, st);
+    if (mixed) {
+        float2* V32 = reinterpret_cast<float2*>(misc + 32);
+        float2* W32 = V32 + kk1 * n;
+        ovl::launch_native_f64_to_f32(V, V32, g, 1, st);
+        ovl::launch_native_f64_to_f32(W, W32, g, 1, st);
+        for (int i = 0; i < k; ++i) {
+            const float2* vi = V32 + (size_t)i * n;
+            const float2* wi = W32 + (size_t)i * n;
+            ovl::launch_dslash_pair(c->U12, 1, vi, wi, c->t32, c->s32, mu, kappa, ks, c->alpha, i, k - 1, part, cnt, g,
+                                    st);
+            if (i + 1 < k)
+                ovl::launch_lanczos_step(1, c->t32, c->s32, vi, wi, i > 0 ? vi - n : vi, i > 0 ? wi - n : wi,
+                                         V32 + (size_t)(i + 1) * n, W32 + (size_t)(i + 1) * n, ks, c->alpha, c->beta,
+                                         c->gamma, c->vscale, i, k, part, cnt, n, st);
+        }
+        ovl::launch_native_f32_to_f64(V32, V, g, k, st);
+        ovl::launch_native_f32_to_f64(W32, W, g, k, st);
+    } else {
+        for (int i = 0; i < k; ++i) {
+            const double2* vi = V + (size_t)i * n;
+            const double2* wi = W + (size_t)i * n;
+            ovl::launch_dslash_pair(c->U64, 0, vi, wi, c->t64, c->s64, mu, kappa, ks, c->alpha, i, k - 1, part, cnt, g,
+                                    st);
+            if (i + 1 < k)
+                ovl::launch_lanczos_step(0, c->t64, c->s64, vi, wi, i > 0 ? vi - n : vi, i > 0 ? wi - n : wi,
+                                         V + (size_t)(i + 1) * n, W + (size_t)(i + 1) * n, ks, c->alpha, c->beta,
+                                         c->gamma, c->vscale, i, k, part, cnt, n, st);
+        }
     }
     ovl::k_wscale<<<(k + 127) / 128, 128, 0, st>>>(c->gamma, ks, wscale);
     // ---- y = |b| V sgn(G) e_1 (inner sign as in the solve)
@@ -597,8 +821,14 @@ extern "C" int ovl_sign_grad(ovl_ctx* c, int k, double mu, double kappa, const v
     const int B = (g.V + ovl::GT - 1) / ovl::GT;
     if (grad_U || grad_mu) {
         dim3 gz((unsigned)((n + ovl::ZT_E - 1) / ovl::ZT_E), (unsigned)((kk + ovl::ZT_Q - 1) / ovl::ZT_Q));
-        ovl::k_gq_combine<<<gz, 256, 0, st>>>(W, M, Z, kk, n);
-        ovl::k_force_sum<<<dim3(B, 5), ovl::GT, 0, st>>>(c->U64, V, Z, kk, gUd, kappa, mu, g, part, cnt, gmu_acc);
+        if (mixed) {
+            ovl::k_gq_combine_f32<<<gz, 256, 0, st>>>(W, M, Z, kk, n);
+            ovl::k_force_sum_f32<<<dim3(B, 5), ovl::GT, 0, st>>>(c->U64, V, Z, kk, gUd, kappa, mu, g, part, cnt,
+                                                                 gmu_acc);
+        } else {
+            ovl::k_gq_combine_df<<<gz, 256, 0, st>>>(W, M, Z, kk, n);
+            ovl::k_force_sum<<<dim3(B, 5), ovl::GT, 0, st>>>(c->U64, V, Z, kk, gUd, kappa, mu, g, part, cnt, gmu_acc);
+        }
         if (grad_U) ovl::k_links_to_canon<<<B, ovl::GT, 0, st>>>(gUd, (double2*)grad_U, g);
     }
     if (grad_b) {

@@ -63,6 +63,10 @@ int dslash_grid(const Geom& g, int threads);
 int dslash_pair_blocks(const Geom& g);
 // nvec FP64 device-layout vectors to the FP32 device layout (component pairs in float4)
 void launch_native_f64_to_f32(const double2* x, void* y, const Geom& g, int nvec, cudaStream_t st);
+void launch_native_f32_to_f64(const void* x, double2* y, const Geom& g, int nvec, cudaStream_t st);
+// nbr[h][i]: internal index of the hop-h neighbour of site i (h < 4 forward, else backward in nu = h & 3),
+// bit-inverted where the hop takes the antiperiodic phase -1
+void launch_build_nbr(int* nbr, const Geom& g, cudaStream_t st);
 // stencil thread layout: -1 automatic (by volume), 0 one thread per site, 1 direction split
 void set_dslash_variant(int mode);
 

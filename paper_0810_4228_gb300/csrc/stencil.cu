@@ -426,6 +426,46 @@ void launch_native_f64_to_f32(const double2* x, void* y, const Geom& g, int nvec
     k_native_f64_to_f32<<<blocks, 256, 0, st>>>(x, (float4*)y, g.V, nvec);
 }
 
+// the inverse: FP32 device layout (float4 [6][V]) to the FP64 device layout (double2 [12][V])
+__global__ void k_native_f32_to_f64(const float4* __restrict__ x, double2* __restrict__ y, int V, int nvec) {
+    const size_t tot = (size_t)nvec * 6 * V;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t vec = e / ((size_t)6 * V);
+        const size_t r = e - vec * 6 * V;
+        const int c2 = (int)(r / V), i = (int)(r - (size_t)c2 * V);
+        const float4 a = x[vec * 6 * (size_t)V + (size_t)c2 * V + i];
+        double2* yv = y + vec * 12 * (size_t)V;
+        yv[(size_t)(2 * c2) * V + i] = make_double2((double)a.x, (double)a.y);
+        yv[(size_t)(2 * c2 + 1) * V + i] = make_double2((double)a.z, (double)a.w);
+    }
+}
+
+void launch_native_f32_to_f64(const void* x, double2* y, const Geom& g, int nvec, cudaStream_t st) {
+    const size_t tot = (size_t)nvec * 6 * g.V;
+    int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+    k_native_f32_to_f64<<<blocks, 256, 0, st>>>((const float4*)x, y, g.V, nvec);
+}
+
+// Neighbour table: nbr[h][i] = internal index of the neighbour of site i in hop h (h < 4: x + nu,
+// h >= 4: x - nu, nu = h & 3), bit-inverted (~index, negative) where the hop crosses the
+// antiperiodic time boundary and takes the phase -1.
+__global__ void k_build_nbr(int* __restrict__ nbr, Geom g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    const Coord c = site_coord(g, i);
+    for (int h = 0; h < 8; ++h) {
+        const int nu = h & 3;
+        const bool fwd = h < 4;
+        const int nb = neighbour(g, c, nu, fwd ? +1 : -1);
+        const bool edge = nu == 3 && (fwd ? (c.x[3] == g.L[3] - 1) : (c.x[3] == 0));
+        nbr[(size_t)h * g.V + i] = (edge && g.bc_t < 0) ? ~nb : nb;
+    }
+}
+
+void launch_build_nbr(int* nbr, const Geom& g, cudaStream_t st) {
+    k_build_nbr<<<(g.V + 127) / 128, 128, 0, st>>>(nbr, g);
+}
+
 // ---------------------------------------------------------------- layouts --
 __global__ void k_pack_gauge(const double2* __restrict__ Uc, double2* __restrict__ U64, float4* __restrict__ U12,
                              float2* __restrict__ U18, float4* __restrict__ Udf, Geom g) {

@@ -256,23 +256,24 @@ class Context:
         self._check(self._lib.ovl_apply_pair_noalloc(self._h, mu, kappa, prec, _ptr(v), _ptr(w), _ptr(t), _ptr(s),
                                                       _ptr(alpha_dev)))
 
-    def dw_grad(self, mu: float, kappa: float, x, g, grad_U=None):
-        """(grad_U, grad_mu) of a real l(y), y = A x, from g = dl/dy*; canonical device tensors."""
+    def dw_grad(self, mu: float, kappa: float, x, g, grad_U=None, flags: int = 0):
+        """(grad_U, grad_mu) of a real l(y), y = A x, from g = dl/dy*; canonical device tensors.
+        flags: 0 (FP64) or F32 (the link force in FP32)."""
         gm = ctypes.c_double()
         self._check(self._lib.ovl_dw_grad(self._h, mu, kappa, _ptr(x), _ptr(g),
-                                          _ptr(grad_U) if grad_U is not None else None, ctypes.byref(gm), 0))
+                                          _ptr(grad_U) if grad_U is not None else None, ctypes.byref(gm), flags))
         return grad_U, gm.value
 
-    def sign_grad(self, k: int, mu: float, kappa: float, b, g, y=None, grad_U=None, grad_b=None):
-        """Derivatives of Re <g, sgn(A) b> with respect to mu, U and b (k-step FP64 two-sided Lanczos
-        from (b, g), no deflation); canonical device tensors.  Returns (grad_mu, info); y, grad_U,
-        grad_b are written when given."""
+    def sign_grad(self, k: int, mu: float, kappa: float, b, g, y=None, grad_U=None, grad_b=None, flags: int = 0):
+        """Derivatives of Re <g, sgn(A) b> with respect to mu, U and b (k-step two-sided Lanczos from
+        (b, g), no deflation; FP64, or FP32 with flags=MIXED); canonical device tensors.  Returns
+        (grad_mu, info); y, grad_U, grad_b are written when given."""
         gm = ctypes.c_double()
         info = Info()
         r = self._lib.ovl_sign_grad(self._h, int(k), mu, kappa, _ptr(b), _ptr(g),
                                     _ptr(y) if y is not None else None,
                                     _ptr(grad_U) if grad_U is not None else None, ctypes.byref(gm),
-                                    _ptr(grad_b) if grad_b is not None else None, 0, ctypes.byref(info))
+                                    _ptr(grad_b) if grad_b is not None else None, int(flags), ctypes.byref(info))
         self._check(r)
         return gm.value, info.as_dict()
 

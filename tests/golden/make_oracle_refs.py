@@ -45,16 +45,14 @@ KAPPA, EPS, M = 0.2, 1.0, 20
 K_LO, K_HI = 800, 1000
 NSAMPLE, NPROJ, PROJ_SEED = 4096, 8, 9000
 
-# one field + chemical potential per group; its sources share the oracle's eigenpairs
+# one field + chemical potential + sources per group (groups of the same field share the
+# eigenpairs through --cache once the first has computed them)
 GROUPS = [
     {"dims": (8, 8, 8, 8), "seed": 1001, "mu": 0.1, "sources": [("gauss8_mu0.1", "gauss", 2001)]},
     {"dims": (8, 8, 8, 8), "seed": 1001, "mu": 0.3, "sources": [("gauss8_mu0.3", "gauss", 2001)]},
     {"dims": (8, 8, 8, 8), "seed": 1001, "mu": 0.5, "sources": [("gauss8_mu0.5", "gauss", 2001)]},
-    {"dims": (6, 6, 6, 6), "seed": 1003, "mu": 0.2,
-     "sources": [(f"batch6_r{r}", "point", r) for r in (0, 5, 11)]},
-    {"dims": (8, 8, 8, 8), "seed": 1004, "mu": 0.2,
-     "sources": [(f"batch8_r{r}", "point", r) for r in (0, 5, 11)]},
-]
+] + [{"dims": (6, 6, 6, 6), "seed": 1003, "mu": 0.2, "sources": [(f"batch6_r{r}", "point", r)]} for r in (0, 5, 11)] \
+  + [{"dims": (8, 8, 8, 8), "seed": 1004, "mu": 0.2, "sources": [(f"batch8_r{r}", "point", r)]} for r in (0, 5, 11)]
 
 
 def _run_group(args):

@@ -49,6 +49,31 @@ def test_dw_gradients_vs_oracle(mods, dims):
     np.testing.assert_allclose(xt.grad.cpu().numpy(), A.conj().T @ w, atol=1e-13)
 
 
+@pytest.mark.parametrize("dims", [(2, 2, 2, 4), (4, 4, 4, 4)])
+def test_dw_gradients_f32_vs_oracle(mods, dims):
+    """The FP32 form of the stencil adjoint (OVL_F32: the link force in FP32) against the oracle's
+    dA/dU: relative error below 1e-6; d/dmu (FP64 in both forms) as in FP64."""
+    torch, O, AG = mods
+    mu = 0.3
+    U = synth.gauge_field(dims, 1.0, 61)
+    x = synth.gaussian_source(dims, 62)
+    w = synth.gaussian_source(dims, 63)
+    rng = np.random.default_rng(64)
+    dU = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    lat = O.Context(dims)
+    lat.set_gauge(torch_c128(U))
+    gU = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+    _, gmu = lat.dw_grad(mu, KAPPA, torch_c128(x), torch_c128(w), gU, flags=O.F32)
+    ref_dir = np.real(np.vdot(w, Fr.dA_dU_apply(U, dU, dims, mu, KAPPA, x)))
+    got_dir = np.real(np.vdot(gU.cpu().numpy().ravel(), dU.ravel()))
+    assert abs(got_dir - ref_dir) <= 1e-6 * abs(ref_dir), (got_dir, ref_dir)
+    ref_mu = np.real(np.vdot(w, Fr.dA_dmu(U, dims, mu, KAPPA) @ x))
+    assert abs(gmu - ref_mu) <= 1e-12 * max(1.0, abs(ref_mu))
+    gU64 = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+    lat.dw_grad(mu, KAPPA, torch_c128(x), torch_c128(w), gU64)
+    assert (gU - gU64).abs().max().item() <= 1e-6 * gU64.abs().max().item()
+
+
 def test_dw_gradients_vs_finite_differences(mods):
     torch, O, AG = mods
     dims, mu = (4, 2, 2, 4), 0.25
