@@ -4,8 +4,8 @@ eigensolver), 16^3 x 8 in mixed precision with 30 deflated eigenpairs, and 12 po
 each of four lattices of uneven sizes with 20 deflated eigenpairs each in one batch.
 
 The dense oracle cannot reach these sizes.  Where the oracle's own LU-based eigensolver can
-(8^4 and 6^4), tests/golden/make_oracle_refs.py stored the oracle's deflated two-sided Lanczos
-result (its own eigenpairs, k = 1100, self-converged): the GPU results are compared with it on
+(8^4 and 6^4), tests/golden/make_oracle_refs.py stored the oracle's deflated Arnoldi result
+(its own ARPACK eigenpairs, k = 1000 or 1600, self-converged): the GPU results are compared with it on
 4096 sampled components, element by element, and on the whole vector through eight stored
 projections.  Everywhere the checks that hold at any size apply as well: the eigenpair relations
 A r = lambda r and A^dag l = conj(lambda) l at sampled sites against the oracle's single-site
@@ -56,20 +56,23 @@ def test_8x4_deflated_arnoldi_and_lanczos2(ovl, mu):
     assert np.all(np.abs(lam.real) <= info["lambda_cut"] + 1e-12)
     _check_pairs_sampled(U, dims, mu, lam, R, L, (0, 19), (0, 1234, 4095), 1e-12)
     np.testing.assert_allclose(L.conj() @ R.T, np.eye(20), atol=1e-9)
-    y2 = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, b)[0].clone()
-    ya = ctx.sign_krylov(ovl.ARNOLDI, 1000, mu, KAPPA, b)[0].clone()
-    ym = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
-    yad = ctx.sign_krylov(ovl.ARNOLDI, 1000, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
+    kk = 1600 if mu == 0.5 else 1000  # mu = 0.5 converges more slowly (3e-9 between k = 800 and 1000)
+    y2 = ctx.sign_krylov(ovl.LANCZOS2, kk, mu, KAPPA, b)[0].clone()
+    ya = ctx.sign_krylov(ovl.ARNOLDI, kk, mu, KAPPA, b)[0].clone()
+    ym = ctx.sign_krylov(ovl.LANCZOS2, kk, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
+    yad = ctx.sign_krylov(ovl.ARNOLDI, kk, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
     assert rel(y2.cpu().numpy(), ya.cpu().numpy()) < 1e-9
     assert rel(ym.cpu().numpy(), y2.cpu().numpy()) < 1e-8
     # double-float Arnoldi: the FP64 Arnoldi process at 48-bit precision
     assert rel(yad.cpu().numpy(), ya.cpu().numpy()) < 1e-11
-    # against the oracle (its own eigenpairs, k = 1100): FP64 1e-10, mixed 1e-8
+    # against the oracle (its own eigenpairs, Arnoldi at k = 1000, or 1600 at mu = 0.5): FP64 1e-10,
+    # mixed 1e-8
     ref = oracle_refs()[f"gauss8_mu{mu}"]
-    assert ref["selfdiff"] < 1e-11 and ref["eig_residual"] < 1e-9
+    assert ref["selfdiff"] < 1e-11 and ref["eig_residual"] < 1e-12
     for y, tol, what in ((y2, 1e-10, "2sL FP64"), (ya, 1e-10, "Arnoldi FP64"), (yad, 1e-10, "Arnoldi double-float"),
                          (ym, 1e-8, "2sL mixed")):
-        assert_oracle_close(y.cpu().numpy(), ref, tol, what)
+        d = assert_oracle_close(y.cpu().numpy(), ref, tol, what)
+        print(f"8^4 mu={mu} {what} vs oracle: sampled rel {d[0]:.2e}, max {d[1]:.2e}, projected {d[2]:.2e}")
     # sgn(A)^2 b = b
     z = ctx.sign_krylov(ovl.LANCZOS2, 1000, mu, KAPPA, y2)[0]
     assert rel(z.cpu().numpy(), b.cpu().numpy()) < 1e-8
