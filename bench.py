@@ -73,7 +73,7 @@ WORKLOAD8 = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3,
 C3_DIMS, C3_SEED_U, C3_SEED_B, C3_MU, C3_M = (16, 16, 16, 8), 1002, 2002, 0.3, 30
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the headline batch's dominant kernel
 # class, from one ncu capture of the current kernels (the roofline's "traffic"); None until measured
-HEAD_TRAFFIC = {}
+HEAD_TRAFFIC = {"pass2_batched_doublefloat": 715643648}  # k_b_regen, 48 sequences (profiles/)
 
 
 def peaks():
@@ -644,17 +644,19 @@ def gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank):
                                                               flags=ovl.OVERLAP), bsingle, 1, 2, flush)
     t_adf = time_solves(torch, ctx, lambda b: ctx.sign_krylov(ovl.ARNOLDI, k_adf, MU, KAPPA, b, out1,
                                                               flags=ovl.OVERLAP | ovl.MIXED), bsingle, 2, nctx, flush)
-    # the double-float Gram-Schmidt sweeps against HBM: 4 passes over v_0..v_j at step j, 16 B per
-    # complex element (CUDA events around each sweep kernel, eager launches)
+    # the double-float Gram-Schmidt sweeps against HBM: the delayed CGS2 reads v_0..v_j twice at
+    # step j (the classical form four times), 16 B per complex element (CUDA events around each
+    # sweep kernel, eager launches)
     ctx.profile(reset=True)
     ctx.sign_krylov(ovl.ARNOLDI, k_adf, MU, KAPPA, srcs[0], out1, flags=ovl.OVERLAP | ovl.MIXED | ovl.PROFILE)
     torch.cuda.synchronize()
     aprof = ctx.profile(reset=True)
     sweep_ms = sum(aprof.get(kk, {}).get("ms", 0.0) for kk in ("multidot", "multiaxpy"))
-    sweep_bytes = 2 * k_adf * (k_adf + 1) * ctx.n * 16
-    adf_sweeps = {"bytes_per_solve": sweep_bytes, "ms": round(sweep_ms, 3),
+    sweep_bytes = k_adf * (k_adf + 1) * ctx.n * 16
+    adf_sweeps = {"bytes_per_solve": sweep_bytes, "ms": round(sweep_ms, 3), "form": "delayed CGS2, two sweeps per step",
                   "GB_s": round(sweep_bytes / (sweep_ms * 1e6), 1) if sweep_ms else None,
                   "frac_hbm": round(sweep_bytes / (sweep_ms * 1e6) / hbm_peak, 3) if sweep_ms else None,
+                  "classical_cgs2_bytes_equivalent_GB_s": round(2 * sweep_bytes / (sweep_ms * 1e6), 1) if sweep_ms else None,
                   "inner_sign_ms": round(aprof.get("inner_sign", {}).get("ms", 0.0), 3),
                   "stencil_ms": round(aprof.get("dslash", {}).get("ms", 0.0), 3)}
     res = {

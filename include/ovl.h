@@ -225,8 +225,11 @@ int ovl_batch_profile(ovl_batch* batch, double* ms3, int* nsolves, int reset);
  * (pass-1 site blocks of 64, 128 or 256 sites; the regeneration kernel at 3 to 6 blocks per SM
  * with one sequence per block, or at 2 to 4 blocks per SM with two sequences of one lattice per
  * block) with short eager solves of the batch itself and keeps the fastest (OVL_NO_TUNE skips
- * this).  Writes the chosen shapes (NULL pointers are skipped); returns OVL_ESTATE before the
- * first tuning. */
+ * this).  The choice is cached per (GPU model, SM count, precision, lattice extents and
+ * right-hand sides of every context): later batches of the same shape in the process take it
+ * without timing, and when the environment variable OVL_TUNE_CACHE names a file the choices are
+ * appended there ("key shape blocks_per_sm pair" lines) and read by later processes.  Writes the
+ * chosen shapes (NULL pointers are skipped); returns OVL_ESTATE before the first tuning. */
 int ovl_batch_tuning(const ovl_batch* batch, int* pass1_block_sites, int* regen_blocks_per_sm,
                      int* regen_seqs_per_block);
 /* Pins the launch shapes (pass1_block_sites 64, 128 or 256; regen_blocks_per_sm 2 to 6;

@@ -20,7 +20,12 @@
 // y = sum_i c_i v_i at the end, or, with OVL_TWO_PASS or when the basis would
 // exceed 32 GiB, an FP64 pass 1 followed by the FP64 regeneration pass.
 #include <algorithm>
+#include <array>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -861,6 +866,7 @@ struct ovl_batch {
     int regen_pair = 0;         // 1: two sequences of one lattice per regeneration block
     bool tuned = false;
     bool pinned = false;        // shapes set by ovl_batch_set_tuning: never retuned
+    bool tune_cached = false;   // the shapes came from the tuning cache (no timing)
     int tuned_mode = -1;
     std::vector<ovl::BSeq> hseq;
     std::vector<double2*> b64, bR, bL, pq;
@@ -1280,6 +1286,56 @@ int enqueue_batch(ovl_batch* b, int k, double mu, double kappa, int flags, cudaS
     return cudaGetLastError() == cudaSuccess ? OVL_OK : bfail(b, OVL_ECUDA, "batch launch");
 }
 
+// Tuning cache: the chosen shapes per (GPU model, SM count, precision, lattice extents and
+// right-hand sides of every context), kept for the process and, when the environment variable
+// OVL_TUNE_CACHE names a file, in that file ("key shape minb pair" per line) across processes.
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 3>> g_tune;
+
+std::string tune_key(const ovl_batch* b) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr{};
+    cudaGetDeviceProperties(&pr, dev);
+    std::string k = std::string(pr.name) + "/" + std::to_string(pr.multiProcessorCount) + "/m" + std::to_string(b->mode);
+    for (size_t j = 0; j < b->ctx.size(); ++j) {
+        const ovl::Geom& g = b->ctx[j]->g;
+        k += "/" + std::to_string(g.L[0]) + "x" + std::to_string(g.L[1]) + "x" + std::to_string(g.L[2]) + "x" +
+             std::to_string(g.L[3]) + "r" + std::to_string(b->nrhs[j]);
+    }
+    for (char& ch : k)
+        if (ch == ' ') ch = '_';
+    return k;
+}
+
+bool tune_lookup(const std::string& key, std::array<int, 3>& out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) {
+        const char* path = std::getenv("OVL_TUNE_CACHE");
+        if (path && *path) {
+            std::ifstream f(path);
+            std::string kk;
+            int a, m, q;
+            while (f >> kk >> a >> m >> q) g_tune[kk] = {a, m, q};
+        }
+        it = g_tune.find(key);
+        if (it == g_tune.end()) return false;
+    }
+    out = it->second;
+    return out[0] >= 0 && out[0] < ovl::NSHAPE && out[1] >= 2 && out[1] <= 6 && (out[2] == 0 || out[2] == 1);
+}
+
+void tune_store(const std::string& key, const std::array<int, 3>& v) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = v;
+    const char* path = std::getenv("OVL_TUNE_CACHE");
+    if (path && *path) {
+        std::ofstream f(path, std::ios::app);
+        f << key << " " << v[0] << " " << v[1] << " " << v[2] << "\n";
+    }
+}
+
 // Autotuner of the batched kernels' launch shapes (site-block size of the pass-1 kernels, blocks
 // per SM of the regeneration kernel): each candidate runs a short eager solve (TUNE_K steps) of the
 // whole batch with events around its phases; the fastest pass-1 and regeneration candidates are
@@ -1441,8 +1497,21 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
     }
     // launch shapes: timed once per batch on its own data (short eager solves), unless OVL_NO_TUNE
     if (!b->pinned && b->tuned_mode != mode && !(flags & OVL_NO_TUNE)) {
-        r = autotune(b, mu, kappa, flags, st);
-        if (r) return r;
+        const std::string key = tune_key(b);
+        std::array<int, 3> v;
+        if (tune_lookup(key, v)) {  // tuned before for this GPU, batch shape and precision
+            b->shape = v[0], b->regen_minb = v[1], b->regen_pair = v[2];
+            b->tuned = true;
+            b->tuned_mode = b->mode;
+            b->tune_cached = true;
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        } else {
+            r = autotune(b, mu, kappa, flags, st);
+            if (r) return r;
+            b->tune_cached = false;
+            tune_store(key, {b->shape, b->regen_minb, b->regen_pair});
+        }
     }
     // the solve, as a graph captured once per (k, flags, mu, kappa); per-phase events need eager launches
     if (flags & OVL_PROFILE) {

@@ -213,8 +213,8 @@ static int ds_grid(const Geom& g) { return (g.V + DS_SITES - 1) / DS_SITES; }
 static bool use_ds(const Geom& g) { return g.V < 152 * 1024; }
 
 // ------------------------------------------------------------ single apply --
-template <int LF>
-__global__ void __launch_bounds__(128, 6) k_dslash(const void* __restrict__ U,
+template <int LF, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_dslash(const void* __restrict__ U,
                                                 const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ x,
                                                 typename VecT<typename LinkReal<LF>::R>::T* __restrict__ y,
                                                 HopCoef<typename LinkReal<LF>::R> hc, int g5, const KState* ks,
@@ -251,16 +251,17 @@ void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, d
                                                                             make_coef<float>(mu, kappa), gamma5, ks, g);
         return;
     }
+    // FP64: four blocks per SM (128 registers: no spills); FP32: eight (64 registers, more loads in flight)
     const int T = 128, B = dslash_grid(g, T);
     if (prec == 0)
-        k_dslash<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)x, (double2*)y, make_coef<double>(mu, kappa),
-                                            gamma5, ks, g);
+        k_dslash<LINK_F64, 4><<<B, T, 0, st>>>(U, (const double2*)x, (double2*)y, make_coef<double>(mu, kappa),
+                                               gamma5, ks, g);
     else if (prec == 1)
-        k_dslash<LINK_F32_12><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
-                                               gamma5, ks, g);
+        k_dslash<LINK_F32_12, 8><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
+                                                  gamma5, ks, g);
     else
-        k_dslash<LINK_F32_18><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
-                                               gamma5, ks, g);
+        k_dslash<LINK_F32_18, 8><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
+                                                  gamma5, ks, g);
 }
 
 // -------------------------------------------------------------- pair apply --

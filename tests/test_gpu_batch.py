@@ -301,3 +301,27 @@ def test_batch_persistent_pass1_equals_stepwise(ovl, mid):
     for r in range(2):
         assert rel(yp[0][r], sgn4 @ ba[r]) < 1e-8
     bt.close()
+
+
+def test_batch_tuning_cache(ovl, small, tmp_path, monkeypatch):
+    """A second batch of the same shape takes the first one's tuned launch shapes from the cache
+    (no timing) and gives bitwise the same result; with OVL_TUNE_CACHE set the choice is also
+    appended to that file for later processes."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("OVL_TUNE_CACHE", str(path))
+    c = _ctx(ovl, small["dims"], small["U"])
+    b = torch_c128(_sources(small["dims"], 4400, 4))  # a batch shape no other test tunes
+    bt = ovl.Batch([c], [4])
+    bt.solve(40, small["mu"], KAPPA, [b], flags=ovl.MIXED)
+    first = bt.tuning()
+    assert first is not None
+    lines = path.read_text().splitlines()
+    assert any(ln.split()[1:] == [str({64: 0, 128: 1, 256: 2}[first[0]]), str(first[1]), str(first[2] - 1)]
+               for ln in lines), (lines, first)
+    bt2 = ovl.Batch([c], [4])
+    y2 = bt2.solve(40, small["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    assert bt2.tuning() == first
+    y1 = bt.solve(40, small["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    assert np.array_equal(y1, y2)
+    bt.close()
+    bt2.close()
