@@ -65,6 +65,7 @@ EPS, SEED_U, SEED_B = 1.0, 1001, 2001
 MU, KAPPA = 0.3, 0.2
 K_GRID = list(range(300, 1001, 50))
 K_REF = 1000
+RS_M, RS_MAX_CYCLES = 100, 16  # restarted Arnoldi extra: steps per cycle, most cycles tried
 DW_DIMS = (48, 48, 48, 64)  # 7.1M sites: every stencil operand is far larger than L2
 NRHS = 12
 WORKLOAD8 = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3, batches of 12 Gaussian b, "
@@ -659,6 +660,28 @@ def gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank):
                   "classical_cgs2_bytes_equivalent_GB_s": round(2 * sweep_bytes / (sweep_ms * 1e6), 1) if sweep_ms else None,
                   "inner_sign_ms": round(aprof.get("inner_sign", {}).get("ms", 0.0), 3),
                   "stencil_ms": round(aprof.get("dslash", {}).get("ms", 0.0), 3)}
+    # restarted Arnoldi: cycles of RS_M steps (a basis of RS_M + 1 double-float vectors instead of
+    # k_adf + 1), the fewest cycles within 1e-8 of the FP64 k = 1000 solve
+    ref1 = ctx.sign_krylov(ovl.LANCZOS2, K_REF, MU, KAPPA, b1)[0].clone()
+    n1 = torch.linalg.vector_norm(ref1).item()
+    rs_cyc, rs_err = None, None
+    for cyc in range(2, RS_MAX_CYCLES + 1):
+        y = ctx.sign_arnoldi_restarted(RS_M, cyc, MU, KAPPA, b1)[0]
+        rs_err = torch.linalg.vector_norm(y - ref1).item() / n1
+        print(f"[bench] calibrate arnoldi_restarted m={RS_M} cycles={cyc} err={rs_err:.3e}", file=sys.stderr,
+              flush=True)
+        if rs_err <= 1e-8:
+            rs_cyc = cyc
+            break
+    rs = {"m": RS_M, "cycles": rs_cyc, "rel_err_vs_k1000_fp64": rs_err,
+          "basis_vectors": RS_M + 1, "basis_vectors_unrestarted": k_adf + 1}
+    if rs_cyc is not None:
+        t_rs = time_solves(torch, ctx, lambda b: ctx.sign_arnoldi_restarted(RS_M, rs_cyc, MU, KAPPA, b, out1,
+                                                                            flags=ovl.OVERLAP), bsingle, 2, nctx, flush)
+        rs.update(ms=statistics.mean(t_rs), solves_per_s=1e3 / statistics.mean(t_rs))
+        if oref is not None:
+            y = ctx.sign_arnoldi_restarted(RS_M, rs_cyc, MU, KAPPA, b1)[0]
+            rs["vs_oracle_source_seed_2001"] = oracle_error(y, oref)
     res = {
         "workload": WORKLOAD8, "deflation_setup": eig,
         "batch_mixed": {"solves_per_s": NRHS * 1e3 / statistics.mean(t_b), "ms_per_batch": statistics.mean(t_b),
@@ -676,6 +699,7 @@ def gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank):
                          "k_ratio_2sl_over_arnoldi": (k_s64 / k_arn) if k_arn else None},
         "arnoldi_doublefloat": {"solves_per_s": 1e3 / statistics.mean(t_adf), "ms": statistics.mean(t_adf),
                                 "k": k_adf, "rel_err_vs_k1000_fp64": err_adf, "gram_schmidt_sweeps": adf_sweeps},
+        "arnoldi_restarted": rs,
         "vs_oracle_source_seed_2001": vs_oracle,
     }
     bt.close()

@@ -233,6 +233,12 @@ __global__ void __launch_bounds__(128, MINB) k_dslash(const void* __restrict__ U
     store_spinor(y, g.V, i, acc[0]);
 }
 
+// blocks per SM of the FP32 single stencil (128 threads each): 6 measured best on GB300 (48^3 x 64:
+// 8 gave 4571 -> 3966 GB/s with 12-real links)
+#ifndef OVL_DSLASH_F32_MINB
+#define OVL_DSLASH_F32_MINB 6
+#endif
+
 static int g_ds_mode = -1;  // -1 auto, 0 one thread per site, 1 direction split
 void set_dslash_variant(int mode) { g_ds_mode = mode; }
 static bool pick_ds(const Geom& g) { return g_ds_mode < 0 ? use_ds(g) : g_ds_mode == 1; }
@@ -251,17 +257,17 @@ void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, d
                                                                             make_coef<float>(mu, kappa), gamma5, ks, g);
         return;
     }
-    // FP64: four blocks per SM (128 registers: no spills); FP32: eight (64 registers, more loads in flight)
+    // FP64: four blocks per SM (128 registers; 80 spilled 1.8 KB); FP32: OVL_DSLASH_F32_MINB per SM
     const int T = 128, B = dslash_grid(g, T);
     if (prec == 0)
         k_dslash<LINK_F64, 4><<<B, T, 0, st>>>(U, (const double2*)x, (double2*)y, make_coef<double>(mu, kappa),
                                                gamma5, ks, g);
     else if (prec == 1)
-        k_dslash<LINK_F32_12, 8><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
-                                                  gamma5, ks, g);
+        k_dslash<LINK_F32_12, OVL_DSLASH_F32_MINB><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y,
+                                                                    make_coef<float>(mu, kappa), gamma5, ks, g);
     else
-        k_dslash<LINK_F32_18, 8><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y, make_coef<float>(mu, kappa),
-                                                  gamma5, ks, g);
+        k_dslash<LINK_F32_18, OVL_DSLASH_F32_MINB><<<B, T, 0, st>>>(U, (const float4*)x, (float4*)y,
+                                                                    make_coef<float>(mu, kappa), gamma5, ks, g);
 }
 
 // -------------------------------------------------------------- pair apply --
