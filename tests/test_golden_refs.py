@@ -25,10 +25,13 @@ def test_every_case_present_and_converged():
         assert float(r["selfdiff"]) < 1e-11, (name, float(r["selfdiff"]))
         N = 12 * int(np.prod(dims))
         assert len(r["idx"]) == 4096 and r["idx"].max() < N and np.all(np.diff(r["idx"]) > 0)
-        # sampled values are a part of a vector of the stored norm: the mean square agrees within
-        # the sampling spread
-        ms = np.mean(np.abs(r["val"]) ** 2) * N
-        assert 0.5 < ms / float(r["norm"]) ** 2 < 2.0, name
+        # the sampled values are a part of a vector of the stored norm
+        assert np.sum(np.abs(r["val"]) ** 2) <= float(r["norm"]) ** 2 * (1 + 1e-12), name
+        if str(r["source_kind"]) == "gauss":
+            # spread over the lattice (a point source's result is concentrated near its site):
+            # the mean square agrees within the sampling spread
+            ms = np.mean(np.abs(r["val"]) ** 2) * N
+            assert 0.5 < ms / float(r["norm"]) ** 2 < 2.0, name
 
 
 def test_projections_bounded_by_cauchy_schwarz():
