@@ -169,3 +169,32 @@ def test_large_lattice_sampled(ovl, layout):
         ref = W.wilson_site(U, dims, mu, KAPPA, x, int(site))
         np.testing.assert_allclose(y[12 * site:12 * site + 12], ref, atol=1e-13)
         np.testing.assert_allclose(y32[12 * site:12 * site + 12], ref, atol=3e-5)
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16, 48), (20, 14, 16, 48)])
+def test_row_grouped_traversal_sampled(ovl, dims):
+    """Lattices whose (x0, x1) rows are whole 64-site blocks take the row-grouped block order of the
+    single stencil (groups of x1 rows, x0 inside a group): 16^3 x 48 (groups of 16 rows) and
+    20 x 14 x 16 x 48 (one group of 14).  Sampled sites, among them the first and last of rows and
+    of the lattice, of the FP64, FP32-12 and FP32-18 stencils against the oracle's single-site
+    evaluator; the one-thread-per-site and direction-split layouts agree."""
+    mu = 0.3
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    U = synth.gauge_field(dims, 1.0, 31)
+    x = synth.gaussian_source(dims, 32)
+    ctx = ovl.Context(dims)
+    ctx.set_gauge(torch_c128(U))
+    xs = torch_c128(x)
+    y = ctx.apply_Dw(mu, KAPPA, xs, flags=ovl.GAMMA5 | ovl.STENCIL_SITE).cpu().numpy()
+    ys = ctx.apply_Dw(mu, KAPPA, xs, flags=ovl.GAMMA5 | ovl.STENCIL_SPLIT).cpu().numpy()
+    assert maxrel(y, ys) < 1e-14
+    y12 = ctx.apply_Dw(mu, KAPPA, xs, flags=ovl.GAMMA5 | ovl.F32 | ovl.STENCIL_SITE).cpu().numpy()
+    y18 = ctx.apply_Dw(mu, KAPPA, xs, flags=ovl.GAMMA5 | ovl.F32_FULL | ovl.STENCIL_SITE).cpu().numpy()
+    row = dims[2] * dims[3]
+    rng = np.random.default_rng(33)
+    sites = [0, 1, row - 1, row, V // 2 - 1, V // 2, V - row, V - 1] + list(rng.integers(0, V, 8))
+    for site in sites:
+        ref = W.wilson_site(U, dims, mu, KAPPA, x, int(site))
+        np.testing.assert_allclose(y[12 * site:12 * site + 12], ref, atol=1e-13)
+        np.testing.assert_allclose(y12[12 * site:12 * site + 12], ref, atol=3e-5)
+        np.testing.assert_allclose(y18[12 * site:12 * site + 12], ref, atol=3e-5)
