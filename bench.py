@@ -75,6 +75,9 @@ C3_DIMS, C3_SEED_U, C3_SEED_B, C3_MU, C3_M = (16, 16, 16, 8), 1002, 2002, 0.3, 3
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the headline batch's dominant kernel
 # class, from one ncu capture of the current kernels (the roofline's "traffic"); None until measured
 HEAD_TRAFFIC = {"pass2_batched_doublefloat": 715643648}  # k_b_regen, 48 sequences (profiles/)
+# ncu dram__bytes_read + write per launch of the single stencil on 48^3 x 64 (row-grouped block order;
+# profiles/stencil_dslash_48x48x48x64_and_32x32x32x64.md)
+DW_TRAFFIC = {"f32_12": 2.970e9, "f32_18": 3.625e9, "f64": 9.75e9}
 
 
 def peaks():
@@ -445,12 +448,23 @@ def autograd_timing(torch, ovl, U_np, b, flush, k=800, gdims=(24, 24, 24, 24)):
         gU = torch.empty((lat.V, 4, 3, 3), dtype=torch.complex128, device="cuda")
         gb, y = torch.empty_like(bb), torch.empty_like(bb)
         t_grad = timed(lambda: lat.sign_grad(k, MU, KAPPA, bb, g, y=y, grad_U=gU, grad_b=gb), 3)
+        gm64 = lat.sign_grad(k, MU, KAPPA, bb, g, y=y, grad_U=gU, grad_b=gb)[0]
+        gU64, gb64 = gU.clone(), gb.clone()
+        t_mix = timed(lambda: lat.sign_grad(k, MU, KAPPA, bb, g, y=y, grad_U=gU, grad_b=gb, flags=ovl.MIXED), 3)
+        gmm = lat.sign_grad(k, MU, KAPPA, bb, g, y=y, grad_U=gU, grad_b=gb, flags=ovl.MIXED)[0]
         t_fwd = timed(lambda: lat.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, bb, y), 3)
+
+        def rel(a, r):
+            return (torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r)).item()
         out["sign_grad_8x4"] = {"k": k, "ms": round(t_grad, 3), "forward_fp64_ms": round(t_fwd, 3),
                                 "ratio_to_forward": round(t_grad / t_fwd, 2),
-                                "outputs": "sgn(A) b, grad_U, grad_mu, grad_b"}
+                                "outputs": "sgn(A) b, grad_U, grad_mu, grad_b",
+                                "mixed": {"ms": round(t_mix, 3), "ratio_to_forward": round(t_mix / t_fwd, 2),
+                                          "rel_diff_vs_fp64": {"grad_U": rel(gU, gU64), "grad_b": rel(gb, gb64),
+                                                               "grad_mu": abs(gmm - gm64) / abs(gm64)},
+                                          "form": "FP32 Lanczos, double-float combination"}}
         lat.close()
-        del gU, gb, y, g, bb
+        del gU, gb, y, g, bb, gU64, gb64
     except Exception as exc:  # report, keep the rest of the line
         out["sign_grad_8x4"] = {"error": repr(exc)[:200]}
     try:
@@ -463,7 +477,8 @@ def autograd_timing(torch, ovl, U_np, b, flush, k=800, gdims=(24, 24, 24, 24)):
         gg = torch.randn(V2 * 12, dtype=torch.complex128, device="cuda")
         gU2 = torch.empty((V2, 4, 3, 3), dtype=torch.complex128, device="cuda")
         ms = timed(lambda: lat2.dw_grad(MU, KAPPA, x, gg, gU2), 10)
-        out["dw_grad"] = {"dims": list(gdims), "sites": V2, "ms": round(ms, 4),
+        ms32 = timed(lambda: lat2.dw_grad(MU, KAPPA, x, gg, gU2, flags=ovl.F32), 10)
+        out["dw_grad"] = {"dims": list(gdims), "sites": V2, "ms": round(ms, 4), "ms_f32": round(ms32, 4),
                           "GB_s": round(DWGRAD_BYTES_SITE * V2 / ms / 1e6, 1),
                           "GFLOP_s": round(DWGRAD_FLOP_SITE * V2 / ms / 1e6, 1),
                           "frac_fp64_roof": round(DWGRAD_FLOP_SITE * V2 / ms / 1e9 / FP64_PEAK_TFLOPS, 3),
@@ -923,6 +938,9 @@ def run_ours(args, world, rank, local):
                       "GFLOP_s": round(r["GFLOP_s"], 1)}
             if nm == "f64":
                 dw[nm]["frac_fp64_roof"] = round(r["GFLOP_s"] / (FP64_PEAK_TFLOPS * 1e3), 3)
+            if tuple(ddims) == DW_DIMS:
+                dw[nm]["traffic"] = DW_TRAFFIC[nm]
+                dw[nm]["traffic_over_algorithmic"] = round(DW_TRAFFIC[nm] / (DW_BYTES[nm] * dV), 3)
         dw["hbm_peak_gbs"] = hbm_peak
 
     cpu = None
