@@ -219,9 +219,11 @@ __device__ __forceinline__ void* vslot(const BSeq& q, int j, bool wvec) {
 // thread carries one accumulator spinor instead of two (fewer registers: more warps per SM).
 // The last step's s (i = klast) is not used, so the y = 1 blocks may skip it once the sequence
 // is marked done.
+// The FP32 form is compiled for 768 resident threads per SM (at most 80 registers): measured on the
+// 48-sequence batch, pass 1 137.1 -> 134.3 ms (64-site blocks) and 145.4 -> 134.7 ms (128).
 template <int LF, class R, int SH>
-__global__ void __launch_bounds__(SHAPE_SITES[SH]) k_b_pair(const BSeq* __restrict__ S, const int* __restrict__ bseq, int i,
-                                               int klast, HopCoef<R> hv, HopCoef<R> hw) {
+__global__ void __launch_bounds__(SHAPE_SITES[SH], LF == LINK_F64 ? 1 : 768 / SHAPE_SITES[SH]) k_b_pair(
+    const BSeq* __restrict__ S, const int* __restrict__ bseq, int i, int klast, HopCoef<R> hv, HopCoef<R> hw) {
     using VT = typename BVec<R>::T;
     const BSeq& q = S[bseq[blockIdx.x]];  // set-up data, not written by the solve
     KState* ks = q.ks;

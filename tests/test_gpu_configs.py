@@ -61,6 +61,9 @@ def test_8x4_deflated_arnoldi_and_lanczos2(ovl, mu):
     ya = ctx.sign_krylov(ovl.ARNOLDI, kk, mu, KAPPA, b)[0].clone()
     ym = ctx.sign_krylov(ovl.LANCZOS2, kk, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
     yad = ctx.sign_krylov(ovl.ARNOLDI, kk, mu, KAPPA, b, flags=ovl.MIXED)[0].clone()
+    # restarted Arnoldi, cycles of 100 steps (101 basis vectors), as many steps in all
+    yr, rinfo = ctx.sign_arnoldi_restarted(100, kk // 100, mu, KAPPA, b)
+    assert rinfo["status"] == 0 and rinfo["k_used"] == kk
     assert rel(y2.cpu().numpy(), ya.cpu().numpy()) < 1e-9
     assert rel(ym.cpu().numpy(), y2.cpu().numpy()) < 1e-8
     # double-float Arnoldi: the FP64 Arnoldi process at 48-bit precision
@@ -70,7 +73,7 @@ def test_8x4_deflated_arnoldi_and_lanczos2(ovl, mu):
     ref = oracle_refs()[f"gauss8_mu{mu}"]
     assert ref["selfdiff"] < 1e-11 and ref["eig_residual"] < 1e-12
     for y, tol, what in ((y2, 1e-10, "2sL FP64"), (ya, 1e-10, "Arnoldi FP64"), (yad, 1e-10, "Arnoldi double-float"),
-                         (ym, 1e-8, "2sL mixed")):
+                         (ym, 1e-8, "2sL mixed"), (yr, 1e-10 if mu < 0.5 else 1e-9, "restarted Arnoldi")):
         d = assert_oracle_close(y.cpu().numpy(), ref, tol, what)
         print(f"8^4 mu={mu} {what} vs oracle: sampled rel {d[0]:.2e}, max {d[1]:.2e}, projected {d[2]:.2e}")
     # sgn(A)^2 b = b
