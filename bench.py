@@ -794,6 +794,23 @@ def run_ours(args, world, rank, local):
         print(json.dumps({"dw_only": True, "dims": list(ddims), "sites": dV,
                           **{nm: {"ms": r["ms"], "GB_s": r["GB_s"]} for nm, r in dres.items()}}))
         return
+    if args.arnoldi_only:
+        # single-source Arnoldi with the double-float basis on the 8^4 workload (for profiler
+        # captures of its Gram-Schmidt sweeps): `--steps` solves at `--k` (default 450), `--m` deflated
+        ovl.load()
+        ctx = ovl.Context(DIMS)
+        ctx.set_gauge(torch.from_numpy(synth.gauge_field(DIMS, EPS, SEED_U)).cuda())
+        if args.m > 0:
+            ctx.deflation_eigs(MU, KAPPA, args.m)
+        b = torch.from_numpy(synth.gaussian_source(DIMS, SEED_B)).cuda()
+        y = torch.empty_like(b)
+        ka = args.k or 450
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        t = time_solves(torch, ctx, lambda bb: ctx.sign_krylov(ovl.ARNOLDI, ka, MU, KAPPA, bb, y,
+                                                               flags=ovl.MIXED | ovl.OVERLAP), [b], args.warmup,
+                        args.steps, flush)
+        print(json.dumps({"arnoldi_only": True, "k": ka, "m": args.m, "ms": statistics.mean(t)}))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -1032,6 +1049,8 @@ def main():
     ap.add_argument("--dw-dims", default="", help="lattice of the stencil bandwidth measurement, e.g. 32,32,32,32")
     ap.add_argument("--profile-one", action="store_true",
                     help="with --solves-only: one extra solve inside cudaProfilerStart/Stop (for ncu)")
+    ap.add_argument("--arnoldi-only", action="store_true",
+                    help="only single-source double-float Arnoldi solves on 8^4 (for profiler captures)")
     ap.add_argument("--solves-only", action="store_true",
                     help="only the timed headline solves (for profiler captures): needs --k, skips calibration, "
                          "profile, e2e, extras, the bandwidth lattice and the CPU baseline")
