@@ -278,6 +278,22 @@ def dw_bandwidth(torch, ovl, reps=20, dims=DW_DIMS):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms": ms, "GB_s": DW_BYTES[name] * V / ms / 1e6, "GFLOP_s": DW_FLOP_SITE * V / ms / 1e6}
+        if name == "f32_12":
+            # the fused pair t = A v, s = A^dag w with alpha = w^dag t (12-real links read once for both:
+            # 576 B/site); each call ends with the host read of alpha, which the timing includes
+            w = ctx.empty_native(1)
+            w.copy_(torch.randn(ctx.n, dtype=torch.complex64, device="cuda"))
+            t, s = ctx.empty_native(1), ctx.empty_native(1)
+            for _ in range(3):
+                ctx.apply_pair(MU, KAPPA, x, w, t, s, prec=1)
+            e0.record(st)
+            for _ in range(reps):
+                ctx.apply_pair(MU, KAPPA, x, w, t, s, prec=1)
+            e1.record(st)
+            e1.synchronize()
+            msp = e0.elapsed_time(e1) / reps
+            res["pair_f32_12"] = {"ms": msp, "GB_s": 576 * V / msp / 1e6, "GFLOP_s": 2 * DW_FLOP_SITE * V / msp / 1e6}
+            del w, t, s
         del x, y
     ctx.close()
     torch.cuda.empty_cache()
@@ -981,7 +997,7 @@ def run_ours(args, world, rank, local):
                       "GFLOP_s": round(r["GFLOP_s"], 1)}
             if nm == "f64":
                 dw[nm]["frac_fp64_roof"] = round(r["GFLOP_s"] / (FP64_PEAK_TFLOPS * 1e3), 3)
-            if tuple(ddims) == DW_DIMS:
+            if tuple(ddims) == DW_DIMS and nm in DW_TRAFFIC:
                 dw[nm]["traffic"] = DW_TRAFFIC[nm]
                 dw[nm]["traffic_over_algorithmic"] = round(DW_TRAFFIC[nm] / (DW_BYTES[nm] * dV), 3)
         dw["hbm_peak_gbs"] = hbm_peak

@@ -329,27 +329,41 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
 // may then run a finalisation step.
 template <int NV>
 __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* counter,
-                                              double* out, double* smem) {
+                                              double* out, double* smem, unsigned int blk, unsigned int nblk) {
     block_sum<NV>(v, smem);
     __shared__ bool last;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)j * gridDim.x + blockIdx.x] = v[j];
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * nblk + blk] = v[j];
         __threadfence();
         unsigned int t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == nblk - 1);
     }
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    // sum partials in a fixed order: thread-strided then tree within block
+    // sum partials in a fixed order: thread-strided then tree within block; the loads of UB
+    // strides are issued together (NV x UB in flight per thread) and then added in the same order
+    constexpr int UB = NV <= 2 ? 8 : 4;
     double acc[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        acc[j] = 0.0;
-        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-            acc[j] += __ldcg(partials + (size_t)j * gridDim.x + b);
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+    const unsigned int bs = blockDim.x;
+    unsigned int b = threadIdx.x;
+    for (; b + (UB - 1) * bs < nblk; b += UB * bs) {
+        double x[NV][UB];
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+#pragma unroll
+            for (int u = 0; u < UB; ++u) x[j][u] = __ldcg(partials + (size_t)j * nblk + b + u * bs);
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+#pragma unroll
+            for (int u = 0; u < UB; ++u) acc[j] += x[j][u];
     }
+    for (; b < nblk; b += bs)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] += __ldcg(partials + (size_t)j * nblk + b);
     block_sum<NV>(acc, smem);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -358,6 +372,12 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials,
     }
     __syncthreads();
     return true;
+}
+// the same over a one-dimensional grid (block blockIdx.x of gridDim.x)
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned int* counter,
+                                              double* out, double* smem) {
+    return grid_sum_last<NV>(v, partials, counter, out, smem, blockIdx.x, gridDim.x);
 }
 
 // Bounded grid barrier for cooperative launches.  `bar` points to two

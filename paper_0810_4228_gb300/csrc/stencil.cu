@@ -56,13 +56,17 @@ static RowGrid row_grid(const Geom& g, int threads) {
     return {true, dim3(row / half, gx, (unsigned)z)};
 }
 
-__device__ __forceinline__ int site_of_thread_rows(const Geom& g) {
+// block bx of nx within its row
+__device__ __forceinline__ int site_of_rows(const Geom& g, int bx, int nx) {
     const int half = blockDim.x >> 1;
     const int par = threadIdx.x >= half;
     const int x0 = blockIdx.z % g.L[0];
     const int x1 = (blockIdx.z / g.L[0]) * gridDim.y + blockIdx.y;
-    const int cb = ((x0 * g.L[1] + x1) * (int)gridDim.x + blockIdx.x) * half + (threadIdx.x - par * half);
+    const int cb = ((x0 * g.L[1] + x1) * nx + bx) * half + (threadIdx.x - par * half);
     return par * g.Vh + cb;
+}
+__device__ __forceinline__ int site_of_thread_rows(const Geom& g) {
+    return site_of_rows(g, blockIdx.x, gridDim.x);
 }
 
 // --------------------------------------------- direction-split variants --
@@ -322,8 +326,12 @@ void launch_dslash(const void* U, int prec, const void* x, void* y, double mu, d
 // -------------------------------------------------------------- pair apply --
 // t = sv * gamma5 D_w(mu) v~,  s = sw * gamma5 D_w(-mu) w~,  alpha[step] = w^dag t
 // with w = sw w~.  Skipped (uniformly) once the solve is done or failed.
-template <int LF>
-__global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
+// The two stencils go to two sets of blocks (which = 0: t and the alpha partials; 1: s), so a thread
+// carries one accumulator spinor (half the registers: more warps per SM); which is blockIdx.y on a
+// one-dimensional grid, the low bit of blockIdx.x on the row-grouped grid.  Only the t blocks take
+// part in the reduction.
+template <int LF, bool ROWS>
+__global__ void __launch_bounds__(128, LF == LINK_F64 ? 2 : OVL_DSLASH_F32_MINB) k_dslash_pair(const void* __restrict__ U,
                                                      const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ v,
                                                      const typename VecT<typename LinkReal<LF>::R>::T* __restrict__ w,
                                                      typename VecT<typename LinkReal<LF>::R>::T* __restrict__ t,
@@ -336,26 +344,40 @@ __global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
     __shared__ double red[3 * 32];  // grid_sum_last<3>: 32 doubles per value
     if (ks->done || ks->status) return;
     const double2 sv = ks->sv, sw = ks->sw;
-    const int i = site_of_thread(g);
+    const int which = ROWS ? (int)(blockIdx.x & 1u) : (int)blockIdx.y;
+    const int i = ROWS ? site_of_rows(g, blockIdx.x >> 1, gridDim.x >> 1) : site_of_thread(g);
+    if (which == 1) {  // s = sw A^dag w~
+        if (i >= 0) {
+            const typename VecT<R>::T* const xs[1] = {w};
+            Spinor<R> acc[1], self;
+            const HopCoef<R> hcs[1] = {hw};
+            apply_site<LF, R, 1>(g, i, U, xs, acc, hcs);
+            load_spinor(w, g.V, i, self);
+            finish_site(acc[0], self, true);
+            const cx<R> csw = mk(R(sw.x), R(sw.y));
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[0].s[sp][a] = csw * acc[0].s[sp][a];
+            store_spinor(s, g.V, i, acc[0]);
+        }
+        return;
+    }
     double part[3] = {0.0, 0.0, 0.0};
-    if (i >= 0) {
-        const typename VecT<R>::T* const xs[2] = {v, w};
-        Spinor<R> acc[2];
-        const HopCoef<R> hcs[2] = {hv, hw};
-        apply_site<LF, R, 2>(g, i, U, xs, acc, hcs);
-        Spinor<R> self;
+    if (i >= 0) {  // t = sv A v~, partials of w~^dag t and |t|^2
+        const typename VecT<R>::T* const xs[1] = {v};
+        Spinor<R> acc[1], self;
+        const HopCoef<R> hcs[1] = {hv};
+        apply_site<LF, R, 1>(g, i, U, xs, acc, hcs);
         load_spinor(v, g.V, i, self);
         finish_site(acc[0], self, true);
         load_spinor(w, g.V, i, self);
-        finish_site(acc[1], self, true);
-        // scale by the (complex) normalisation of v~, w~
-        const cx<R> csv = mk(R(sv.x), R(sv.y)), csw = mk(R(sw.x), R(sw.y));
+        const cx<R> csv = mk(R(sv.x), R(sv.y));
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 acc[0].s[sp][a] = csv * acc[0].s[sp][a];
-                acc[1].s[sp][a] = csw * acc[1].s[sp][a];
                 // w~^dag t in FP64
                 cx<double> z = cdot(up(self.s[sp][a]), up(acc[0].s[sp][a]));
                 part[0] += z.r;
@@ -363,10 +385,13 @@ __global__ void __launch_bounds__(256) k_dslash_pair(const void* __restrict__ U,
                 part[2] += norm2(up(acc[0].s[sp][a]));
             }
         store_spinor(t, g.V, i, acc[0]);
-        store_spinor(s, g.V, i, acc[1]);
     }
     double out[3];
-    if (grid_sum_last<3>(part, partials, counter, out, red)) {
+    const unsigned nx = ROWS ? gridDim.x >> 1 : gridDim.x;
+    const unsigned bx = ROWS ? blockIdx.x >> 1 : blockIdx.x;
+    const unsigned blk = ROWS ? bx + nx * (blockIdx.y + gridDim.y * blockIdx.z) : bx;
+    const unsigned nblk = ROWS ? nx * gridDim.y * gridDim.z : nx;
+    if (grid_sum_last<3>(part, partials, counter, out, red, blk, nblk)) {
         if (threadIdx.x == 0) {
             // alpha = w^dag t = conj(sw) * (w~^dag t)
             cx<double> a = cdot(d2c(sw), mk(out[0], out[1]));
@@ -400,15 +425,31 @@ void launch_dslash_pair(const void* U, int prec, const void* v, const void* w, v
                 make_coef<float>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
         return;
     }
+    // large lattices: the row-grouped block order of the single stencil (same block count, so the
+    // same partial-sum slots; the partials are summed in linear block order)
     const int T = 128;
-    if (prec == 0)
-        k_dslash_pair<LINK_F64><<<B, T, 0, st>>>(U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s,
-                                                 make_coef<double>(mu, kappa), make_coef<double>(-mu, kappa), ks,
-                                                 alpha, step, klast, partials, counter, g);
-    else
-        k_dslash_pair<LINK_F32_12><<<B, T, 0, st>>>(U, (const float4*)v, (const float4*)w, (float4*)t, (float4*)s,
-                                                    make_coef<float>(mu, kappa), make_coef<float>(-mu, kappa), ks,
-                                                    alpha, step, klast, partials, counter, g);
+    RowGrid rg = row_grid(g, T);
+    rg.grid.x *= 2;  // the two stencils
+    const dim3 g1(B, 2);
+    if (prec == 0) {
+        if (rg.ok)
+            k_dslash_pair<LINK_F64, true><<<rg.grid, T, 0, st>>>(
+                U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s, make_coef<double>(mu, kappa),
+                make_coef<double>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
+        else
+            k_dslash_pair<LINK_F64, false><<<g1, T, 0, st>>>(
+                U, (const double2*)v, (const double2*)w, (double2*)t, (double2*)s, make_coef<double>(mu, kappa),
+                make_coef<double>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
+    } else {
+        if (rg.ok)
+            k_dslash_pair<LINK_F32_12, true><<<rg.grid, T, 0, st>>>(
+                U, (const float4*)v, (const float4*)w, (float4*)t, (float4*)s, make_coef<float>(mu, kappa),
+                make_coef<float>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
+        else
+            k_dslash_pair<LINK_F32_12, false><<<g1, T, 0, st>>>(
+                U, (const float4*)v, (const float4*)w, (float4*)t, (float4*)s, make_coef<float>(mu, kappa),
+                make_coef<float>(-mu, kappa), ks, alpha, step, klast, partials, counter, g);
+    }
 }
 
 // ------------------------------------------------------ two-pass regeneration --

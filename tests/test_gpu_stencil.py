@@ -198,3 +198,39 @@ def test_row_grouped_traversal_sampled(ovl, dims):
         np.testing.assert_allclose(y[12 * site:12 * site + 12], ref, atol=1e-13)
         np.testing.assert_allclose(y12[12 * site:12 * site + 12], ref, atol=3e-5)
         np.testing.assert_allclose(y18[12 * site:12 * site + 12], ref, atol=3e-5)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-14), (1, 3e-6)])
+def test_pair_row_grouped_large(ovl, prec, tol):
+    """The fused pair on a lattice that takes the row-grouped block order (16^3 x 48): t = A v and
+    s = A^dag w against the single stencil (itself checked against the oracle there) and at
+    sampled sites against the oracle's single-site evaluator; alpha = w^dag t (reduced over the
+    three-dimensional grid in linear block order) against torch's FP64 inner product of the
+    results."""
+    import torch
+    dims, mu = (16, 16, 16, 48), 0.3
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    U = synth.gauge_field(dims, 1.0, 41)
+    v = synth.gaussian_source(dims, 42)
+    w = synth.gaussian_source(dims, 43)
+    ctx = ovl.Context(dims)
+    ctx.set_gauge(torch_c128(U))
+    nv, nw = ctx.empty_native(prec), ctx.empty_native(prec)
+    ctx.pack(torch_c128(v), nv, prec)
+    ctx.pack(torch_c128(w), nw, prec)
+    t, s = ctx.empty_native(prec), ctx.empty_native(prec)
+    alpha = ctx.apply_pair(mu, KAPPA, nv, nw, t, s, prec)
+    tc = torch.empty(ctx.n, dtype=torch.complex128, device="cuda")
+    sc = torch.empty_like(tc)
+    ctx.unpack(t, tc, prec)
+    ctx.unpack(s, sc, prec)
+    tr = ctx.apply_Dw(mu, KAPPA, torch_c128(v), flags=ovl.GAMMA5)
+    sr = ctx.apply_Dw(mu, KAPPA, torch_c128(w), flags=ovl.DAGGER)
+    assert maxrel(tc.cpu().numpy(), tr.cpu().numpy()) < tol
+    assert maxrel(sc.cpu().numpy(), sr.cpu().numpy()) < tol
+    ar = torch.vdot(torch_c128(w), tc).item()
+    assert abs(alpha - ar) / abs(ar) < (1e-12 if prec == 0 else 1e-5)
+    t_np = tc.cpu().numpy()
+    for site in (0, V // 2 + 7, V - 1):
+        ref = W.wilson_site(U, dims, mu, KAPPA, v, site)
+        np.testing.assert_allclose(t_np[12 * site:12 * site + 12], ref, atol=1e-13 if prec == 0 else 3e-5)
