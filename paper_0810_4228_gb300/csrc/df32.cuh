@@ -198,4 +198,38 @@ __device__ __forceinline__ void load_link_df(const dfc* __restrict__ U, int V, i
     }
 }
 
+// in-block accumulators: compensated FP32 pairs for FP32 data, plain FP64 for FP64 data
+struct AccF {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void acc_add(AccF& a, float p, float pe) {
+    const float s = __fadd_rn(a.hi, p);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ void acc_prod(AccF& a, float x, float y, float sg = 1.f) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    acc_add(a, sg * p, sg * pe);
+}
+struct AccD {
+    double v = 0.0;
+};
+__device__ __forceinline__ void acc_prod(AccD& a, double x, double y, double sg = 1.0) { a.v += sg * x * y; }
+
+template <class A, class R>
+__device__ __forceinline__ void acc_cdot(A* a, cx<R> x, cx<R> y) {  // += conj(x) y
+    acc_prod(a[0], x.r, y.r);
+    acc_prod(a[0], x.i, y.i);
+    acc_prod(a[1], x.r, y.i);
+    acc_prod(a[1], x.i, y.r, R(-1));
+}
+template <class A, class R>
+__device__ __forceinline__ void acc_norm2(A& a, cx<R> x) {
+    acc_prod(a, x.r, x.r);
+    acc_prod(a, x.i, x.i);
+}
+
 }  // namespace ovl

@@ -16,6 +16,7 @@
 // The e^{+-mu} factors, kappa and the antiperiodic time phase are applied as
 // real scalars to the projected half spinor, so links stay in SU(3).
 #include <algorithm>
+#include <type_traits>
 
 #include "stencil_impl.cuh"
 
@@ -363,7 +364,10 @@ __global__ void __launch_bounds__(128, LF == LINK_F64 ? 2 : OVL_DSLASH_F32_MINB)
         }
         return;
     }
-    double part[3] = {0.0, 0.0, 0.0};
+    // per-thread sums: FP64 for FP64 data; for FP32 data exact FP32 products summed as compensated
+    // FP32 pairs (TwoSum) on the FP32 pipe, widened to FP64 for the block and grid sums
+    using A = typename std::conditional<sizeof(R) == 4, AccF, AccD>::type;
+    A pa[3];
     if (i >= 0) {  // t = sv A v~, partials of w~^dag t and |t|^2
         const typename VecT<R>::T* const xs[1] = {v};
         Spinor<R> acc[1], self;
@@ -378,13 +382,16 @@ __global__ void __launch_bounds__(128, LF == LINK_F64 ? 2 : OVL_DSLASH_F32_MINB)
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 acc[0].s[sp][a] = csv * acc[0].s[sp][a];
-                // w~^dag t in FP64
-                cx<double> z = cdot(up(self.s[sp][a]), up(acc[0].s[sp][a]));
-                part[0] += z.r;
-                part[1] += z.i;
-                part[2] += norm2(up(acc[0].s[sp][a]));
+                acc_cdot(pa, self.s[sp][a], acc[0].s[sp][a]);  // w~^dag t
+                acc_norm2(pa[2], acc[0].s[sp][a]);
             }
         store_spinor(t, g.V, i, acc[0]);
+    }
+    double part[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if constexpr (sizeof(R) == 4) part[j] = (double)pa[j].hi + (double)pa[j].lo;
+        else part[j] = pa[j].v;
     }
     double out[3];
     const unsigned nx = ROWS ? gridDim.x >> 1 : gridDim.x;
