@@ -50,11 +50,11 @@ METRIC = "sgn(γ5Dw(μ))b solves/s at 1e-8 rel err, mixed vs FP64; Dw GB/s vs HB
 HEAD_DIMS = [(6, 6, 6, 6), (8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 8)]
 HEAD_SEEDS = [1003, 1004, 1005, 1006]
 HEAD_MU, HEAD_M = 0.2, 20
-HEAD_K_GRID = list(range(400, 1001, 50))
+HEAD_K_GRID = list(range(400, 1001, 10))
 HEAD_K_REF = 1500
 # Krylov size of the reference arm (the driver runs it before this arm, so it cannot read this
 # arm's calibration): the k the calibration below chose on GB300 for the headline batch
-REF_K_DEFAULT = 550
+REF_K_DEFAULT = 480
 HEAD_WORKLOAD = ("12 spin-colour point sources x 4 lattices {6^4, 8^4, 12^4, 16^3x8} (48 sequences, "
                  "58896 sites), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.2, batched two-sided Lanczos, "
                  "20 eigenvalues of smallest |Re lambda| deflated per lattice")
