@@ -63,7 +63,7 @@ ORACLE_REFS = os.path.join(ROOT, "tests", "golden", "oracle_refs.npz")
 DIMS = (8, 8, 8, 8)
 EPS, SEED_U, SEED_B = 1.0, 1001, 2001
 MU, KAPPA = 0.3, 0.2
-K_GRID = list(range(300, 1001, 50))
+K_GRID = list(range(300, 1001, 10))
 K_REF = 1000
 RS_M, RS_MAX_CYCLES = 60, 24  # restarted Arnoldi extra: steps per cycle (fastest of 40-200 at 8^4), most cycles
 OV_NEV = 6  # eigenvalues of D_ov nearest 0 in the 8^4 extras
@@ -631,7 +631,7 @@ def gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank):
     cal = calibrate_k(ovl, ctx, torch, b1, [("mixed", ovl.MIXED), ("fp64", 0)])
     (k_s, err_s), (k_s64, err_s64) = cal["mixed"], cal["fp64"]
     cal_a = calibrate_k(ovl, ctx, torch, b1, [("arnoldi", 0, ovl.ARNOLDI), ("arnoldi_df", ovl.MIXED, ovl.ARNOLDI)],
-                        grid=list(range(250, 801, 25)))
+                        grid=list(range(250, 801, 10)))
     (k_arn, err_arn), (k_adf, err_adf) = cal_a["arnoldi"], cal_a["arnoldi_df"]
     vs_oracle = None
     if oref is not None:
@@ -767,7 +767,7 @@ def gauss8_extras(torch, ovl, args, flush, orefs, hbm_peak, rank):
 
 def config3_extra(torch, ovl, flush, steps):
     """16^3 x 8, mu = 0.3, 30 deflated eigenpairs: single-source mixed precision at the smallest k
-    on a grid (step 50, at most 800) within 1e-8 of the FP64 k = 1200 solve, against FP64 at its own
+    on a grid (step 10, at most 800) within 1e-8 of the FP64 k = 1200 solve, against FP64 at its own
     calibrated k; the error of each stated against the FP64 reference."""
     from paper_0810_4228_gb300 import synth
     ctx = ovl.Context(C3_DIMS)
@@ -782,7 +782,7 @@ def config3_extra(torch, ovl, flush, steps):
            "reference": "FP64 two-sided Lanczos, k = 1200"}
     for name, fl in (("mixed", ovl.MIXED), ("fp64", 0)):
         chosen, err = 800, None
-        for k in range(400, 801, 50):
+        for k in range(400, 801, 10):
             y = ctx.sign_krylov(ovl.LANCZOS2, k, C3_MU, KAPPA, b, flags=fl)[0]
             err = torch.linalg.vector_norm(y - ref).item() / nrm
             if err <= 1e-8:
