@@ -75,7 +75,7 @@ WORKLOAD8 = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3,
 C3_DIMS, C3_SEED_U, C3_SEED_B, C3_MU, C3_M = (16, 16, 16, 8), 1002, 2002, 0.3, 30
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the headline batch's dominant kernel
 # class, from one ncu capture of the current kernels (the roofline's "traffic"); None until measured
-HEAD_TRAFFIC = {"pass2_batched_doublefloat": 715643648}  # k_b_regen, 48 sequences (profiles/)
+HEAD_TRAFFIC = {"pass2_batched_doublefloat": 734946413}  # k_b_regen, 48 sequences, mean of 479 launches (profiles/)
 # ncu dram__bytes_read + write per launch of the single stencil on 48^3 x 64 (row-grouped block order;
 # profiles/stencil_dslash_48x48x48x64_and_32x32x32x64.md)
 DW_TRAFFIC = {"f32_12": 2.970e9, "f32_18": 3.625e9, "f64": 9.75e9}
