@@ -68,6 +68,9 @@ def test_batch_launch_count_matches_the_launch_list():
     # without deflation the two projection pairs go, with the stepwise pass 1 it is 2k - 1 launches
     assert bench.batch_launches(12, 550, 0) == 755 - 12 * 4
     assert bench.batch_launches(12, 550, 20, persistent_pass1=False) == 755 - 1 + (2 * 550 - 1)
+    # the launch list of one 48-sequence headline batch at k = 480 without deflation (stepwise pass 1:
+    # its 128-site blocks exceed one resident grid) counts 2027 launches
+    assert bench.headline_launches(480, m=0) == 2027
 
 
 def test_measured_peaks_lookup(tmp_path, monkeypatch):
