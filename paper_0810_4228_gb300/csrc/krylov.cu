@@ -10,6 +10,8 @@
 // All reductions accumulate in FP64 and are deterministic (fixed block order).
 // Every kernel returns at once (uniformly) when the solve is finished or failed,
 // so a whole solve can be captured once as a CUDA graph and replayed.
+#include <type_traits>
+#include "df32.cuh"
 #include "ovl_kernels.h"
 
 namespace ovl {
@@ -75,7 +77,11 @@ __global__ void __launch_bounds__(256) k_lanczos_step(const T* __restrict__ t, c
     }
     const cx<R> ca_ = mk(R(ca.r), R(ca.i)), da_ = mk(R(da.r), R(da.i));
     const cx<R> cg_ = mk(R(cg.r), R(cg.i)), db_ = mk(R(db.r), R(db.i));
-    double part[4] = {0.0, 0.0, 0.0, 0.0};  // Re/Im w^^dag v^, |v^|^2, |w^|^2
+    // per-thread sums of Re/Im w^^dag v^, |v^|^2, |w^|^2: FP64 for FP64 vectors; for FP32 vectors exact
+    // FP32 products summed as compensated FP32 pairs on the FP32 pipe (GB300's FP64 pipe would bound
+    // the kernel), widened to FP64 for the block and grid sums
+    using A = typename std::conditional<sizeof(R) == 4, AccF, AccD>::type;
+    A pa[4];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         cx<R> v = Elem<T>::ld(t, e) - ca_ * Elem<T>::ld(vi, e);
         cx<R> w = Elem<T>::ld(s, e) - da_ * Elem<T>::ld(wi, e);
@@ -89,12 +95,15 @@ __global__ void __launch_bounds__(256) k_lanczos_step(const T* __restrict__ t, c
         }
         Elem<T>::st(vn, e, v);
         Elem<T>::st(wn, e, w);
-        const cx<double> vd = up(v), wd = up(w);
-        const cx<double> z = cdot(wd, vd);
-        part[0] += z.r;
-        part[1] += z.i;
-        part[2] += norm2(vd);
-        part[3] += norm2(wd);
+        acc_cdot(pa, w, v);  // w^^dag v^
+        acc_norm2(pa[2], v);
+        acc_norm2(pa[3], w);
+    }
+    double part[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if constexpr (sizeof(R) == 4) part[j] = (double)pa[j].hi + (double)pa[j].lo;
+        else part[j] = pa[j].v;
     }
     double out[4];
     if (grid_sum_last<4>(part, partials, counter, out, red)) {
