@@ -98,9 +98,11 @@ typedef struct ovl_ctx ovl_ctx;
                                      process (Sec. 2, Eq. 2.2-2.3) in exact arithmetic             */
 #define OVL_PASS2_DF     0x100000 /* MIXED: regeneration pass in double-float arithmetic (FP32 pairs,
                                     about 48 significant bits, on the FP32 pipe).  Default: double-
-                                    float in batched solves, FP64 in single solves (one source per
-                                    tile is latency bound, where double-float's longer dependency
-                                    chains cost more than the narrow FP64 pipe)                   */
+                                    float in batched solves and in single mixed 2sL solves on lattices
+                                    above the persistent limit (run as a batch of one), FP64 in the
+                                    other single solves (one source per tile is latency bound, where
+                                    double-float's longer dependency chains cost more than the
+                                    narrow FP64 pipe)                                              */
 #define OVL_NO_GRAPH     0x2000  /* sign_krylov: launch kernels directly, no CUDA graph     */
 #define OVL_STENCIL_SITE  0x10000 /* apply_Dw: force one thread per site (default: by volume)    */
 #define OVL_STENCIL_SPLIT 0x20000 /* apply_Dw: force the direction-split layout (4 threads/site)   */
@@ -318,7 +320,11 @@ int ovl_get_deflation(ovl_ctx* ctx, int* m_out, double* lambda, void* R, void* L
  * stored: k + 1 vectors of 16 bytes per complex element, FP64 or double-float with OVL_MIXED).
  * Returns OVL_EBREAKDOWN on a serious 2sL breakdown (out holds the
  * approximation from the steps before it), OVL_ESINGULAR if the projected matrix has an
- * eigenvalue on the imaginary axis, OVL_ENOCONV if the inner sign did not converge. */
+ * eigenvalue on the imaginary axis, OVL_ENOCONV if the inner sign did not converge.
+ * OVL_LANCZOS2 with OVL_MIXED (and no flags but OVL_OVERLAP, OVL_HOST) on a lattice whose tiles do
+ * not fit the persistent passes (more than 8 tiles of 32 sites per SM) runs as a batch of one
+ * (ovl_batch_solve: double-float regeneration, autotuned launch shapes); the context keeps that
+ * batch and its graph until its gauge field, deflation set, stream or buffers change. */
 int ovl_sign_krylov(ovl_ctx* ctx, int method, int k, double mu, double kappa,
                     const void* b, void* out, int flags, ovl_info* info);
 

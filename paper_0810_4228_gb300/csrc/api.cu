@@ -65,9 +65,16 @@ void free_solve(ovl_ctx* c) {
     c->partials_bytes = 0;
 }
 
-void drop_graph(ovl_ctx* c) {
+void drop_solve_graph(ovl_ctx* c) {
     if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
     c->graph = GraphEntry();
+}
+
+void drop_graph(ovl_ctx* c) {
+    drop_solve_graph(c);
+    // the one-sequence batch captured the context's buffers and settings as well
+    if (c->self_batch) ovl_batch_destroy(c->self_batch);
+    c->self_batch = nullptr;
 }
 
 // fixed-size buffers (independent of k)
@@ -831,7 +838,7 @@ int sign_solve(ovl_ctx* c, int method, int k, int rs, double mu, double kappa, c
         GraphEntry& ge = c->graph;
         if (!(ge.valid && ge.method == method && ge.k == k && ge.rs == rs && ge.flags == gflags && ge.m == c->m &&
               ge.mu == mu && ge.kappa == kappa)) {
-            drop_graph(c);
+            drop_solve_graph(c);
             cudaGraph_t graph = nullptr;
             // capture on a private stream (the caller's may be the legacy default stream, which
             // cannot be captured); the graph is then launched on the caller's stream
@@ -906,6 +913,24 @@ int ovl_sign_krylov(ovl_ctx* c, int method, int k, double mu, double kappa, cons
         return fail(c, OVL_EINVAL, "mu/kappa differ from those of the installed deflation");
     if (method == OVL_ARNOLDI && (flags & OVL_TWO_PASS))
         return fail(c, OVL_EINVAL, "two-pass is defined for two-sided Lanczos only");
+    // mixed two-sided Lanczos on a lattice too large for the persistent passes: the batched kernels
+    // as a batch of one (the stepwise path's FP64 regeneration is bound by the FP64 pipe; the
+    // batch regenerates in double-float).  Options only the stepwise path has keep it.
+    if (method == OVL_LANCZOS2 && (flags & OVL_MIXED) && !(flags & ~(OVL_MIXED | OVL_OVERLAP | OVL_HOST)) &&
+        !ovl::persistent_ok(c->g, c->num_sms)) {
+        if (!c->self_batch) {
+            const int one = 1;
+            ovl_ctx* self = c;
+            const int rb = ovl_batch_create(&c->self_batch, &self, 1, &one);
+            if (rb) {
+                c->self_batch = nullptr;
+                return fail(c, rb, "one-sequence batch");
+            }
+        }
+        const int rs = ovl_batch_solve(c->self_batch, k, mu, kappa, &b, &out, flags, info);
+        if (rs) return fail(c, rs, ovl_batch_last_error(c->self_batch));
+        return OVL_OK;
+    }
     return sign_solve(c, method, k, 0, mu, kappa, b, out, flags, info);
 }
 

@@ -867,6 +867,7 @@ struct ovl_batch {
     // graph
     cudaGraphExec_t exec = nullptr;
     int g_k = -1, g_flags = 0;
+    std::vector<int> g_m;  // deflation size of every context when the graph was captured
     double g_mu = 0, g_kappa = 0;
     std::string err;
 };
@@ -1497,7 +1498,10 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
         r = enqueue_batch(b, k, mu, kappa, flags, st);
         if (r) return r;
     } else {
-        if (!b->exec || b->g_k != k || b->g_flags != gflags || b->g_mu != mu || b->g_kappa != kappa) {
+        std::vector<int> msig;
+        for (const ovl_ctx* c : b->ctx) msig.push_back(c->m);
+        if (!b->exec || b->g_k != k || b->g_flags != gflags || b->g_mu != mu || b->g_kappa != kappa ||
+            b->g_m != msig) {
             if (b->exec) cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
             if (!b->cap_st && cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking) != cudaSuccess)
@@ -1519,6 +1523,7 @@ int ovl_batch_solve(ovl_batch* b, int k, double mu, double kappa, const void* co
                 return bfail(b, OVL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
             }
             b->g_k = k, b->g_flags = gflags, b->g_mu = mu, b->g_kappa = kappa;
+            b->g_m = msig;
         }
         if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return bfail(b, OVL_ECUDA, "graph launch");
     }

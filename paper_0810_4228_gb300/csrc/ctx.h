@@ -39,6 +39,9 @@ struct ovl_ctx {
     size_t n = 0;  // 12 V complex per vector
     cudaStream_t st = nullptr;
     cudaStream_t cap_st = nullptr;  // private stream the solve graph is captured on
+    // one-sequence batch that runs mixed two-sided Lanczos solves on lattices too large for the
+    // persistent passes (its regeneration is the double-float kernel), created on first use
+    ovl_batch* self_batch = nullptr;
     int device = 0, num_sms = 0;
     std::string err;
 

@@ -325,3 +325,84 @@ def test_batch_tuning_cache(ovl, small, tmp_path, monkeypatch):
     assert np.array_equal(y1, y2)
     bt.close()
     bt2.close()
+
+
+@pytest.fixture(scope="module")
+def big(ovl):
+    """16^3 x 12 (49152 sites): more tiles than the persistent passes hold on chip on 152 SMs
+    (at most 8 tiles of 32 sites per block), so single-source mixed solves take the batched
+    kernels as a batch of one."""
+    dims, mu = (16, 16, 16, 12), 0.2
+    U = synth.gauge_field(dims, 1.0, 3300)
+    return dict(dims=dims, mu=mu, U=U, b=synth.gaussian_source(dims, 3301))
+
+
+def test_single_source_mixed_routed_through_batch_of_one(ovl, big):
+    """A mixed two-sided Lanczos solve of one source on a lattice above the persistent limit runs the
+    batched kernels (double-float regeneration): bitwise the result of a user batch of one, and at
+    small k the same process as the stepwise mixed path and the FP64 solve (Sec. 5)."""
+    ctx = _ctx(ovl, big["dims"], big["U"])
+    b = torch_c128(big["b"])
+    mu = big["mu"]
+    y_r, i_r = ctx.sign_krylov(ovl.LANCZOS2, 30, mu, KAPPA, b, flags=ovl.MIXED)
+    assert i_r["status"] == 0 and i_r["k_used"] == 30
+    bt = ovl.Batch([ctx], [1])
+    y_b = bt.solve(30, mu, KAPPA, [b.reshape(1, -1)], flags=ovl.MIXED)[0][0].cpu().numpy()[0]
+    bt.close()
+    y_r = y_r.cpu().numpy()
+    assert np.array_equal(y_r, y_b)
+    y_s, _ = ctx.sign_krylov(ovl.LANCZOS2, 30, mu, KAPPA, b, flags=ovl.MIXED | ovl.STEPWISE)
+    y_64, _ = ctx.sign_krylov(ovl.LANCZOS2, 30, mu, KAPPA, b)
+    assert rel(y_r, y_s.cpu().numpy()) < 1e-6
+    assert rel(y_r, y_64.cpu().numpy()) < 1e-5
+
+
+def test_single_source_mixed_routed_deflated_converged(ovl, big):
+    """With 20 deflated critical pairs the routed mixed solve reaches the FP64 two-pass result of the
+    same k to 1e-8 (the accuracy target of Sec. 5); D_ov b with host buffers equals b + gamma5 y; a
+    changed deflation set (m = 20 -> 8) is taken up by the next solve."""
+    ctx = _ctx(ovl, big["dims"], big["U"])
+    mu, k = big["mu"], 600
+    e = ctx.deflation_eigs(mu, KAPPA, 20)
+    assert e["m"] == 20
+    b = torch_c128(big["b"])
+    y_r, i_r = ctx.sign_krylov(ovl.LANCZOS2, k, mu, KAPPA, b, flags=ovl.MIXED)
+    y_64, i_64 = ctx.sign_krylov(ovl.LANCZOS2, k, mu, KAPPA, b, flags=ovl.TWO_PASS)
+    assert i_r["status"] == 0 and i_64["status"] == 0
+    # |b_perp^R| after the oblique split (Eq. 4.5): the same in both paths, not |b|
+    assert abs(i_r["bperp_norm"] - i_64["bperp_norm"]) < 1e-6 * i_64["bperp_norm"]
+    assert abs(i_r["bperp_norm"] - np.linalg.norm(big["b"])) > 1e-6 * i_64["bperp_norm"]
+    y_r, y_64 = y_r.cpu().numpy(), y_64.cpu().numpy()
+    assert rel(y_r, y_64) < 1e-8
+    bh = np.ascontiguousarray(big["b"])
+    yo, _ = ctx.sign_krylov(ovl.LANCZOS2, k, mu, KAPPA, bh, flags=ovl.MIXED | ovl.OVERLAP)
+    g5 = np.tile(np.repeat([1.0, 1, -1, -1], 3), synth.volume(big["dims"]))
+    assert isinstance(yo, np.ndarray)
+    assert rel(yo, bh + g5 * y_r) < 1e-14
+    lam, R, L = ctx.get_deflation()
+    ctx.set_deflation(mu, KAPPA, lam[:8], R[:8].contiguous(), L[:8].contiguous())
+    y8, _ = ctx.sign_krylov(ovl.LANCZOS2, 40, mu, KAPPA, b, flags=ovl.MIXED)
+    y8s, _ = ctx.sign_krylov(ovl.LANCZOS2, 40, mu, KAPPA, b, flags=ovl.MIXED | ovl.STEPWISE)
+    assert rel(y8.cpu().numpy(), y8s.cpu().numpy()) < 1e-6
+
+
+def test_user_batch_recaptures_on_deflation_change(ovl):
+    """A batch's captured graph holds each context's deflation size: after set_deflation changes
+    it (m = 8 -> 4) the next solve re-captures and equals a fresh batch's solve."""
+    c4 = config4()
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:8]
+    R, L = X[:, idx].T.copy(), Xi[idx, :].conj().copy()
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(R), torch_c128(L))
+    b = torch_c128(_sources(c4["dims"], 4500, 1))
+    bt = ovl.Batch([ctx], [1])
+    y8 = bt.solve(30, c4["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx[:4]], torch_c128(R[:4]), torch_c128(L[:4]))
+    y4 = bt.solve(30, c4["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    bt2 = ovl.Batch([ctx], [1])
+    y4f = bt2.solve(30, c4["mu"], KAPPA, [b], flags=ovl.MIXED)[0][0].cpu().numpy()
+    assert np.array_equal(y4, y4f)
+    assert rel(y4, y8) > 1e-6  # the deflation size changes the k = 30 result
+    bt.close()
+    bt2.close()
