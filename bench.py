@@ -68,6 +68,7 @@ K_REF = 1000
 RS_M, RS_MAX_CYCLES = 60, 24  # restarted Arnoldi extra: steps per cycle (fastest of 40-200 at 8^4), most cycles
 OV_NEV = 6  # eigenvalues of D_ov nearest 0 in the 8^4 extras
 DW_DIMS = (48, 48, 48, 64)  # 7.1M sites: every stencil operand is far larger than L2
+LARGE_K = 40  # Krylov steps of the single-source timing on that lattice (cost per step)
 NRHS = 12
 WORKLOAD8 = ("8^4 lattice (N=49152), SU(3) exp(i*1.0*H) links, m_w=-1.5, mu=0.3, batches of 12 Gaussian b, "
              "two-sided Lanczos, 20 eigenvalues of smallest |Re lambda| deflated")
@@ -255,8 +256,36 @@ def time_solves(torch, ctx, fn, bufs, warmup, steps, flush):
     return times
 
 
-def dw_bandwidth(torch, ovl, reps=20, dims=DW_DIMS):
-    """Stencil GB/s on a lattice far larger than L2 (device-layout vectors)."""
+def large_single_source(torch, ovl, ctx, k=LARGE_K):
+    """One Gaussian source on the stencil lattice, mixed two-sided Lanczos at a fixed k (the cost
+    per Krylov step, not a converged solve): the default path (on a lattice above the persistent
+    limit, the batched kernels as a batch of one, double-float regeneration) against the stepwise
+    single-source kernels (FP64 regeneration), each against the FP64 two-pass solve of the same k.
+    The lattice is far larger than L2, so no flush is needed between solves."""
+    b = torch.randn(ctx.n, dtype=torch.complex128, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+    y = torch.empty_like(b)
+    st = torch.cuda.current_stream()
+    out = {"k": k, "mu": MU}
+    y64 = ctx.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, b, flags=ovl.TWO_PASS)[0].clone()
+    for name, fl in (("default_batch_of_one", ovl.MIXED), ("stepwise", ovl.MIXED | ovl.STEPWISE)):
+        ctx.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, b, y, flags=fl)  # tuning, graph capture
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.sign_krylov(ovl.LANCZOS2, k, MU, KAPPA, b, y, flags=fl)
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        err = (torch.linalg.vector_norm(y - y64) / torch.linalg.vector_norm(y64)).item()
+        out[name] = {"ms": round(statistics.median(ts), 2), "rel_vs_fp64_two_pass": err}
+    del b, y, y64
+    return out
+
+
+def dw_bandwidth(torch, ovl, reps=20, dims=DW_DIMS, single_source=None):
+    """Stencil GB/s on a lattice far larger than L2 (device-layout vectors).  With a dict for
+    single_source, also the single-source solve timing of large_single_source on that lattice."""
     from paper_0810_4228_gb300 import synth
     V = dims[0] * dims[1] * dims[2] * dims[3]
     ctx = ovl.Context(dims)
@@ -300,6 +329,12 @@ def dw_bandwidth(torch, ovl, reps=20, dims=DW_DIMS):
             res["pair_f32_12"] = {"ms": msp, "GB_s": 576 * V / msp / 1e6, "GFLOP_s": 2 * DW_FLOP_SITE * V / msp / 1e6}
             del w, t, s
         del x, y
+    torch.cuda.empty_cache()
+    if single_source is not None:
+        try:
+            single_source.update(large_single_source(torch, ovl, ctx))
+        except Exception as exc:  # report, keep the stencil measurement
+            single_source["error"] = repr(exc)[:200]
     ctx.close()
     torch.cuda.empty_cache()
     return dims, V, res
@@ -994,9 +1029,10 @@ def run_ours(args, world, rank, local):
             except Exception as exc:  # report, keep the headline measurement
                 extras["autograd"] = {"error": repr(exc)[:200]}
     dw = None
+    single_large = {}
     if rank == 0 and not args.no_dw:
         try:
-            ddims, dV, dres = dw_bandwidth(torch, ovl)
+            ddims, dV, dres = dw_bandwidth(torch, ovl, single_source=single_large)
         except Exception as exc:  # report, keep the solve measurement
             dres, ddims, dV = {}, DW_DIMS, 0
             dw = {"error": repr(exc)[:200]}
@@ -1010,6 +1046,8 @@ def run_ours(args, world, rank, local):
                 dw[nm]["traffic"] = DW_TRAFFIC[nm]
                 dw[nm]["traffic_over_algorithmic"] = round(DW_TRAFFIC[nm] / (DW_BYTES[nm] * dV), 3)
         dw["hbm_peak_gbs"] = hbm_peak
+        if single_large:
+            dw["single_source_mixed"] = single_large
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
