@@ -198,20 +198,23 @@ __device__ __forceinline__ void load_link_df(const dfc* __restrict__ U, int V, i
     }
 }
 
-// in-block accumulators: compensated FP32 pairs for FP32 data, plain FP64 for FP64 data
+// in-block accumulators: compensated FP32 pairs for FP32 data, plain FP64 for FP64 data.
+// AccF adds each exact product p + pe (TwoProduct by FMA) with TwoSum into hi and collects the
+// rounding errors and the pe terms in lo (the compensated dot product of Ogita, Rump and Oishi,
+// 2005, kept as an unevaluated pair); host-callable so that its accuracy can be checked on the CPU.
 struct AccF {
     float hi = 0.f, lo = 0.f;
 };
-__device__ __forceinline__ void acc_add(AccF& a, float p, float pe) {
-    const float s = __fadd_rn(a.hi, p);
-    const float bb = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+OVL_HD void acc_add(AccF& a, float p, float pe) {
+    const float s = DF_ADD(a.hi, p);
+    const float bb = DF_SUB(s, a.hi);
+    const float e = DF_ADD(DF_SUB(a.hi, DF_SUB(s, bb)), DF_SUB(p, bb));
     a.hi = s;
-    a.lo = __fadd_rn(a.lo, __fadd_rn(e, pe));
+    a.lo = DF_ADD(a.lo, DF_ADD(e, pe));
 }
-__device__ __forceinline__ void acc_prod(AccF& a, float x, float y, float sg = 1.f) {
-    const float p = __fmul_rn(x, y);
-    const float pe = __fmaf_rn(x, y, -p);
+OVL_HD void acc_prod(AccF& a, float x, float y, float sg = 1.f) {
+    const float p = DF_MUL(x, y);
+    const float pe = DF_FMA(x, y, -p);
     acc_add(a, sg * p, sg * pe);
 }
 struct AccD {

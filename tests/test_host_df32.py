@@ -47,6 +47,12 @@ void w_dot(int n, const float* a, const float* b, const int* neg, float* o) {
     }
     df z = ovl::dfacc_value(A); o[0] = z.hi; o[1] = z.lo;
 }
+// sum_i sg_i x_i y_i of FP32 data with the kernels' in-block accumulator AccF (hi, lo unrounded)
+void w_accf(int n, const float* x, const float* y, const float* sg, float* o) {
+    ovl::AccF A;
+    for (int i = 0; i < n; ++i) ovl::acc_prod(A, x[i], y[i], sg[i]);
+    o[0] = A.hi; o[1] = A.lo;
+}
 }
 """
 
@@ -69,6 +75,7 @@ def lib():
     for nm in ("w_mul", "w_add", "w_add_lazy"):
         getattr(L, nm).argtypes = [f, f, f, f, pf]
     L.w_dot.argtypes = [ctypes.c_int, pf, pf, pi, pf]
+    L.w_accf.argtypes = [ctypes.c_int, pf, pf, pf, pf]
     return L
 
 
@@ -147,3 +154,59 @@ def test_sum_of_products(lib, n):
         exact = sum(terms, Fraction(0))
         mag = sum((abs(t) for t in terms), Fraction(0))
         assert abs(_val(o) - exact) <= (n + 8) * U2 * mag
+
+
+def _accf(lib, x, y, sg):
+    n = len(x)
+    o = _out()
+    lib.w_accf(n, (ctypes.c_float * n)(*x), (ctypes.c_float * n)(*y), (ctypes.c_float * n)(*sg), o)
+    return o
+
+
+@pytest.mark.parametrize("n", [1, 12, 24, 200, 2000])
+def test_compensated_fp32_sum_of_products(lib, n):
+    """AccF, the per-thread accumulator of the FP32 kernels' reductions (alpha = w^dag t, the norms
+    and w^^dag v^ of Eq. 4.2): every FP32 product enters exactly (FMA TwoProduct), the leading parts
+    are added with TwoSum and the errors in FP32, so hi + lo is within gamma_2n^2 of the sum of
+    the products' magnitudes (gamma_m = m u / (1 - m u)) of the exact sum, the bound of the
+    compensated dot product (Ogita, Rump and Oishi, 2005) without its final rounding."""
+    rng = random.Random(100 + n)
+    u = Fraction(1, 2 ** 24)
+    g2n = (2 * n * u) / (1 - 2 * n * u)
+    for _ in range(100 if n < 2000 else 10):
+        x = [float(np.float32(rng.uniform(-1, 1) * 2.0 ** rng.randint(-8, 8))) for _ in range(n)]
+        y = [float(np.float32(rng.uniform(-1, 1) * 2.0 ** rng.randint(-8, 8))) for _ in range(n)]
+        sg = [rng.choice((1.0, -1.0)) for _ in range(n)]
+        o = _accf(lib, x, y, sg)
+        terms = [Fraction(a) * Fraction(b) * int(g) for a, b, g in zip(x, y, sg)]
+        exact = sum(terms, Fraction(0))
+        mag = sum((abs(t) for t in terms), Fraction(0))
+        assert abs(_val(o) - exact) <= g2n * g2n * mag
+
+
+def test_compensated_fp32_sum_under_cancellation(lib):
+    """Products that cancel to a sum 1e6 times smaller than their magnitudes: plain FP32
+    accumulation loses every digit, AccF keeps the exact sum to the gamma_2n^2 bound."""
+    rng = random.Random(7)
+    n = 64
+    u = Fraction(1, 2 ** 24)
+    g2n = (2 * n * u) / (1 - 2 * n * u)
+    for _ in range(50):
+        half = [(float(np.float32(rng.uniform(0.5, 1) * 2.0 ** rng.randint(-4, 4))),
+                 float(np.float32(rng.uniform(0.5, 1)))) for _ in range(n // 2)]
+        x = [a for a, _ in half] + [a for a, _ in half]
+        y = [b for _, b in half] + [float(np.float32(b * (1 + rng.uniform(-1e-6, 1e-6)))) for _, b in half]
+        sg = [1.0] * (n // 2) + [-1.0] * (n // 2)
+        order = list(range(n))
+        rng.shuffle(order)
+        x, y, sg = [x[i] for i in order], [y[i] for i in order], [sg[i] for i in order]
+        o = _accf(lib, x, y, sg)
+        terms = [Fraction(a) * Fraction(b) * int(g) for a, b, g in zip(x, y, sg)]
+        exact = sum(terms, Fraction(0))
+        mag = sum((abs(t) for t in terms), Fraction(0))
+        err = abs(_val(o) - exact)
+        assert err <= g2n * g2n * mag
+        plain = np.float32(0)
+        for a, b, g in zip(x, y, sg):
+            plain = np.float32(plain + np.float32(np.float32(a) * np.float32(b)) * np.float32(g))
+        assert err * 1000 < abs(Fraction(float(plain)) - exact) or abs(Fraction(float(plain)) - exact) == 0
