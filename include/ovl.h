@@ -87,6 +87,9 @@ typedef struct ovl_ctx ovl_ctx;
                                     out of every FP32 pass-1 vector (v^ -= R L^dag v^, w^ -= L R^dag w^).
                                     Off by default: with FP32 copies of R, L the projected operator
                                     differs from A at the 1e-8 level, which then bounds the accuracy */
+/* OVL_REPROJ applied every p-th step only (1 <= p <= 127): the pass-1 vectors of the steps i with
+ * (i + 1) % p == 0 are projected; p = 1 is OVL_REPROJ.  p > 1 runs the stepwise kernels. */
+#define OVL_REPROJ_PERIOD(p) (OVL_REPROJ | (((p) & 0x7f) << 24))
 #define OVL_STEPWISE     0x40000 /* sign_krylov MIXED: one kernel per recurrence step instead of the
                                     persistent cooperative kernels (default on small lattices)   */
 #define OVL_PASS2_F64    0x80000 /* MIXED: regeneration pass in native FP64                       */

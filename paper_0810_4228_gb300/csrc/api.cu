@@ -316,6 +316,7 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
     const bool twopass = mixed || (flags & OVL_TWO_PASS);
     const int m = c->m;
     const int mproj = (flags & OVL_REPROJ) ? m : 0;
+    const int rperiod = (flags & OVL_REPROJ) ? std::max(1, (flags >> 24) & 0x7f) : 1;  // OVL_REPROJ_PERIOD
 
     prof(c, KC_SETUP, [&] { ovl::launch_state_init(ks, st); });
     if (m > 0) {
@@ -341,7 +342,7 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
             cudaMemcpyAsync(c->W64[0], c->bL, n * sizeof(double2), cudaMemcpyDeviceToDevice, st);
         }
         // pass 1: basis (stored for one-pass FP64) and coefficients
-        const bool persist = mixed && !(flags & OVL_STEPWISE) && ovl::persistent_ok(g, c->num_sms);
+        const bool persist = mixed && !(flags & OVL_STEPWISE) && rperiod == 1 && ovl::persistent_ok(g, c->num_sms);
         if (persist) {
             cudaMemsetAsync(c->bar, 0, 64, st);
             int lr = 0;
@@ -361,19 +362,21 @@ int enqueue_solve(ovl_ctx* c, int method, int k, double mu, double kappa, int fl
                     ovl::launch_dslash_pair(c->U12, 1, c->v32[i % 3], c->w32[i % 3], c->t32, c->s32, mu, kappa, ks,
                                             c->alpha, i, k - 1, part, cnt, g, st);
                 });
-                // optional re-projection of the deflated directions (p = L^dag t, q = R^dag s)
+                // optional re-projection of the deflated directions (p = L^dag t, q = R^dag s), at the
+                // steps the period selects
                 double2* pq2 = c->pq + 2048;
-                if (i + 1 < k && mproj > 0)
+                const int mp = (i + 1) % rperiod == 0 ? mproj : 0;
+                if (i + 1 < k && mp > 0)
                     prof(c, KC_DEFLATE, [&] {
-                        ovl::launch_multidot_f32(c->L32, n, mproj, c->t32, pq2, part, n, st, ks);
-                        ovl::launch_multidot_f32(c->R32, n, mproj, c->s32, pq2 + mproj, part, n, st, ks);
+                        ovl::launch_multidot_f32(c->L32, n, mp, c->t32, pq2, part, n, st, ks);
+                        ovl::launch_multidot_f32(c->R32, n, mp, c->s32, pq2 + mp, part, n, st, ks);
                     }, 4);
                 if (i + 1 < k)
                     prof(c, KC_LSTEP, [&] {
                         ovl::launch_lanczos_step(1, c->t32, c->s32, c->v32[i % 3], c->w32[i % 3],
                                                  c->v32[(i + 2) % 3], c->w32[(i + 2) % 3], c->v32[(i + 1) % 3],
                                                  c->w32[(i + 1) % 3], ks, c->alpha, c->beta, c->gamma, c->vscale, i,
-                                                 k, part, cnt, n, st, c->R32, c->L32, pq2, mproj);
+                                                 k, part, cnt, n, st, c->R32, c->L32, pq2, mp);
                     });
             } else {
                 const double2* vi = twopass ? c->R64[i % 3] : c->V64 + (size_t)i * n;
@@ -830,8 +833,8 @@ int sign_solve(ovl_ctx* c, int method, int k, int rs, double mu, double kappa, c
     ovl::launch_pack_spinor(bin, c->b64, 0, c->g, c->st);
     CUDA_TRY(c, cudaGetLastError());
 
-    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_STEPWISE | OVL_PASS2_F64 |
-                                OVL_PASS2_DF | OVL_ARNOLDI_CGS2);
+    const int gflags = flags & (OVL_MIXED | OVL_TWO_PASS | OVL_INNER_NEWTON | OVL_REPROJ | OVL_REPROJ_PERIOD(0x7f) |
+                                OVL_STEPWISE | OVL_PASS2_F64 | OVL_PASS2_DF | OVL_ARNOLDI_CGS2);
     bool ran = false;
     c->prof_on = (flags & OVL_PROFILE) != 0;
     if (!(flags & (OVL_NO_GRAPH | OVL_PROFILE))) {

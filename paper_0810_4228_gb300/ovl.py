@@ -28,6 +28,13 @@ OVERLAP, MIXED, TWO_PASS, INNER_NEWTON, NO_GRAPH, PROFILE = 0x100, 0x200, 0x400,
 STENCIL_SITE, STENCIL_SPLIT, REPROJ, STEPWISE, PASS2_F64, PASS2_DF = 0x10000, 0x20000, 0x8000, 0x40000, 0x80000, 0x100000
 NO_TUNE, ARNOLDI_CGS2 = 0x200000, 0x400000
 
+
+def REPROJ_PERIOD(p: int) -> int:
+    """REPROJ applied every p-th step of the FP32 pass (1 <= p <= 127; p = 1 is REPROJ)."""
+    if not 1 <= int(p) <= 127:
+        raise ValueError("re-projection period must be within 1..127")
+    return REPROJ | ((int(p) & 0x7F) << 24)
+
 _ERRNAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EBREAKDOWN: "EBREAKDOWN",
              ESINGULAR: "ESINGULAR", ENOCONV: "ENOCONV", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE"}
 

@@ -58,3 +58,19 @@ def test_flags_match_header():
         m = re.search(r"#define\s+OVL_%s\s+(0x[0-9a-fA-F]+|\d+)" % name, src)
         assert m, name
         assert int(m.group(1), 0) == getattr(ovl, name), name
+
+
+def test_reprojection_period_matches_header():
+    """OVL_REPROJ_PERIOD(p) of the header (re-projection every p-th step) and the binding's
+    REPROJ_PERIOD encode p the same way, in bits 24-30 beside the OVL_REPROJ bit."""
+    from paper_0810_4228_gb300 import ovl
+    with open(os.path.join(ROOT, "include", "ovl.h")) as f:
+        src = f.read()
+    m = re.search(r"#define\s+OVL_REPROJ_PERIOD\(p\)\s+\(OVL_REPROJ \| \(\(\(p\) & 0x7f\) << 24\)\)", src)
+    assert m
+    for p in (1, 2, 5, 127):
+        assert ovl.REPROJ_PERIOD(p) == ovl.REPROJ | (p << 24)
+        assert ovl.REPROJ_PERIOD(p) < 2 ** 31  # a non-negative C int
+    for bad in (0, 128):
+        with pytest.raises(ValueError):
+            ovl.REPROJ_PERIOD(bad)

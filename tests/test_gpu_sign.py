@@ -350,6 +350,28 @@ def test_mixed_deflated_reprojection_option(ovl, c4):
     assert rel(y, c4["ref"]) < 1e-6
 
 
+def test_mixed_reprojection_period(ovl, c4):
+    """Re-projection every p-th step (stepwise kernels): p = 1 is the every-step re-projection,
+    bitwise; a period beyond k projects nothing, bitwise the stepwise solve without it; p = 5 stays
+    within the same bound as p = 1."""
+    lam, X, Xi = c4["lam"], c4["X"], c4["Xi"]
+    idx = np.argsort(np.abs(lam.real))[:20]
+    ctx = _ctx(ovl, c4["dims"], c4["U"])
+    ctx.set_deflation(c4["mu"], KAPPA, lam[idx], torch_c128(X[:, idx].T.copy()), torch_c128(Xi[idx, :].conj().copy()))
+    mu, b = c4["mu"], c4["b"]
+    st = ovl.MIXED | ovl.STEPWISE
+    y1, _ = _solve(ovl, ctx, ovl.LANCZOS2, 120, mu, b, flags=st | ovl.REPROJ)
+    y1p, _ = _solve(ovl, ctx, ovl.LANCZOS2, 120, mu, b, flags=st | ovl.REPROJ_PERIOD(1))
+    assert np.array_equal(y1, y1p)
+    y0, _ = _solve(ovl, ctx, ovl.LANCZOS2, 120, mu, b, flags=st)
+    yinf, _ = _solve(ovl, ctx, ovl.LANCZOS2, 120, mu, b, flags=ovl.MIXED | ovl.REPROJ_PERIOD(127))
+    assert np.array_equal(y0, yinf)
+    assert not np.array_equal(y0, y1)
+    y5, info = _solve(ovl, ctx, ovl.LANCZOS2, 300, mu, b, flags=ovl.MIXED | ovl.REPROJ_PERIOD(5))
+    assert info["status"] == 0
+    assert rel(y5, c4["ref"]) < 1e-6
+
+
 def test_newton_fallback_on_hard_spectrum(ovl):
     """Ritz values close to the imaginary axis (2^3 x 4, eps = 1.0, min |Re lambda| ~ 0.03):
     whatever inner method finishes, the result matches the dense sign."""
