@@ -75,16 +75,7 @@ template <class R> struct AccOf;
 template <> struct AccOf<float> { using T = AccF; };
 template <> struct AccOf<double> { using T = AccD; };
 
-// Pair addition for the block and sequence sums of AccF values (TwoSum of the leading parts)
-__device__ __forceinline__ AccF accf_add(AccF a, AccF b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-    AccF r;
-    r.hi = s;
-    r.lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
-    return r;
-}
+// accf_add(AccF, AccF), the pair addition of the block and sequence sums, is in df32.cuh
 __device__ __forceinline__ AccF acc_shfl(AccF a, int o) {
     AccF r;
     r.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);

@@ -217,6 +217,17 @@ OVL_HD void acc_prod(AccF& a, float x, float y, float sg = 1.f) {
     const float pe = DF_FMA(x, y, -p);
     acc_add(a, sg * p, sg * pe);
 }
+// Pair addition for the block and sequence sums of AccF values (TwoSum of the leading parts, the
+// trailing parts and the rounding error added in FP32)
+OVL_HD AccF accf_add(AccF a, AccF b) {
+    const float s = DF_ADD(a.hi, b.hi);
+    const float bb = DF_SUB(s, a.hi);
+    const float e = DF_ADD(DF_SUB(a.hi, DF_SUB(s, bb)), DF_SUB(b.hi, bb));
+    AccF r;
+    r.hi = s;
+    r.lo = DF_ADD(DF_ADD(a.lo, b.lo), e);
+    return r;
+}
 struct AccD {
     double v = 0.0;
 };

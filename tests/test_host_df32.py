@@ -47,6 +47,18 @@ void w_dot(int n, const float* a, const float* b, const int* neg, float* o) {
     }
     df z = ovl::dfacc_value(A); o[0] = z.hi; o[1] = z.lo;
 }
+// 32 lanes, each with an AccF sum of n products, combined as a warp's xor-butterfly of accf_add
+// (the order of the kernels' shuffle reductions); lane 0's pair out
+void w_accf_warp(int n, const float* x, const float* y, const float* sg, float* o) {
+    ovl::AccF a[32], b[32];
+    for (int l = 0; l < 32; ++l)
+        for (int i = 0; i < n; ++i) ovl::acc_prod(a[l], x[l * n + i], y[l * n + i], sg[l * n + i]);
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int l = 0; l < 32; ++l) b[l] = ovl::accf_add(a[l], a[l ^ off]);
+        for (int l = 0; l < 32; ++l) a[l] = b[l];
+    }
+    o[0] = a[0].hi; o[1] = a[0].lo;
+}
 // sum_i sg_i x_i y_i of FP32 data with the kernels' in-block accumulator AccF (hi, lo unrounded)
 void w_accf(int n, const float* x, const float* y, const float* sg, float* o) {
     ovl::AccF A;
@@ -76,6 +88,7 @@ def lib():
         getattr(L, nm).argtypes = [f, f, f, f, pf]
     L.w_dot.argtypes = [ctypes.c_int, pf, pf, pi, pf]
     L.w_accf.argtypes = [ctypes.c_int, pf, pf, pf, pf]
+    L.w_accf_warp.argtypes = [ctypes.c_int, pf, pf, pf, pf]
     return L
 
 
@@ -210,3 +223,25 @@ def test_compensated_fp32_sum_under_cancellation(lib):
         for a, b, g in zip(x, y, sg):
             plain = np.float32(plain + np.float32(np.float32(a) * np.float32(b)) * np.float32(g))
         assert err * 1000 < abs(Fraction(float(plain)) - exact) or abs(Fraction(float(plain)) - exact) == 0
+
+
+@pytest.mark.parametrize("n", [1, 12, 48])
+def test_compensated_fp32_warp_reduction(lib, n):
+    """32 per-lane AccF sums combined by the warp butterfly of accf_add (TwoSum of the leading parts,
+    the trailing parts and the error in FP32), as in the batched kernels' block and sequence sums:
+    within gamma_m^2 of the magnitudes, m = 2 n + 2 log2(32) + 2 roundings along any path."""
+    rng = random.Random(300 + n)
+    u = Fraction(1, 2 ** 24)
+    m = 2 * n + 12
+    gm = (m * u) / (1 - m * u)
+    N = 32 * n
+    for _ in range(40):
+        x = [float(np.float32(rng.uniform(-1, 1) * 2.0 ** rng.randint(-8, 8))) for _ in range(N)]
+        y = [float(np.float32(rng.uniform(-1, 1) * 2.0 ** rng.randint(-8, 8))) for _ in range(N)]
+        sg = [rng.choice((1.0, -1.0)) for _ in range(N)]
+        o = _out()
+        lib.w_accf_warp(n, (ctypes.c_float * N)(*x), (ctypes.c_float * N)(*y), (ctypes.c_float * N)(*sg), o)
+        terms = [Fraction(a) * Fraction(b) * int(g) for a, b, g in zip(x, y, sg)]
+        exact = sum(terms, Fraction(0))
+        mag = sum((abs(t) for t in terms), Fraction(0))
+        assert abs(_val(o) - exact) <= gm * gm * mag
