@@ -6,6 +6,8 @@ helper is compared with an independent definition.
   oracle's chiral gamma matrices;
 * the SU(3) products U h and U^dag h against numpy, and the third-row reconstruction of the
   12-real link format against the full matrix of a random SU(3) element;
+* complex division (Smith's algorithm) against exact rational arithmetic, at magnitudes where
+  the textbook formula over- or underflows;
 * the even/odd device layout: site_coord / internal_index are inverse bijections onto the
   lattice, the parity half matches (x1 + x2 + x3 + x4) mod 2, and neighbour() lands on the
   oracle's forward and backward neighbours, on lattices with odd spatial extents too."""
@@ -84,6 +86,12 @@ void w_row2(const double* U, double* out) {
         out[2 * a + 1] = L.u[2][a].i;
     }
 }
+// a / b by the library's complex division (the recurrence's 1 / beta, 1 / conj(gamma))
+void w_cdiv(double ar, double ai, double br, double bi, double* out) {
+    const cx<double> z = cdiv(mk(ar, ai), mk(br, bi));
+    out[0] = z.r;
+    out[1] = z.i;
+}
 // for every internal index i: coords[i] = (x1, x2, x3, x4, parity), back[i] = internal_index(x),
 // nbr[i][2 nu + d] = neighbour(x, nu, d ? -1 : +1)
 void w_geom(const int* dims, int* coords, int* back, int* nbr) {
@@ -126,6 +134,7 @@ def lib():
     L.w_mul_link.argtypes = [pd, pd, ctypes.c_int, pd]
     L.w_row2.argtypes = [pd, pd]
     L.w_geom.argtypes = [pi, pi, pi, pi]
+    L.w_cdiv.argtypes = [ctypes.c_double] * 4 + [pd]
     return L
 
 
@@ -219,3 +228,24 @@ def test_even_odd_layout_and_neighbours(lib, dims):
     for nu in range(4):
         assert np.array_equal(nbr[:, 2 * nu], internal_of_canon[fwd[canon, nu]])
         assert np.array_equal(nbr[:, 2 * nu + 1], internal_of_canon[bwd[canon, nu]])
+
+
+def test_complex_division(lib):
+    """a / b within a few ulps of the exact quotient (fractions), including |b|^2 outside the double
+    range, where dividing by |b|^2 directly would overflow or underflow."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(40)
+    cases = [(complex(*rng.standard_normal(2)) * 10.0 ** rng.integers(-8, 8),
+              complex(*rng.standard_normal(2)) * 10.0 ** rng.integers(-8, 8)) for _ in range(500)]
+    cases += [(1e300 + 1e300j, 1e300 + 2e300j), (1e-300 + 3e-300j, 2e-300 - 1e-300j), (1 + 1j, 1e-170 + 1e-170j),
+              (3.0 + 0j, 0 + 2j), (0j, 1 - 1j)]
+    for a, b in cases:
+        out = np.empty(2)
+        lib.w_cdiv(a.real, a.imag, b.real, b.imag, _dp(out))
+        assert np.isfinite(out).all(), (a, b)
+        ar, ai, br, bi = (Fr(v) for v in (a.real, a.imag, b.real, b.imag))
+        d = br * br + bi * bi
+        qr, qi = (ar * br + ai * bi) / d, (ai * br - ar * bi) / d
+        mag = max(abs(qr), abs(qi))
+        tol = 8 * Fr(2) ** -53 * mag
+        assert abs(Fr(out[0]) - qr) <= tol and abs(Fr(out[1]) - qi) <= tol, (a, b, out)
