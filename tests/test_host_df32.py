@@ -47,6 +47,20 @@ void w_dot(int n, const float* a, const float* b, const int* neg, float* o) {
     }
     df z = ovl::dfacc_value(A); o[0] = z.hi; o[1] = z.lo;
 }
+// the double-float link products of the regeneration: U (9 complex, row-major) and h (6 complex,
+// [spin][colour]) given as doubles, split into double-float; out = U h or U^dag h as hi, lo pairs
+void w_link_df(const double* U, const double* h, int dag, float* out) {
+    ovl::Link<df> L;
+    ovl::Half<df> x, o;
+    for (int e = 0; e < 9; ++e) L.u[e / 3][e % 3] = ovl::mk(df(U[2 * e]), df(U[2 * e + 1]));
+    for (int e = 0; e < 6; ++e) x.h[e / 3][e % 3] = ovl::mk(df(h[2 * e]), df(h[2 * e + 1]));
+    if (dag) ovl::mul_link_dag<df>(L, x, o);
+    else ovl::mul_link<df>(L, x, o);
+    for (int e = 0; e < 6; ++e) {
+        const ovl::cx<df> z = o.h[e / 3][e % 3];
+        out[4 * e] = z.r.hi; out[4 * e + 1] = z.r.lo; out[4 * e + 2] = z.i.hi; out[4 * e + 3] = z.i.lo;
+    }
+}
 // 32 lanes, each with an AccF sum of n products, combined as a warp's xor-butterfly of accf_add
 // (the order of the kernels' shuffle reductions); lane 0's pair out
 void w_accf_warp(int n, const float* x, const float* y, const float* sg, float* o) {
@@ -89,6 +103,8 @@ def lib():
     L.w_dot.argtypes = [ctypes.c_int, pf, pf, pi, pf]
     L.w_accf.argtypes = [ctypes.c_int, pf, pf, pf, pf]
     L.w_accf_warp.argtypes = [ctypes.c_int, pf, pf, pf, pf]
+    pd = ctypes.POINTER(ctypes.c_double)
+    L.w_link_df.argtypes = [pd, pd, ctypes.c_int, pf]
     return L
 
 
@@ -245,3 +261,46 @@ def test_compensated_fp32_warp_reduction(lib, n):
         exact = sum(terms, Fraction(0))
         mag = sum((abs(t) for t in terms), Fraction(0))
         assert abs(_val(o) - exact) <= gm * gm * mag
+
+
+@pytest.mark.parametrize("dag", [0, 1])
+def test_double_float_link_products(lib, dag):
+    """U h and U^dag h in double-float (the link multiply of the double-float regeneration, Eq. 1.2),
+    with U a random SU(3) matrix and h a random half spinor split from doubles: every output
+    component, a sum of six products, is within (6 + 8) u^2 of its terms' magnitudes of the exact
+    sum of the split inputs' products, and within 1e-13 of the FP64 product (the splits keep 48 of
+    the inputs' 53 bits)."""
+    import sys
+    sys.path.insert(0, ROOT)
+    from paper_0810_4228_gb300 import synth
+    rng = np.random.default_rng(50 + dag)
+    Us = synth.random_su3(30, 1.0, rng)
+    pd = ctypes.POINTER(ctypes.c_double)
+
+    def split(x):
+        hi = float(np.float32(x))
+        return Fraction(hi) + Fraction(float(np.float32(x - hi)))
+
+    for u in Us:
+        h = rng.standard_normal((2, 3)) + 1j * rng.standard_normal((2, 3))
+        ub = np.ascontiguousarray(u.reshape(9)).view(np.float64)
+        hb = np.ascontiguousarray(h.reshape(6)).view(np.float64)
+        out = (ctypes.c_float * 24)()
+        lib.w_link_df(ub.ctypes.data_as(pd), hb.ctypes.data_as(pd), dag, out)
+        got = np.array([float(Fraction(out[4 * e]) + Fraction(out[4 * e + 1])) +
+                        1j * float(Fraction(out[4 * e + 2]) + Fraction(out[4 * e + 3])) for e in range(6)]).reshape(2, 3)
+        M = u.conj().T if dag else u
+        ref = (M @ h.T).T
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+        # exact sums of the split inputs, component by component
+        Us_ = [[(split(M[a, k].real), split(M[a, k].imag)) for k in range(3)] for a in range(3)]
+        hs_ = [[(split(h[sp, k].real), split(h[sp, k].imag)) for k in range(3)] for sp in range(2)]
+        for sp in range(2):
+            for a in range(3):
+                tr = [Us_[a][k][0] * hs_[sp][k][0] for k in range(3)] + [-Us_[a][k][1] * hs_[sp][k][1] for k in range(3)]
+                ti = [Us_[a][k][0] * hs_[sp][k][1] for k in range(3)] + [Us_[a][k][1] * hs_[sp][k][0] for k in range(3)]
+                e = 3 * sp + a
+                for terms, q in ((tr, 0), (ti, 2)):
+                    val = Fraction(out[4 * e + q]) + Fraction(out[4 * e + q + 1])
+                    mag = sum((abs(t) for t in terms), Fraction(0))
+                    assert abs(val - sum(terms, Fraction(0))) <= 14 * U2 * mag
