@@ -204,8 +204,10 @@ int ovl_dw_grad(ovl_ctx* ctx, double mu, double kappa, const void* x, const void
  * deflation set) and nrhs[j] right-hand sides for context j.  Every sequence (context, rhs)
  * runs the two-sided Lanczos solve of ovl_sign_krylov (Sec. 4, Eq. 4.2-4.5), but each batched
  * kernel covers all sequences in one launch, with per-sequence reductions, and the whole solve
- * is captured as one CUDA graph (re-captured when k, mu, kappa or the precision change).
- * Precision: OVL_MIXED = FP32 pass 1 and FP64 regeneration pass (Sec. 5); otherwise FP64, one
+ * is captured as one CUDA graph (re-captured when k, mu, kappa, the precision or a context's
+ * deflation size change).
+ * Precision: OVL_MIXED = FP32 pass 1 and a regeneration pass in double-float arithmetic (about
+ * 48 significant bits; native FP64 with OVL_PASS2_F64) (Sec. 5); otherwise FP64, one
  * pass with the basis stored, or two passes with OVL_TWO_PASS or when the stored basis would
  * exceed 32 GiB.  The contexts must share one stream (the first's); the batch
  * owns its workspace (for n = 12 V summed over sequences: about 8 n FP32 + 7 n FP64 complex
@@ -215,8 +217,9 @@ int ovl_batch_create(ovl_batch** out, ovl_ctx* const* ctxs, int nctx, const int*
 int ovl_batch_destroy(ovl_batch* batch);
 const char* ovl_batch_last_error(const ovl_batch* batch);
 /* b[j], out[j]: nrhs[j] canonical complex128 vectors of context j, one after another (device,
- * or host with OVL_HOST).  flags: OVL_MIXED, OVL_TWO_PASS, OVL_OVERLAP, OVL_HOST, OVL_NO_GRAPH,
- * OVL_PROFILE.  info: one
+ * or host with OVL_HOST).  flags: OVL_MIXED, OVL_TWO_PASS, OVL_PASS2_F64, OVL_STEPWISE (pass 1
+ * one launch per step even when the batch fits one resident grid), OVL_NO_TUNE, OVL_OVERLAP,
+ * OVL_HOST, OVL_NO_GRAPH, OVL_PROFILE.  info: one
  * entry per sequence in (context, rhs) order (may be NULL).  OVL_PROFILE: eager launches with
  * per-phase events (see ovl_batch_profile).  Returns the first failing
  * sequence's status (the others' results are still written). */
