@@ -376,8 +376,10 @@ class Context:
 
     def sign_krylov(self, method: int, k: int, mu: float, kappa: float, b, out=None, flags: int = 0):
         """out = sgn(gamma5 D_w(mu)) b, or D_ov(mu) b with flags |= OVERLAP, by ARNOLDI or LANCZOS2.
-        flags |= MIXED: two-sided Lanczos in two passes (FP32 pass 1, FP64-accurate regeneration);
-        Arnoldi with its basis and Gram-Schmidt sweeps in double-float arithmetic.
+        flags |= MIXED: two-sided Lanczos in two passes (FP32 pass 1, FP64-accurate regeneration;
+        on lattices above the persistent kernels' limit run as a batch of one with double-float
+        regeneration); Arnoldi with its basis and Gram-Schmidt sweeps in double-float arithmetic.
+        REPROJ_PERIOD(p): re-projection of the deflated directions every p-th FP32 step.
         Returns (out, info dict).  b may be a CUDA tensor or host memory."""
         import torch
         if out is None:
